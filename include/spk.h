@@ -1,0 +1,191 @@
+/*
+ * spk.h -- C ABI of libspk, a GB300 (sm_103a) implementation of the
+ * sketched-and-truncated polynomial Krylov method (s-PKSM) of Palitta,
+ * Schweitzer and Simoncini, "Sketched and truncated polynomial Krylov
+ * subspace methods: matrix Sylvester equations" (arXiv 2311.16019), for
+ *
+ *     A X + X B = C1 C2^T,   A: n1 x n1, B: n2 x n2 sparse, C1: n1 x r,
+ *     C2: n2 x r,  r << n                                  (Eq. (1.1)).
+ *
+ * Conventions for every entry point
+ *  - Pointers named *_dev are DEVICE pointers on the handle's device; the
+ *    caller owns them and keeps them alive until the call returns.  Pointers
+ *    named *_host are host pointers.  Nothing is retained after a call except
+ *    the library-owned buffers inside spk_result (see spk_result_free).
+ *  - Block vectors (n x r) are ROW-MAJOR: element (i, c) at [i * r + c].
+ *  - CSR matrices are 0-based, int32 row pointers and column indices,
+ *    float64 values, columns sorted within each row.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; calls that return scalars or host
+ *    data synchronise that stream before returning.
+ *  - Return value: SPK_OK (0) or a negative SPK_ERR_* code.  A human-readable
+ *    reason is kept per handle (spk_last_error).  No call aborts, traps or
+ *    falls back to the CPU: every arithmetic step of the method runs in this
+ *    library's CUDA kernels.
+ */
+#ifndef SPK_H
+#define SPK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+    SPK_OK = 0,
+    SPK_ERR_ARG = -1,                 /* invalid argument / shape / size       */
+    SPK_ERR_CUDA = -2,                /* a CUDA runtime call failed            */
+    SPK_ERR_ALLOC = -3,               /* device allocation failed              */
+    SPK_ERR_BREAKDOWN = -4,           /* rank-deficient new block (Cholesky)   */
+    SPK_ERR_SINGULAR_PROJECTED = -5,  /* projected equation (Eq. (3.4)) not solvable
+                                         by the sign iteration (zero pivot or an
+                                         eigenvalue off the open right half plane) */
+    SPK_ERR_NONFINITE = -6,           /* NaN/Inf met in a reduction            */
+    SPK_ERR_NOT_CONVERGED = -7,       /* maxit reached; factors still returned */
+    SPK_ERR_TIMEOUT = -8,             /* bounded device/host wait expired      */
+    SPK_ERR_UNSUPPORTED = -9          /* option combination not built          */
+};
+
+/* ---- option enums ------------------------------------------------------ */
+enum { SPK_SKETCH_SRHT = 0, SPK_SKETCH_IDENTITY = 1 };
+enum { SPK_PREC_FP64 = 0, SPK_PREC_MIXED_FP32 = 1, SPK_PREC_MIXED_BF16 = 2 };
+enum { SPK_CHECK_EVERY_P = 0, SPK_CHECK_ADAPTIVE = 1 };
+/* host-side fault injection bits for spk_opts.inject (tests only) */
+enum {
+    SPK_INJECT_NAN_C1 = 1u << 0,      /* treat C1 as containing a NaN          */
+    SPK_INJECT_RANK_DEFICIENT = 1u << 1, /* duplicate column 0 of C1 into 1    */
+    SPK_INJECT_TIMEOUT = 1u << 2,     /* bounded waits get a zero budget       */
+    SPK_INJECT_SINGULAR = 1u << 3     /* make the projected solve report a zero pivot */
+};
+
+typedef struct spk_handle spk_handle;
+
+/* CSR operator on the device (caller-owned). */
+typedef struct spk_csr {
+    int32_t nrows, ncols;
+    int64_t nnz;
+    const int32_t* rowptr_dev;   /* nrows + 1 */
+    const int32_t* col_dev;      /* nnz */
+    const double*  val_dev;      /* nnz */
+} spk_csr;
+
+/* Options of Algorithm 1 (inputs k, maxit, tol, p, S_U, S_V) plus the
+ * implementation's choices.  spk_opts_default fills every field. */
+typedef struct spk_opts {
+    int32_t k_left;          /* truncation k for K(A, C1): orthogonalise the new
+                                block against the last k blocks (Eq. (2.3))    */
+    int32_t k_right;         /* truncation k for K(B^T, C2)                    */
+    int32_t s;               /* sketch rows (SRHT); ignored for IDENTITY       */
+    int32_t maxit;           /* maximum number of iterations d                 */
+    int32_t p;               /* check period of Algorithm 1                    */
+    int32_t sketch_kind;     /* SPK_SKETCH_*                                   */
+    int32_t precision;       /* SPK_PREC_*                                     */
+    int32_t check_schedule;  /* SPK_CHECK_EVERY_P or SPK_CHECK_ADAPTIVE        */
+    int32_t same_sketch;     /* nonzero: S_V = S_U (needs n1 == n2)            */
+    int32_t fixed_d;         /* >0: run exactly this many iterations, one check
+                                at the end, tol ignored                         */
+    int32_t max_newton;      /* cap on sign-function iterations (a9)           */
+    uint32_t inject;         /* SPK_INJECT_* (host-side), 0 in production      */
+    double tol;              /* stop when rho / ||beta1 beta2^T||_F < tol      */
+    double trunc_tol;        /* keep singular values of Y above trunc_tol*s_1  */
+    uint64_t seed;           /* sketch draws (SplitMix64 streams)              */
+    int32_t reserved[8];
+} spk_opts;
+
+/* Result of a solve.  X1/X2 and the history arrays are library-owned and
+ * released by spk_result_free. */
+typedef struct spk_result {
+    int32_t status;          /* SPK_OK, SPK_ERR_NOT_CONVERGED or an error      */
+    int32_t iters;           /* final d                                        */
+    int32_t rank;            /* ell: columns of X1 and X2                      */
+    int32_t n1, n2;
+    int32_t n_hist;          /* number of residual checks                      */
+    int32_t converged;
+    int32_t newton_iters;    /* sign-function iterations of the last check     */
+    double rel_rho;          /* last rho / ||beta1 beta2^T||_F                 */
+    double rho;              /* last sketched residual norm (Eq. (3.5))        */
+    double* X1_dev;          /* n1 x rank row-major, device                    */
+    double* X2_dev;          /* n2 x rank row-major, device                    */
+    int32_t* hist_d_host;    /* iteration of each check                        */
+    double* hist_rel_host;   /* rho / ||beta1 beta2^T|| at each check          */
+    int64_t mem_basis_vectors;    /* length-n vectors of the two windows       */
+    int64_t mem_solution_vectors; /* 2 * rank                                  */
+    double ms_arnoldi, ms_project, ms_recover;  /* GPU time per phase          */
+    int32_t reserved[8];
+} spk_result;
+
+/* ---- lifetime ---------------------------------------------------------- */
+int  spk_create(spk_handle** h, int device);
+void spk_destroy(spk_handle* h);
+const char* spk_last_error(spk_handle* h);
+const char* spk_status_string(int status);
+int  spk_version(void);
+void spk_opts_default(spk_opts* o);
+
+/* ---- the solver (Algorithm 1) -------------------------------------------
+ * spk_solve: the whole s-PKSM path of Algorithm 1 on the device.  A is the
+ * left operator (n1 x n1), BT = B^T (n2 x n2) generates K(B^T, C2)
+ * (Eq. (1.2)).  C1_dev (n1 x r), C2_dev (n2 x r) row-major device.
+ * 1 <= r <= 4.  Returns SPK_OK, SPK_ERR_NOT_CONVERGED (factors of the last
+ * check still returned) or an error (out->X1_dev == NULL).               */
+int spk_solve(spk_handle* h, const spk_csr* A, const spk_csr* BT,
+              const double* C1_dev, const double* C2_dev, int r,
+              const spk_opts* opts, void* stream, spk_result* out);
+
+/* spk_solve_adjoint: the transposed equation A^T L + L B^T = G1 G2^T with the
+ * same solver (operators A^T and B; L = X1 X2^T on return).  Used for the
+ * gradient of a loss of X (differentiate Eq. (1.1)).                      */
+int spk_solve_adjoint(spk_handle* h, const spk_csr* AT, const spk_csr* B,
+                      const double* G1_dev, const double* G2_dev, int q,
+                      const spk_opts* opts, void* stream, spk_result* out);
+
+/* spk_adjoint_gradients: given X = X1 X2^T (solution), L = L1 L2^T (adjoint),
+ * C1, C2 and the derivative operators A_theta = dA/dtheta, B_theta = dB/dtheta
+ * (CSR, device), writes dC1 = L C2 (n1 x r), dC2 = L^T C1 (n2 x r) row-major
+ * device, and *dtheta_host = -<L, A_theta X + X B_theta>_F.               */
+int spk_adjoint_gradients(spk_handle* h, const spk_result* X, const spk_result* L,
+                          const double* C1_dev, const double* C2_dev, int r,
+                          const spk_csr* A_theta, const spk_csr* B_theta,
+                          double* dC1_dev, double* dC2_dev, double* dtheta_host,
+                          void* stream);
+
+void spk_result_free(spk_result* res);
+
+/* ---- single steps, for parity tests ----------------------------------- */
+/* Sketch draws (Section 2.2; SplitMix64 streams as documented in the
+ * library): rows_dev[s] ascending in [0, n'), n' = 2^ceil(log2 n), and
+ * signs_dev[n] in {-1, +1}.                                               */
+int spk_sketch_draws(spk_handle* h, int64_t n, int32_t s, uint64_t seed,
+                     int32_t sketch_id, int32_t* rows_dev, int8_t* signs_dev,
+                     void* stream);
+/* SX = S X with S[j,i] = e_i (-1)^popcount(rho_j & i) / sqrt(s);
+ * X_dev n x r row-major, SX_dev s x r column-major.                       */
+int spk_sketch_apply(spk_handle* h, int64_t n, int32_t s, uint64_t seed,
+                     int32_t sketch_id, const double* X_dev, int32_t r,
+                     double* SX_dev, void* stream);
+/* Y = A X for CSR A and X_dev (ncols x r row-major), Y_dev (nrows x r).   */
+int spk_spmm(spk_handle* h, const spk_csr* A, const double* X_dev, int32_t r,
+             double* Y_dev, void* stream);
+/* Small dense Sylvester solve H Y + Y G^T = F (column-major m x m, device)
+ * by the scaled Newton sign iteration; Y_dev m x m column-major.          */
+int spk_sylvester_dense(spk_handle* h, int32_t m, const double* H_dev,
+                        const double* G_dev, const double* F_dev, double* Y_dev,
+                        int32_t* newton_iters_host, void* stream);
+
+/* Copy an internal FP64 buffer of the handle's last solve to the host, for
+ * element-wise parity tests of single steps: "U_T"/"V_T" (whitening factors
+ * T_U, T_V, (maxit+1) r square, column-major), "U_Ht"/"V_Ht" (projected
+ * matrices H~, G~, same layout), "U_hband"/"V_hband" (Hessenberg blocks:
+ * per iteration d, k+1 blocks r x r row-major; block q is h_{d-k+1+q, d},
+ * block k is h_{d+1,d}), "U_beta"/"V_beta" (r x r).  count = doubles wanted;
+ * *avail_out receives the buffer's size in doubles.  SPK_ERR_ARG if the
+ * name is unknown.                                                        */
+int spk_inspect(spk_handle* h, const char* name, double* dst_host, int64_t count,
+                int64_t* avail_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPK_H */

@@ -1,0 +1,466 @@
+// Truncated block Arnoldi kernels (Algorithm 1's basis loop; Eq. (2.3)).
+//
+// Per iteration d and operator (A, U) or (B^T, V):
+//   spmm_dots   : U~ = A U_d (thread per CSR row; the r-wide row of U is one
+//                 or two 16-byte loads) fused with the window inner products
+//                 h_{i,d} = U_i^T U~ for up to four window blocks; per-CTA
+//                 partial sums, reduced in a fixed order (deterministic).
+//   update_gram : U~ -= sum_i U_i h_{i,d} (classical Gram-Schmidt on the
+//                 locally orthonormal window -- equal to Algorithm 1's
+//                 modified Gram-Schmidt in exact arithmetic) and G = U~^T U~.
+//   chol_small  : Cholesky G = R^T R (R upper, positive diagonal), R^{-1}.
+//   scale_gram / scale_store : Cholesky QR applied twice (CholQR2):
+//                 U_{d+1} = (U~ R1^{-1}) R2^{-1}, h_{d+1,d} = R2 R1.
+// The second (two-pass) sweep re-runs spmm (no dots), update and the two
+// scalings with the stored coefficients, which reproduces U_j bit for bit.
+#include "spk_internal.cuh"
+
+#include <algorithm>
+
+namespace spk {
+
+namespace {
+
+constexpr int kFuse = 4;  // window blocks handled per dots pass
+
+template <int R, typename TB, typename TC>
+__device__ __forceinline__ void load_row(const TB* p, TC (&v)[R]) {
+#pragma unroll
+  for (int a = 0; a < R; ++a) v[a] = (TC)Store<TB>::ld(p + a);
+}
+
+// Block-wide sum of NV per-thread values; thread e < NV of warp 0..: result to out[e].
+template <int NV>
+__device__ void block_reduce_store(double (&acc)[NV], double* out) {
+  __shared__ double red[32][NV > 0 ? NV : 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int e = 0; e < NV; ++e) {
+    double v = warp_sum(acc[e]);
+    if (lane == 0) red[wid][e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NV; e += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w][e];
+    out[e] = s;
+  }
+  __syncthreads();
+}
+
+template <typename TB, typename TC, typename TV, int R, bool DOTS>
+__global__ void __launch_bounds__(256) k_spmm_dots(const int32_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ col,
+                                                   const TV* __restrict__ val, int64_t n,
+                                                   const TB* __restrict__ U, TC* __restrict__ W,
+                                                   WindowPtrs win, double* __restrict__ partial) {
+  double acc[DOTS ? kFuse * R * R : 1];
+  if constexpr (DOTS) {
+#pragma unroll
+    for (int e = 0; e < kFuse * R * R; ++e) acc[e] = 0.0;
+  }
+  const int nwin = DOTS ? win.nwin : 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    TC w[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) w[a] = TC(0);
+    const int e0 = rowptr[i], e1 = rowptr[i + 1];
+    for (int e = e0; e < e1; ++e) {
+      const TC v = (TC)val[e];
+      TC u[R];
+      load_row<R>(U + (int64_t)col[e] * R, u);
+#pragma unroll
+      for (int a = 0; a < R; ++a) w[a] = fma(v, u[a], w[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a) W[i * R + a] = w[a];
+    if constexpr (DOTS) {
+#pragma unroll
+      for (int q = 0; q < kFuse; ++q) {
+        if (q < nwin) {
+          TC u[R];
+          load_row<R>(static_cast<const TB*>(win.blk[q]) + i * R, u);
+#pragma unroll
+          for (int a = 0; a < R; ++a)
+#pragma unroll
+            for (int b = 0; b < R; ++b)
+              acc[(q * R + a) * R + b] = fma((double)u[a], (double)w[b], acc[(q * R + a) * R + b]);
+        }
+      }
+    }
+  }
+  if constexpr (DOTS) block_reduce_store<kFuse * R * R>(acc, partial + (int64_t)blockIdx.x * kFuse * R * R);
+}
+
+// Dots of an already computed U~ against up to four more window blocks.
+template <typename TB, typename TC, int R>
+__global__ void __launch_bounds__(256) k_dots(const TC* __restrict__ W, int64_t n, WindowPtrs win,
+                                              double* __restrict__ partial) {
+  double acc[kFuse * R * R];
+#pragma unroll
+  for (int e = 0; e < kFuse * R * R; ++e) acc[e] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    TC w[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) w[a] = W[i * R + a];
+#pragma unroll
+    for (int q = 0; q < kFuse; ++q) {
+      if (q < win.nwin) {
+        TC u[R];
+        load_row<R>(static_cast<const TB*>(win.blk[q]) + i * R, u);
+#pragma unroll
+        for (int a = 0; a < R; ++a)
+#pragma unroll
+          for (int b = 0; b < R; ++b)
+            acc[(q * R + a) * R + b] = fma((double)u[a], (double)w[b], acc[(q * R + a) * R + b]);
+      }
+    }
+  }
+  block_reduce_store<kFuse * R * R>(acc, partial + (int64_t)blockIdx.x * kFuse * R * R);
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nparts, int stride,
+                                  int count, double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += partial[(int64_t)p * stride + e];
+    out[e] = s;
+  }
+}
+
+template <typename TB, typename TC, int R>
+__global__ void __launch_bounds__(256) k_update_gram(TC* __restrict__ W, int64_t n, WindowPtrs win,
+                                                     const double* __restrict__ h,
+                                                     double* __restrict__ partial, int want_gram) {
+  __shared__ TC hs[kMaxWin * R * R];
+  for (int e = threadIdx.x; e < win.nwin * R * R; e += blockDim.x) hs[e] = (TC)h[e];
+  __syncthreads();
+  double acc[R * R];
+#pragma unroll
+  for (int e = 0; e < R * R; ++e) acc[e] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    TC w[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) w[a] = W[i * R + a];
+    for (int q = 0; q < win.nwin; ++q) {
+      TC u[R];
+      load_row<R>(static_cast<const TB*>(win.blk[q]) + i * R, u);
+      const TC* hq = hs + q * R * R;
+#pragma unroll
+      for (int b = 0; b < R; ++b) {
+        TC s = w[b];
+#pragma unroll
+        for (int a = 0; a < R; ++a) s = fma(-u[a], hq[a * R + b], s);
+        w[b] = s;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a) W[i * R + a] = w[a];
+    if (want_gram) {
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) acc[a * R + b] = fma((double)w[a], (double)w[b], acc[a * R + b]);
+    }
+  }
+  if (want_gram) block_reduce_store<R * R>(acc, partial + (int64_t)blockIdx.x * R * R);
+}
+
+// G = sum of partial Grams; R upper with R^T R = G; Rinv = R^{-1}.
+__global__ void k_chol_small(const double* __restrict__ partial, int nparts, int r,
+                             double* __restrict__ Rout, double* __restrict__ Rinv,
+                             uint32_t* flags, double rel_floor) {
+  __shared__ double G[kMaxR * kMaxR];
+  const int rr = r * r;
+  for (int e = threadIdx.x; e < rr; e += blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += partial[(int64_t)p * rr + e];
+    G[e] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double R[kMaxR][kMaxR] = {};
+  double tr = 0.0;
+  bool bad = false;
+  for (int a = 0; a < r; ++a) tr += G[a * r + a];
+  if (!isfinite(tr)) bad = true;
+  for (int j = 0; j < r && !bad; ++j) {
+    double s = G[j * r + j];
+    for (int l = 0; l < j; ++l) s -= R[l][j] * R[l][j];
+    if (!(s > rel_floor * tr) || !(tr > 0.0)) {
+      atomicOr(flags, kFlagBreakdown);
+      s = (tr > 0.0 && isfinite(tr)) ? fmax(s, rel_floor * tr) : 1.0;
+      if (!(s > 0.0)) s = 1.0;
+    }
+    R[j][j] = sqrt(s);
+    for (int i = j + 1; i < r; ++i) {
+      double t = G[j * r + i];
+      for (int l = 0; l < j; ++l) t -= R[l][j] * R[l][i];
+      R[j][i] = t / R[j][j];
+    }
+  }
+  if (bad) {
+    atomicOr(flags, kFlagNonfinite);
+    for (int a = 0; a < r; ++a) R[a][a] = 1.0;
+  }
+  double Ri[kMaxR][kMaxR] = {};
+  for (int j = 0; j < r; ++j) {
+    Ri[j][j] = 1.0 / R[j][j];
+    for (int i = j - 1; i >= 0; --i) {
+      double t = 0.0;
+      for (int l = i + 1; l <= j; ++l) t += R[i][l] * Ri[l][j];
+      Ri[i][j] = -t / R[i][i];
+    }
+  }
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b < r; ++b) {
+      if (Rout) Rout[a * r + b] = R[a][b];
+      if (Rinv) Rinv[a * r + b] = Ri[a][b];
+    }
+}
+
+template <typename TC, int R>
+__global__ void __launch_bounds__(256) k_scale_gram(TC* __restrict__ W, int64_t n,
+                                                    const double* __restrict__ Rinv,
+                                                    double* __restrict__ partial) {
+  __shared__ TC ri[R * R];
+  if (threadIdx.x < R * R) ri[threadIdx.x] = (TC)Rinv[threadIdx.x];
+  __syncthreads();
+  double acc[R * R];
+#pragma unroll
+  for (int e = 0; e < R * R; ++e) acc[e] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    TC w[R], o[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) w[a] = W[i * R + a];
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      TC s = TC(0);
+#pragma unroll
+      for (int a = 0; a <= b; ++a) s = fma(w[a], ri[a * R + b], s);
+      o[b] = s;
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a) W[i * R + a] = o[a];
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) acc[a * R + b] = fma((double)o[a], (double)o[b], acc[a * R + b]);
+  }
+  block_reduce_store<R * R>(acc, partial + (int64_t)blockIdx.x * R * R);
+}
+
+template <typename TB, typename TC, int R>
+__global__ void __launch_bounds__(256) k_scale_store(const TC* __restrict__ W, int64_t n,
+                                                     const double* __restrict__ Rinv,
+                                                     TB* __restrict__ dst) {
+  __shared__ TC ri[R * R];
+  if (threadIdx.x < R * R) ri[threadIdx.x] = (TC)Rinv[threadIdx.x];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    TC w[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) w[a] = W[i * R + a];
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      TC s = TC(0);
+#pragma unroll
+      for (int a = 0; a <= b; ++a) s = fma(w[a], ri[a * R + b], s);
+      Store<TB>::st(dst + i * R + b, s);
+    }
+  }
+}
+
+// X (n x ell, row-major FP64) += sum_q U_q Wrows[q r .. q r + r-1, :]
+template <typename TB>
+__global__ void k_x_accumulate(double* __restrict__ X, int64_t n, int ell, int r, WindowPtrs blocks,
+                               const double* __restrict__ Wrows, int64_t ldw) {
+  const int64_t total = n * ell;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ell;
+    const int c = (int)(e - i * ell);
+    double s = X[e];
+    for (int q = 0; q < blocks.nwin; ++q) {
+      const TB* u = static_cast<const TB*>(blocks.blk[q]) + i * r;
+      for (int a = 0; a < r; ++a) s = fma((double)Store<TB>::ld(u + a), Wrows[(q * r + a) + c * ldw], s);
+    }
+    X[e] = s;
+  }
+}
+
+__global__ void k_spmm_wide(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ val, int64_t n, int w,
+                            const double* __restrict__ X, double* __restrict__ Y) {
+  const int64_t total = n * w;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / w;
+    const int c = (int)(e - i * w);
+    double s = 0.0;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s = fma(val[k], X[(int64_t)col[k] * w + c], s);
+    Y[e] = s;
+  }
+}
+
+template <typename TD>
+__global__ void k_convert(const double* __restrict__ src, TD* __restrict__ dst, int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    Store<TD>::st(dst + e, (decltype(Store<TD>::ld(dst)))src[e]);
+}
+
+// mode 0: C = A B;  mode 1: C = A B^T  (r x r row-major)
+__global__ void k_combine_small(const double* A, const double* B, double* C, int r, int mode) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double out[kMaxR * kMaxR];
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b < r; ++b) {
+      double s = 0.0;
+      for (int l = 0; l < r; ++l) s += A[a * r + l] * (mode == 0 ? B[l * r + b] : B[b * r + l]);
+      out[a * r + b] = s;
+    }
+  for (int e = 0; e < r * r; ++e) C[e] = out[e];
+}
+
+int default_grid(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 4));
+}
+
+}  // namespace
+
+template <typename TB, typename TC, typename TV>
+void spmm_dots_launch(const int32_t* rowptr, const int32_t* col, const TV* val, int64_t n, int r,
+                      const TB* U, TC* W, WindowPtrs win, double* partial, int grid,
+                      cudaStream_t st) {
+  // first group fused with the product, further groups as separate passes
+  WindowPtrs g0 = win;
+  g0.nwin = std::min(win.nwin, kFuse);
+  const bool dots = win.nwin > 0;
+#define SPK_SPMM(RR)                                                                           \
+  if (dots)                                                                                    \
+    k_spmm_dots<TB, TC, TV, RR, true><<<grid, 256, 0, st>>>(rowptr, col, val, n, U, W, g0, partial); \
+  else                                                                                         \
+    k_spmm_dots<TB, TC, TV, RR, false><<<grid, 256, 0, st>>>(rowptr, col, val, n, U, W, g0, partial);
+  switch (r) {
+    case 1: SPK_SPMM(1) break;
+    case 2: SPK_SPMM(2) break;
+    case 3: SPK_SPMM(3) break;
+    default: SPK_SPMM(4) break;
+  }
+#undef SPK_SPMM
+  for (int g = kFuse; g < win.nwin; g += kFuse) {
+    WindowPtrs gw;
+    gw.nwin = std::min(kFuse, win.nwin - g);
+    for (int q = 0; q < gw.nwin; ++q) gw.blk[q] = win.blk[g + q];
+    double* part = partial + (int64_t)(g / kFuse) * grid * kFuse * r * r;
+    switch (r) {
+      case 1: k_dots<TB, TC, 1><<<grid, 256, 0, st>>>(W, n, gw, part); break;
+      case 2: k_dots<TB, TC, 2><<<grid, 256, 0, st>>>(W, n, gw, part); break;
+      case 3: k_dots<TB, TC, 3><<<grid, 256, 0, st>>>(W, n, gw, part); break;
+      default: k_dots<TB, TC, 4><<<grid, 256, 0, st>>>(W, n, gw, part); break;
+    }
+  }
+}
+
+void reduce_partials_launch(const double* partial, int nparts, int stride, int count,
+                            double* out, cudaStream_t st) {
+  k_reduce_partials<<<(count + 127) / 128, 128, 0, st>>>(partial, nparts, stride, count, out);
+}
+
+template <typename TB, typename TC>
+void update_gram_launch(TC* W, int64_t n, int r, WindowPtrs win, const double* h, double* partial,
+                        int grid, int want_gram, cudaStream_t st) {
+  switch (r) {
+    case 1: k_update_gram<TB, TC, 1><<<grid, 256, 0, st>>>(W, n, win, h, partial, want_gram); break;
+    case 2: k_update_gram<TB, TC, 2><<<grid, 256, 0, st>>>(W, n, win, h, partial, want_gram); break;
+    case 3: k_update_gram<TB, TC, 3><<<grid, 256, 0, st>>>(W, n, win, h, partial, want_gram); break;
+    default: k_update_gram<TB, TC, 4><<<grid, 256, 0, st>>>(W, n, win, h, partial, want_gram); break;
+  }
+}
+
+void chol_small_launch(const double* partial, int nparts, int r, double* R, double* Rinv,
+                       uint32_t* flags, double rel_floor, cudaStream_t st) {
+  k_chol_small<<<1, 32, 0, st>>>(partial, nparts, r, R, Rinv, flags, rel_floor);
+}
+
+template <typename TC>
+void scale_gram_launch(TC* W, int64_t n, int r, const double* Rinv, double* partial, int grid,
+                       cudaStream_t st) {
+  switch (r) {
+    case 1: k_scale_gram<TC, 1><<<grid, 256, 0, st>>>(W, n, Rinv, partial); break;
+    case 2: k_scale_gram<TC, 2><<<grid, 256, 0, st>>>(W, n, Rinv, partial); break;
+    case 3: k_scale_gram<TC, 3><<<grid, 256, 0, st>>>(W, n, Rinv, partial); break;
+    default: k_scale_gram<TC, 4><<<grid, 256, 0, st>>>(W, n, Rinv, partial); break;
+  }
+}
+
+template <typename TB, typename TC>
+void scale_store_launch(const TC* W, int64_t n, int r, const double* Rinv, TB* dst,
+                        cudaStream_t st) {
+  const int grid = default_grid(n);
+  switch (r) {
+    case 1: k_scale_store<TB, TC, 1><<<grid, 256, 0, st>>>(W, n, Rinv, dst); break;
+    case 2: k_scale_store<TB, TC, 2><<<grid, 256, 0, st>>>(W, n, Rinv, dst); break;
+    case 3: k_scale_store<TB, TC, 3><<<grid, 256, 0, st>>>(W, n, Rinv, dst); break;
+    default: k_scale_store<TB, TC, 4><<<grid, 256, 0, st>>>(W, n, Rinv, dst); break;
+  }
+}
+
+template <typename TB>
+void x_accumulate_launch(double* X, int64_t n, int ell, int r, WindowPtrs blocks,
+                         const double* Wrows, int64_t ldw, cudaStream_t st) {
+  if (ell <= 0 || blocks.nwin <= 0) return;
+  k_x_accumulate<TB><<<default_grid(n * ell), 256, 0, st>>>(X, n, ell, r, blocks, Wrows, ldw);
+}
+
+void spmm_wide_launch(const int32_t* rowptr, const int32_t* col, const double* val, int64_t n,
+                      int w, const double* X, double* Y, cudaStream_t st) {
+  if (w <= 0 || n <= 0) return;
+  k_spmm_wide<<<default_grid(n * w), 256, 0, st>>>(rowptr, col, val, n, w, X, Y);
+}
+
+template <typename TV>
+void convert_values_launch(const double* src, TV* dst, int64_t count, cudaStream_t st) {
+  k_convert<TV><<<default_grid(count), 256, 0, st>>>(src, dst, count);
+}
+template <typename TB>
+void convert_block_launch(const double* src, TB* dst, int64_t count, cudaStream_t st) {
+  k_convert<TB><<<default_grid(count), 256, 0, st>>>(src, dst, count);
+}
+
+void combine_small_launch(const double* A, const double* B, double* C, int r, int mode,
+                          cudaStream_t st) {
+  k_combine_small<<<1, 32, 0, st>>>(A, B, C, r, mode);
+}
+
+// ---- explicit instantiations: FP64, mixed FP32, mixed BF16-basis
+#define SPK_INST(TB, TC, TV)                                                                     \
+  template void spmm_dots_launch<TB, TC, TV>(const int32_t*, const int32_t*, const TV*, int64_t, \
+                                             int, const TB*, TC*, WindowPtrs, double*, int,     \
+                                             cudaStream_t);                                     \
+  template void update_gram_launch<TB, TC>(TC*, int64_t, int, WindowPtrs, const double*,         \
+                                           double*, int, int, cudaStream_t);                    \
+  template void scale_store_launch<TB, TC>(const TC*, int64_t, int, const double*, TB*,          \
+                                           cudaStream_t);                                       \
+  template void x_accumulate_launch<TB>(double*, int64_t, int, int, WindowPtrs, const double*,  \
+                                        int64_t, cudaStream_t);                                 \
+  template void convert_block_launch<TB>(const double*, TB*, int64_t, cudaStream_t);
+SPK_INST(double, double, double)
+SPK_INST(float, float, float)
+SPK_INST(__nv_bfloat16, float, float)
+#undef SPK_INST
+template void scale_gram_launch<double>(double*, int64_t, int, const double*, double*, int,
+                                        cudaStream_t);
+template void scale_gram_launch<float>(float*, int64_t, int, const double*, double*, int,
+                                       cudaStream_t);
+template void convert_values_launch<float>(const double*, float*, int64_t, cudaStream_t);
+
+}  // namespace spk

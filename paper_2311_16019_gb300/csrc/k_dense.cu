@@ -1,0 +1,502 @@
+// Dense FP64 kernels for the projected problem (Eq. (3.4)) and the
+// low-rank truncation of its solution (Algorithm 1, after the loop).
+//
+//  gemm_f64     C = alpha op(A) op(B) + beta C, column-major, 64x64x16 tiles.
+//  gje_invert   in-place Gauss-Jordan inversion with partial pivoting
+//               (exchange/sweep form); one launch per pivot column, the CTA
+//               that owns column j+1 finds the next pivot right after
+//               updating it; log|det| accumulated in pivot order.
+//  sign_combine H <- (c H + H^{-1}/c)/2 and the size of the change.
+//  trsm         X <- T^{-1} X for upper-triangular T (column sweep).
+//  jacobi       one-sided Jacobi rotations on disjoint column pairs (SVD).
+// GB300 has no fast FP64 tensor path (its FP64 rate is the CUDA-core rate),
+// so these are CUDA-core FP64 kernels.
+#include "spk_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace spk {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm(int ta, int tb, int M, int N, int K, double alpha,
+                                              const double* __restrict__ A, int64_t lda,
+                                              const double* __restrict__ B, int64_t ldb,
+                                              double beta, double* __restrict__ C, int64_t ldc) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+      int i, kk;
+      if (!ta) { i = e % BM; kk = e / BM; } else { kk = e % BK; i = e / BK; }
+      const int gi = m0 + i, gk = k0 + kk;
+      double v = 0.0;
+      if (gi < M && gk < K) v = !ta ? A[gi + (int64_t)gk * lda] : A[gk + (int64_t)gi * lda];
+      As[kk][i] = v;
+    }
+    for (int e = threadIdx.x; e < BN * BK; e += 256) {
+      int j, kk;
+      if (!tb) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
+      const int gj = n0 + j, gk = k0 + kk;
+      double v = 0.0;
+      if (gj < N && gk < K) v = !tb ? B[gk + (int64_t)gj * ldb] : B[gj + (int64_t)gk * ldb];
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int gj = n0 + ty + 16 * j;
+    if (gj >= N) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int gi = m0 + tx + 16 * i;
+      if (gi >= M) continue;
+      double* c = C + gi + (int64_t)gj * ldc;
+      *c = (beta == 0.0) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
+    }
+  }
+}
+
+__global__ void k_copy_matrix(const double* __restrict__ A, int64_t lda, double* __restrict__ B,
+                              int64_t ldb, int M, int N) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / M, i = e - j * M;
+    B[i + j * ldb] = A[i + j * lda];
+  }
+}
+
+__global__ void k_set_zero(double* A, int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    A[e] = 0.0;
+}
+
+__global__ void k_scale_matrix(double* A, int64_t ld, int M, int N, double a) {
+  const int64_t total = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / M, i = e - j * M;
+    A[i + j * ld] *= a;
+  }
+}
+
+// ---- Gauss-Jordan inversion
+constexpr int kGjeCols = 8;     // columns per CTA
+constexpr int kGjeThreads = 256;
+
+// Block argmax of |A[i + col*ld]| over i in [j, m), ties to the smaller index.
+__device__ void block_argmax(const double* A, int64_t ld, int m, int j, int col, int* p_out,
+                             double* v_out) {
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  double best = -1.0;
+  int bidx = m;
+  for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+    const double v = fabs(A[i + (int64_t)col * ld]);
+    if (v > best || (v == best && i < bidx)) { best = v; bidx = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, best, o);
+    const int oi = __shfl_down_sync(0xffffffffu, bidx, o);
+    if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = -1.0;
+    int ix = m;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      if (bv[w] > b || (bv[w] == b && bi[w] < ix)) { b = bv[w]; ix = bi[w]; }
+    *p_out = ix;
+    *v_out = b;
+  }
+  __syncthreads();
+}
+
+// Pivot bookkeeping for column j (called by one CTA, after column j is current).
+__device__ void gje_prepare_pivot(double* A, int64_t ld, int m, int j, GjeState gs) {
+  __shared__ int sp;
+  __shared__ double sv;
+  block_argmax(A, ld, m, j, j, &sp, &sv);
+  const int p = sp;
+  double* c = gs.cvec + (int64_t)(j & 1) * m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    int src = i;
+    if (i == j) src = p; else if (i == p) src = j;
+    c[i] = A[src + (int64_t)j * ld];
+  }
+  if (threadIdx.x == 0) {
+    const double piv = A[p + (int64_t)j * ld];
+    gs.ipiv[j] = p;
+    gs.scal[2 + (j & 1)] = piv;
+    if (!(fabs(piv) > 1e-300) || !isfinite(piv)) atomicOr(gs.flags, kFlagZeroPivot);
+    gs.scal[0] += log(fabs(piv));
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kGjeThreads) k_gje_first(double* A, int64_t ld, int m, GjeState gs) {
+  if (threadIdx.x == 0) gs.scal[0] = 0.0;
+  __syncthreads();
+  gje_prepare_pivot(A, ld, m, 0, gs);
+}
+
+__global__ void __launch_bounds__(kGjeThreads) k_gje_step(double* A, int64_t ld, int m, int j, GjeState gs) {
+  const int p = gs.ipiv[j];
+  const double piv = gs.scal[2 + (j & 1)];
+  const double rpiv = 1.0 / piv;
+  const double* c = gs.cvec + (int64_t)(j & 1) * m;
+  const int l0 = blockIdx.x * kGjeCols;
+  const int l1 = min(m, l0 + kGjeCols);
+  for (int l = l0; l < l1; ++l) {
+    double* col = A + (int64_t)l * ld;
+    const double aj = col[p];   // row j after the swap
+    const double ap = col[j];   // row p after the swap
+    __syncthreads();
+    if (l == j) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] = (i == j) ? rpiv : -c[i] * rpiv;
+    } else {
+      const double f = aj * rpiv;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double v;
+        if (i == j) v = f;
+        else {
+          const double base = (i == p) ? ap : col[i];
+          v = fma(-c[i], f, base);
+        }
+        col[i] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (j + 1 < m && (j + 1) >= l0 && (j + 1) < l1) gje_prepare_pivot(A, ld, m, j + 1, gs);
+}
+
+// Undo the row exchanges: (P A)^{-1} = A^{-1} P^T, swap columns in reverse order.
+__global__ void k_gje_colperm(double* A, int64_t ld, int m, const int32_t* __restrict__ ipiv) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    for (int j = m - 1; j >= 0; --j) {
+      const int p = ipiv[j];
+      if (p != j) {
+        const double t = A[i + (int64_t)j * ld];
+        A[i + (int64_t)j * ld] = A[i + (int64_t)p * ld];
+        A[i + (int64_t)p * ld] = t;
+      }
+    }
+  }
+}
+
+__global__ void k_sign_combine(double* __restrict__ Hk, const double* __restrict__ Hinv,
+                               int64_t ld, int m, double c, double* __restrict__ partial) {
+  const int64_t total = (int64_t)m * m;
+  double d2 = 0.0, n2 = 0.0;
+  const double ic = 1.0 / c;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / m, i = e - j * m;
+    const int64_t o = i + j * ld;
+    const double h = Hk[o];
+    const double hn = 0.5 * (c * h + ic * Hinv[o]);
+    d2 += (hn - h) * (hn - h);
+    n2 += hn * hn;
+    Hk[o] = hn;
+  }
+  __shared__ double r1[32], r2[32];
+  d2 = warp_sum(d2);
+  n2 = warp_sum(n2);
+  if ((threadIdx.x & 31) == 0) { r1[threadIdx.x >> 5] = d2; r2[threadIdx.x >> 5] = n2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += r1[w]; b += r2[w]; }
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// X <- T^{-1} X, one CTA per right-hand side column.
+__global__ void k_trsm_upper_left(const double* __restrict__ T, int64_t ldT, int m, double* X,
+                                  int64_t ldX) {
+  double* x = X + (int64_t)blockIdx.x * ldX;
+  __shared__ double xi_s;
+  for (int i = m - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) {
+      const double xi = x[i] / T[i + (int64_t)i * ldT];
+      x[i] = xi;
+      xi_s = xi;
+    }
+    __syncthreads();
+    const double xi = xi_s;
+    const double* t = T + (int64_t)i * ldT;
+    for (int l = threadIdx.x; l < i; l += blockDim.x) x[l] = fma(-xi, t[l], x[l]);
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x0, uint64_t i) {
+  uint64_t z = x0 + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Standard normal entries by the Box-Muller transform of two uniforms.
+__global__ void k_gaussian(double* A, int64_t count, uint64_t seed) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double u1 = ((double)(mix64(seed, 2 * e) >> 11) + 1.0) * 0x1.0p-53;
+    const double u2 = (double)(mix64(seed, 2 * e + 1) >> 11) * 0x1.0p-53;
+    A[e] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_jacobi_pair(double* A, int64_t lda, int M, int N, double* V,
+                                                     int64_t ldv, const int* __restrict__ pairs,
+                                                     double* __restrict__ offs) {
+  const int p = pairs[2 * blockIdx.x], q = pairs[2 * blockIdx.x + 1];
+  if (p >= N || q >= N) {
+    if (threadIdx.x == 0) offs[blockIdx.x] = 0.0;
+    return;
+  }
+  double* ap = A + (int64_t)p * lda;
+  double* aq = A + (int64_t)q * lda;
+  double al = 0.0, be = 0.0, ga = 0.0;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const double x = ap[i], y = aq[i];
+    al = fma(x, x, al);
+    be = fma(y, y, be);
+    ga = fma(x, y, ga);
+  }
+  __shared__ double r[3][32];
+  __shared__ double cs_s, sn_s;
+  __shared__ int rot;
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga = warp_sum(ga);
+  if ((threadIdx.x & 31) == 0) {
+    r[0][threadIdx.x >> 5] = al;
+    r[1][threadIdx.x >> 5] = be;
+    r[2][threadIdx.x >> 5] = ga;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, g = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += r[0][w]; b += r[1][w]; g += r[2][w]; }
+    double off = 0.0;
+    rot = 0;
+    if (a > 0.0 && b > 0.0) off = fabs(g) / sqrt(a * b);
+    if (off > 1e-16 && g != 0.0) {
+      const double zeta = (b - a) / (2.0 * g);
+      const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      const double cs = 1.0 / sqrt(1.0 + t * t);
+      cs_s = cs;
+      sn_s = cs * t;
+      rot = 1;
+    }
+    offs[blockIdx.x] = off;
+  }
+  __syncthreads();
+  if (!rot) return;
+  const double cs = cs_s, sn = sn_s;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const double x = ap[i], y = aq[i];
+    ap[i] = cs * x - sn * y;
+    aq[i] = sn * x + cs * y;
+  }
+  if (V) {
+    double* vp = V + (int64_t)p * ldv;
+    double* vq = V + (int64_t)q * ldv;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const double x = vp[i], y = vq[i];
+      vp[i] = cs * x - sn * y;
+      vq[i] = sn * x + cs * y;
+    }
+  }
+}
+
+__global__ void k_col_norms(const double* __restrict__ A, int64_t lda, int M, double* out) {
+  const double* a = A + (int64_t)blockIdx.x * lda;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) s = fma(a[i], a[i], s);
+  __shared__ double r[32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) r[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += r[w];
+    out[blockIdx.x] = sqrt(t);
+  }
+}
+
+// Columns sorted by decreasing sigma (rank by counting; ties to the smaller
+// index), kept while sigma > tol * sigma_max.  Single CTA, N <= 4096.
+__global__ void k_select_sv(const double* __restrict__ sigma, int N, double tol, int* idx,
+                            double* f1, double* f2, int* ell_out) {
+  __shared__ double smax;
+  __shared__ int cnt;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int j = 0; j < N; ++j) m = fmax(m, sigma[j]);
+    smax = m;
+    cnt = 0;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const double sj = sigma[j];
+    if (!(sj > tol * smax) || !(smax > 0.0)) continue;
+    int rank = 0;
+    for (int o = 0; o < N; ++o) {
+      const double so = sigma[o];
+      rank += (so > sj) || (so == sj && o < j);
+    }
+    idx[rank] = j;
+    f1[rank] = sqrt(sj);
+    f2[rank] = 1.0 / sqrt(sj);
+    atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *ell_out = cnt;
+}
+
+__global__ void k_gather_cols(const double* __restrict__ A, int64_t lda, int M,
+                              const int* __restrict__ idx, const double* __restrict__ f, int ncols,
+                              double* __restrict__ out, int64_t ldo) {
+  const int64_t total = (int64_t)M * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e / M, i = e - t * M;
+    out[i + t * ldo] = A[i + (int64_t)idx[t] * lda] * f[t];
+  }
+}
+
+// scratch[0] = sum_{i,j} A[i + j n] B[j + i n]  = trace(A B), n x n column-major
+__global__ void k_trace_product(const double* __restrict__ A, const double* __restrict__ B, int n,
+                                double* out) {
+  double s = 0.0;
+  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
+    const int64_t j = e / n, i = e - j * n;
+    s = fma(A[i + j * n], B[j + i * n], s);
+  }
+  __shared__ double r[32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) r[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += r[w];
+    out[0] = t;
+  }
+}
+
+int grid_for(int64_t work, int block) {
+  int64_t g = (work + block - 1) / block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
+}
+
+}  // namespace
+
+void gemm_f64(char ta, char tb, int M, int N, int K, double alpha, const double* A, int64_t lda,
+              const double* B, int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  k_gemm<<<grid, 256, 0, st>>>(ta == 'T', tb == 'T', M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+void copy_matrix_launch(const double* A, int64_t lda, double* B, int64_t ldb, int M, int N,
+                        cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  k_copy_matrix<<<grid_for((int64_t)M * N, 256), 256, 0, st>>>(A, lda, B, ldb, M, N);
+}
+
+void set_zero_launch(double* A, int64_t count, cudaStream_t st) {
+  if (count <= 0) return;
+  k_set_zero<<<grid_for(count, 256), 256, 0, st>>>(A, count);
+}
+
+void scale_matrix_launch(double* A, int64_t ld, int M, int N, double a, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  k_scale_matrix<<<grid_for((int64_t)M * N, 256), 256, 0, st>>>(A, ld, M, N, a);
+}
+
+void gje_invert(double* A, int64_t lda, int m, GjeState gs, cudaStream_t st) {
+  if (m <= 0) return;
+  k_gje_first<<<1, kGjeThreads, 0, st>>>(A, lda, m, gs);
+  const int blocks = (m + kGjeCols - 1) / kGjeCols;
+  for (int j = 0; j < m; ++j) k_gje_step<<<blocks, kGjeThreads, 0, st>>>(A, lda, m, j, gs);
+  k_gje_colperm<<<grid_for(m, 128), 128, 0, st>>>(A, lda, m, gs.ipiv);
+}
+
+int sign_combine_grid(int m) { return grid_for((int64_t)m * m, 256) > 304 ? 304 : grid_for((int64_t)m * m, 256); }
+
+void sign_combine_launch(double* Hk, const double* Hinv, int64_t ld, int m, double c,
+                         double* partial, int grid, cudaStream_t st) {
+  k_sign_combine<<<grid, 256, 0, st>>>(Hk, Hinv, ld, m, c, partial);
+}
+
+void trsm_upper_left_launch(const double* T, int64_t ldT, int m, double* X, int64_t ldX, int ncol,
+                            cudaStream_t st) {
+  if (ncol <= 0 || m <= 0) return;
+  k_trsm_upper_left<<<ncol, 256, 0, st>>>(T, ldT, m, X, ldX);
+}
+
+void gaussian_fill_launch(double* A, int64_t count, uint64_t seed, cudaStream_t st) {
+  k_gaussian<<<grid_for(count, 256), 256, 0, st>>>(A, count, seed);
+}
+
+void jacobi_round_launch(double* A, int64_t lda, int M, int N, double* V, int64_t ldv,
+                         const int* pairs, int npairs, double* offs, cudaStream_t st) {
+  k_jacobi_pair<<<npairs, 256, 0, st>>>(A, lda, M, N, V, ldv, pairs, offs);
+}
+
+void col_norms_launch(const double* A, int64_t lda, int M, int N, double* out, cudaStream_t st) {
+  if (N <= 0) return;
+  k_col_norms<<<N, 256, 0, st>>>(A, lda, M, out);
+}
+
+void select_sv_launch(const double* sigma, int N, double tol, int* idx, double* f1, double* f2,
+                      int* ell_out, cudaStream_t st) {
+  k_select_sv<<<1, 256, 0, st>>>(sigma, N, tol, idx, f1, f2, ell_out);
+}
+
+void gather_cols_launch(const double* A, int64_t lda, int M, const int* idx, const double* f,
+                        int ncols, double* out, int64_t ldo, cudaStream_t st) {
+  if (ncols <= 0 || M <= 0) return;
+  k_gather_cols<<<grid_for((int64_t)M * ncols, 256), 256, 0, st>>>(A, lda, M, idx, f, ncols, out, ldo);
+}
+
+double trace_product(const double* A, const double* B, int n, double* scratch, cudaStream_t st) {
+  k_trace_product<<<1, 256, 0, st>>>(A, B, n, scratch);
+  double h = 0.0;
+  cudaMemcpyAsync(&h, scratch, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  return h;
+}
+
+}  // namespace spk

@@ -1,0 +1,255 @@
+// Projected matrices and the residual estimate (Eq. (2.5), Section 5, Eq. (3.5)).
+//
+// H~_d = Hhat_d + Hhat E_d^T with Hhat_d = T_d H_d T_d^{-1} and
+// Hhat = T_H h_{d+1,d} tau_d^{-1} is kept up to date by the bordering update of
+// Section 5: from H~_{d-1} and the new columns of T and H,
+//   (1,2) block = (-H~_{d-1} T_H + T_{d-1} H_col + T_H h_{d,d}) tau_d^{-1}
+//   (2,1) block = tau_d h_{d,d-1} tau_{d-1}^{-1}            (last block column)
+//   (2,2) block = tau_d (h_{d,d} - h_{d,d-1} tau_{d-1}^{-1} E^T T_H) tau_d^{-1}
+// (T_H = T[0:(d-1)r, (d-1)r:dr], tau_d its diagonal block; the last term of
+// the (1,2) block carries tau_d^{-1} -- direct expansion of T H T^{-1}), then
+// the correction H~_d = Hhat_d + T_H' h_{d+1,d} tau_d^{-1} E_d^T is added with
+// the newest column T_H' of T_{d+1}.
+// rho (Eq. (3.5)) uses the whitened subdiagonals
+//   hhat = tau_{d+1} h_{d+1,d} tau_d^{-1},  ghat = theta_{d+1} g_{d+1,d} theta_d^{-1}.
+#include "spk_internal.cuh"
+
+#include <algorithm>
+
+namespace spk {
+
+namespace {
+
+__host__ __device__ void upper_inv(const double* T, int64_t ldT, int off, int r, double* Ri) {
+  // Ri (r x r row-major) = inverse of the upper-triangular block T[off.., off..]
+  for (int e = 0; e < r * r; ++e) Ri[e] = 0.0;
+  for (int j = 0; j < r; ++j) {
+    Ri[j * r + j] = 1.0 / T[off + j + (int64_t)(off + j) * ldT];
+    for (int i = j - 1; i >= 0; --i) {
+      double t = 0.0;
+      for (int l = i + 1; l <= j; ++l) t += T[off + i + (int64_t)(off + l) * ldT] * Ri[l * r + j];
+      Ri[i * r + j] = -t / T[off + i + (int64_t)(off + i) * ldT];
+    }
+  }
+}
+
+__host__ __device__ void tblock(const double* T, int64_t ldT, int off, int r, double* B) {
+  for (int a = 0; a < r; ++a)
+    for (int c = 0; c < r; ++c) B[a * r + c] = T[off + a + (int64_t)(off + c) * ldT];
+}
+
+__host__ __device__ void mm(const double* A, const double* B, double* C, int r) {
+  double o[kMaxR * kMaxR];
+  for (int a = 0; a < r; ++a)
+    for (int c = 0; c < r; ++c) {
+      double s = 0.0;
+      for (int l = 0; l < r; ++l) s += A[a * r + l] * B[l * r + c];
+      o[a * r + c] = s;
+    }
+  for (int e = 0; e < r * r; ++e) C[e] = o[e];
+}
+
+// Rows i < mp of the new block column of H~.
+__global__ void k_border_col(double* __restrict__ Ht, int64_t ldH, int mp, int r,
+                             const double* __restrict__ T, int64_t ldT,
+                             const double* __restrict__ hslots, int first_block, int nslots,
+                             const double* __restrict__ h_dd) {
+  __shared__ double tinv[kMaxR * kMaxR];
+  __shared__ double hdd[kMaxR * kMaxR];
+  if (threadIdx.x == 0) upper_inv(T, ldT, mp, r, tinv);
+  if (threadIdx.x < r * r) hdd[threadIdx.x] = h_dd[threadIdx.x];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= mp) return;
+  double v[kMaxR] = {0, 0, 0, 0};
+  // -H~_{d-1} T_H
+  for (int l = 0; l < mp; ++l) {
+    const double h = Ht[i + (int64_t)l * ldH];
+    for (int c = 0; c < r; ++c) v[c] -= h * T[l + (int64_t)(mp + c) * ldT];
+  }
+  // + T_{d-1} H_col (band of blocks first_block .. first_block+nslots-1)
+  for (int q = 0; q < nslots; ++q) {
+    const int b = first_block + q;  // 1-based block index
+    for (int a = 0; a < r; ++a) {
+      const int l = (b - 1) * r + a;
+      const double t = T[i + (int64_t)l * ldT];
+      for (int c = 0; c < r; ++c) v[c] += t * hslots[(q * r + a) * r + c];
+    }
+  }
+  // + T_H h_{d,d}
+  for (int a = 0; a < r; ++a) {
+    const double t = T[i + (int64_t)(mp + a) * ldT];
+    for (int c = 0; c < r; ++c) v[c] += t * hdd[a * r + c];
+  }
+  for (int c = 0; c < r; ++c) {
+    double s = 0.0;
+    for (int a = 0; a <= c; ++a) s += v[a] * tinv[a * r + c];
+    Ht[i + (int64_t)(mp + c) * ldH] = s;
+  }
+}
+
+}  // namespace
+
+// Rows mp..mp+r of H~ (the (2,1) and (2,2) blocks of the bordering update).
+__host__ __device__ void border_small_body(double* Ht, int64_t ldH, int mp, int r, const double* T,
+                                           int64_t ldT, const double* h_sub, const double* h_dd) {
+  double tau[kMaxR * kMaxR], tinv[kMaxR * kMaxR], X[kMaxR * kMaxR], Y[kMaxR * kMaxR];
+  tblock(T, ldT, mp, r, tau);
+  upper_inv(T, ldT, mp, r, tinv);
+  if (mp == 0) {
+    mm(tau, h_dd, X, r);
+    mm(X, tinv, Y, r);
+    for (int a = 0; a < r; ++a)
+      for (int c = 0; c < r; ++c) Ht[a + (int64_t)c * ldH] = Y[a * r + c];
+    return;
+  }
+  double tpinv[kMaxR * kMaxR];
+  upper_inv(T, ldT, mp - r, r, tpinv);
+  // (2,1): tau_d h_{d,d-1} tau_{d-1}^{-1}
+  double hs_tp[kMaxR * kMaxR];
+  mm(h_sub, tpinv, hs_tp, r);
+  mm(tau, hs_tp, X, r);
+  for (int a = 0; a < r; ++a)
+    for (int c = 0; c < r; ++c) Ht[mp + a + (int64_t)(mp - r + c) * ldH] = X[a * r + c];
+  // (2,2): tau_d (h_{d,d} - h_{d,d-1} tau_{d-1}^{-1} E^T T_H) tau_d^{-1}
+  double ET[kMaxR * kMaxR];
+  for (int a = 0; a < r; ++a)
+    for (int c = 0; c < r; ++c) ET[a * r + c] = T[mp - r + a + (int64_t)(mp + c) * ldT];
+  mm(hs_tp, ET, X, r);
+  for (int e = 0; e < r * r; ++e) X[e] = h_dd[e] - X[e];
+  mm(tau, X, Y, r);
+  mm(Y, tinv, X, r);
+  for (int a = 0; a < r; ++a)
+    for (int c = 0; c < r; ++c) Ht[mp + a + (int64_t)(mp + c) * ldH] = X[a * r + c];
+}
+
+namespace {
+
+__global__ void k_border_small(double* __restrict__ Ht, int64_t ldH, int mp, int r,
+                               const double* __restrict__ T, int64_t ldT,
+                               const double* __restrict__ h_sub, const double* __restrict__ h_dd) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  border_small_body(Ht, ldH, mp, r, T, ldT, h_sub, h_dd);
+}
+
+// H~[:, m-r:m] += T[:, m:m+r] h_{d+1,d} tau_d^{-1}  (rows < m)
+__global__ void k_border_correct(double* __restrict__ Ht, int64_t ldH, int m, int r,
+                                 const double* __restrict__ T, int64_t ldT,
+                                 const double* __restrict__ h_next) {
+  __shared__ double K[kMaxR * kMaxR];
+  if (threadIdx.x == 0) {
+    double tinv[kMaxR * kMaxR];
+    upper_inv(T, ldT, m - r, r, tinv);
+    mm(h_next, tinv, K, r);
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double v[kMaxR];
+  for (int a = 0; a < r; ++a) v[a] = T[i + (int64_t)(m + a) * ldT];
+  for (int c = 0; c < r; ++c) {
+    double s = 0.0;
+    for (int a = 0; a < r; ++a) s += v[a] * K[a * r + c];
+    Ht[i + (int64_t)(m - r + c) * ldH] += s;
+  }
+}
+
+// out3 = {rho, rho/||beta_U beta_V^T||_F, ||beta_U beta_V^T||_F}
+__global__ void k_rho(const double* __restrict__ Y, int64_t ldY, int m, int r,
+                      const double* __restrict__ TU, int64_t ldTU, const double* __restrict__ TV,
+                      int64_t ldTV, const double* __restrict__ hU, const double* __restrict__ hV,
+                      const double* __restrict__ bU, const double* __restrict__ bV,
+                      double* __restrict__ out3) {
+  __shared__ double hh[kMaxR * kMaxR], gh[kMaxR * kMaxR];
+  __shared__ double red[32];
+  __shared__ double nb;
+  if (threadIdx.x == 0) {
+    double tau[kMaxR * kMaxR], tinv[kMaxR * kMaxR], X[kMaxR * kMaxR];
+    tblock(TU, ldTU, m, r, tau);
+    upper_inv(TU, ldTU, m - r, r, tinv);
+    mm(tau, hU, X, r);
+    mm(X, tinv, hh, r);
+    tblock(TV, ldTV, m, r, tau);
+    upper_inv(TV, ldTV, m - r, r, tinv);
+    mm(tau, hV, X, r);
+    mm(X, tinv, gh, r);
+    double s = 0.0;
+    for (int a = 0; a < r; ++a)
+      for (int b = 0; b < r; ++b) {
+        double f = 0.0;
+        for (int l = 0; l < r; ++l) f += bU[a * r + l] * bV[b * r + l];
+        s += f * f;
+      }
+    nb = sqrt(s);
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    // row block: (hhat Y[m-r:m, j])_a
+    for (int a = 0; a < r; ++a) {
+      double s = 0.0;
+      for (int b = 0; b < r; ++b) s += hh[a * r + b] * Y[m - r + b + (int64_t)j * ldY];
+      acc += s * s;
+    }
+    // column block: (Y[j, m-r:m] ghat^T)_a
+    for (int a = 0; a < r; ++a) {
+      double s = 0.0;
+      for (int b = 0; b < r; ++b) s += Y[j + (int64_t)(m - r + b) * ldY] * gh[a * r + b];
+      acc += s * s;
+    }
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    const double rho = sqrt(s);
+    out3[0] = rho;
+    out3[1] = rho / nb;
+    out3[2] = nb;
+  }
+}
+
+__global__ void k_fill_rhs(double* F, int64_t ldF, int r, const double* bU, const double* bV) {
+  const int e = threadIdx.x;
+  if (e >= r * r) return;
+  const int a = e / r, b = e - a * r;
+  double s = 0.0;
+  for (int l = 0; l < r; ++l) s += bU[a * r + l] * bV[b * r + l];
+  F[a + (int64_t)b * ldF] = s;
+}
+
+}  // namespace
+
+void border_col_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, int64_t ldT,
+                       const double* hslots, int first_block, int nslots, const double* h_dd,
+                       cudaStream_t st) {
+  if (mp <= 0) return;
+  k_border_col<<<(mp + 127) / 128, 128, 0, st>>>(Ht, ldH, mp, r, T, ldT, hslots, first_block,
+                                                 nslots, h_dd);
+}
+
+void border_small_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, int64_t ldT,
+                         const double* h_sub, const double* h_dd, cudaStream_t st) {
+  k_border_small<<<1, 32, 0, st>>>(Ht, ldH, mp, r, T, ldT, h_sub, h_dd);
+}
+
+void border_correct_launch(double* Ht, int64_t ldH, int m, int r, const double* T, int64_t ldT,
+                           const double* h_next, cudaStream_t st) {
+  k_border_correct<<<(m + 127) / 128, 128, 0, st>>>(Ht, ldH, m, r, T, ldT, h_next);
+}
+
+void rho_launch(const double* Y, int64_t ldY, int m, int r, const double* TU, int64_t ldTU,
+                const double* TV, int64_t ldTV, const double* hU, const double* hV,
+                const double* betaU, const double* betaV, double* out3, cudaStream_t st) {
+  k_rho<<<1, 256, 0, st>>>(Y, ldY, m, r, TU, ldTU, TV, ldTV, hU, hV, betaU, betaV, out3);
+}
+
+void fill_rhs_launch(double* F, int64_t ldF, int m, int r, const double* betaU,
+                     const double* betaV, cudaStream_t st) {
+  (void)m;
+  k_fill_rhs<<<1, 32, 0, st>>>(F, ldF, r, betaU, betaV);
+}
+
+}  // namespace spk

@@ -1,0 +1,240 @@
+// Whitening QR update (Proposition 2.1; Algorithm 1's sketched-basis QR).
+//
+// Given Q_d (s x dr, orthonormal columns, FP64 column-major) and the sketch
+// w = S U_{d+1} (s x r), block classical Gram-Schmidt with one
+// reorthogonalisation:
+//     t1 = Q_d^T w,  w1 = w - Q_d t1,  t2 = Q_d^T w1,  w2 = w1 - Q_d t2,
+//     Q_new tau_{d+1} = w2  (Cholesky QR applied twice),
+//     T_{d+1} = [[T_d, t1 + t2], [0, tau_{d+1}]].
+// All FP64 (also in the mixed forms).  Every reduction has a fixed order.
+#include "spk_internal.cuh"
+
+#include <algorithm>
+
+namespace spk {
+
+namespace {
+
+// t[j*r + c] = sum_i Q[i + j*ldq] * w[i + c*s]; one warp per column j.
+template <int R>
+__global__ void __launch_bounds__(256) k_qt_dot(const double* __restrict__ Q, int64_t ldq, int64_t s,
+                                                int m, const double* __restrict__ w,
+                                                double* __restrict__ t) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= m) return;
+  const double* q = Q + (int64_t)warp * ldq;
+  double acc[R];
+#pragma unroll
+  for (int c = 0; c < R; ++c) acc[c] = 0.0;
+  for (int64_t i = lane; i < s; i += 32) {
+    const double qi = q[i];
+#pragma unroll
+    for (int c = 0; c < R; ++c) acc[c] = fma(qi, w[i + c * s], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < R; ++c) {
+    const double v = warp_sum(acc[c]);
+    if (lane == 0) t[(int64_t)warp * R + c] = v;
+  }
+}
+
+constexpr int kRowTile = 256;
+constexpr int kColChunk = 256;
+
+// partial[(chunk*s + i)*r + c] = sum_{j in chunk} Q[i + j*ldq] * t[j*r + c]
+template <int R>
+__global__ void __launch_bounds__(kRowTile) k_q_times_t(const double* __restrict__ Q, int64_t ldq,
+                                                        int64_t s, int m,
+                                                        const double* __restrict__ t,
+                                                        double* __restrict__ partial) {
+  __shared__ double ts[kColChunk * R];
+  const int chunk = blockIdx.y;
+  const int j0 = chunk * kColChunk;
+  const int j1 = min(m, j0 + kColChunk);
+  for (int e = threadIdx.x; e < (j1 - j0) * R; e += blockDim.x) ts[e] = t[(int64_t)j0 * R + e];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * kRowTile + threadIdx.x;
+  if (i >= s) return;
+  double acc[R];
+#pragma unroll
+  for (int c = 0; c < R; ++c) acc[c] = 0.0;
+  const double* q = Q + i + (int64_t)j0 * ldq;
+  for (int j = 0; j < j1 - j0; ++j) {
+    const double qi = q[(int64_t)j * ldq];
+#pragma unroll
+    for (int c = 0; c < R; ++c) acc[c] = fma(qi, ts[j * R + c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < R; ++c) partial[((int64_t)chunk * s + i) * R + c] = acc[c];
+}
+
+// w_out[i + c*s] = w_in[i + c*s] - sum_chunk partial[chunk][i][c]
+template <int R>
+__global__ void k_q_update_finish(const double* __restrict__ w_in, double* __restrict__ w_out,
+                                  const double* __restrict__ partial, int64_t s, int nchunk) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s;
+       i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      double acc = 0.0;
+      for (int ch = 0; ch < nchunk; ++ch) acc += partial[((int64_t)ch * s + i) * R + c];
+      w_out[i + c * s] = w_in[i + c * s] - acc;
+    }
+  }
+}
+
+template <int NV>
+__device__ void block_reduce_store(double (&acc)[NV], double* out) {
+  __shared__ double red[32][NV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int e = 0; e < NV; ++e) {
+    double v = warp_sum(acc[e]);
+    if (lane == 0) red[wid][e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NV; e += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w][e];
+    out[e] = s;
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_ts_gram(const double* __restrict__ w, int64_t s,
+                                                 double* __restrict__ partial) {
+  double acc[R * R];
+#pragma unroll
+  for (int e = 0; e < R * R; ++e) acc[e] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) v[c] = w[i + c * s];
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) acc[a * R + b] = fma(v[a], v[b], acc[a * R + b]);
+  }
+  block_reduce_store<R * R>(acc, partial + (int64_t)blockIdx.x * R * R);
+}
+
+// out[i + c*ldo] = sum_{a<=c} w[i + a*s] Rinv[a][c]   (w may alias out when ldo == s)
+template <int R>
+__global__ void k_ts_scale(const double* w, int64_t s, const double* __restrict__ Rinv,
+                           double* out, int64_t ldo) {
+  __shared__ double ri[R * R];
+  if (threadIdx.x < R * R) ri[threadIdx.x] = Rinv[threadIdx.x];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < s;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v[R], o[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) v[c] = w[i + c * s];
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      double acc = 0.0;
+#pragma unroll
+      for (int a = 0; a <= c; ++a) acc = fma(v[a], ri[a * R + c], acc);
+      o[c] = acc;
+    }
+#pragma unroll
+    for (int c = 0; c < R; ++c) out[i + c * ldo] = o[c];
+  }
+}
+
+__global__ void k_t_write(double* __restrict__ T, int64_t ldT, int m, int r,
+                          const double* __restrict__ t1, const double* __restrict__ t2,
+                          const double* __restrict__ tau) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (m + r) * r; e += gridDim.x * blockDim.x) {
+    const int j = e / r, c = e - j * r;
+    double v;
+    if (j < m) {
+      v = t1 ? t1[(int64_t)j * r + c] : 0.0;
+      if (t2) v += t2[(int64_t)j * r + c];
+    } else {
+      const int a = j - m;
+      v = (a <= c) ? tau[a * r + c] : 0.0;
+    }
+    T[j + (int64_t)(m + c) * ldT] = v;
+  }
+}
+
+int grid_for(int64_t work, int block) {
+  int64_t g = (work + block - 1) / block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 4));
+}
+
+}  // namespace
+
+void qt_dot_launch(const double* Q, int64_t ldq, int64_t s, int m, const double* w, int r,
+                   double* t, cudaStream_t st) {
+  if (m <= 0) return;
+  const int blocks = (m + 7) / 8;
+  switch (r) {
+    case 1: k_qt_dot<1><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
+    case 2: k_qt_dot<2><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
+    case 3: k_qt_dot<3><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
+    default: k_qt_dot<4><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
+  }
+}
+
+void q_update_launch(const double* Q, int64_t ldq, int64_t s, int m, const double* t, int r,
+                     const double* w_in, double* w_out, double* partial, int nchunk,
+                     cudaStream_t st) {
+  if (m <= 0) {
+    cudaMemcpyAsync(w_out, w_in, sizeof(double) * s * r, cudaMemcpyDeviceToDevice, st);
+    return;
+  }
+  dim3 grid((unsigned)((s + kRowTile - 1) / kRowTile), (unsigned)nchunk);
+  const int g2 = grid_for(s, 256);
+  switch (r) {
+    case 1:
+      k_q_times_t<1><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, t, partial);
+      k_q_update_finish<1><<<g2, 256, 0, st>>>(w_in, w_out, partial, s, nchunk);
+      break;
+    case 2:
+      k_q_times_t<2><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, t, partial);
+      k_q_update_finish<2><<<g2, 256, 0, st>>>(w_in, w_out, partial, s, nchunk);
+      break;
+    case 3:
+      k_q_times_t<3><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, t, partial);
+      k_q_update_finish<3><<<g2, 256, 0, st>>>(w_in, w_out, partial, s, nchunk);
+      break;
+    default:
+      k_q_times_t<4><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, t, partial);
+      k_q_update_finish<4><<<g2, 256, 0, st>>>(w_in, w_out, partial, s, nchunk);
+      break;
+  }
+}
+
+int q_update_chunks(int m) { return std::max(1, (m + kColChunk - 1) / kColChunk); }
+
+void ts_gram_launch(const double* w, int64_t s, int r, double* partial, int grid, cudaStream_t st) {
+  switch (r) {
+    case 1: k_ts_gram<1><<<grid, 256, 0, st>>>(w, s, partial); break;
+    case 2: k_ts_gram<2><<<grid, 256, 0, st>>>(w, s, partial); break;
+    case 3: k_ts_gram<3><<<grid, 256, 0, st>>>(w, s, partial); break;
+    default: k_ts_gram<4><<<grid, 256, 0, st>>>(w, s, partial); break;
+  }
+}
+
+void ts_scale_launch(double* w, int64_t s, int r, const double* Rinv, double* out, int64_t ldo,
+                     cudaStream_t st) {
+  const int g = grid_for(s, 256);
+  switch (r) {
+    case 1: k_ts_scale<1><<<g, 256, 0, st>>>(w, s, Rinv, out, ldo); break;
+    case 2: k_ts_scale<2><<<g, 256, 0, st>>>(w, s, Rinv, out, ldo); break;
+    case 3: k_ts_scale<3><<<g, 256, 0, st>>>(w, s, Rinv, out, ldo); break;
+    default: k_ts_scale<4><<<g, 256, 0, st>>>(w, s, Rinv, out, ldo); break;
+  }
+}
+
+void t_write_launch(double* T, int64_t ldT, int m, int r, const double* t1, const double* t2,
+                    const double* tau, cudaStream_t st) {
+  k_t_write<<<grid_for((int64_t)(m + r) * r, 256), 256, 0, st>>>(T, ldT, m, r, t1, t2, tau);
+}
+
+}  // namespace spk

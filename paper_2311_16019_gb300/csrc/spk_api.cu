@@ -1,0 +1,1091 @@
+// libspk C ABI: handle, workspace and the device-side driver of Algorithm 1
+// (s-PKSM) of the paper.  Every arithmetic step runs in this library's
+// kernels; the host only sequences launches, reads back the residual
+// estimate at check iterations, and sizes buffers.
+//
+// One iteration d, for each side (A, U) and (B^T, V):
+//   spmm + window dots -> reduce -> GS update + Gram -> Cholesky (R1)
+//   -> scale + Gram -> Cholesky (R2) -> h_{d+1,d} = R2 R1 -> U_{d+1}
+//   -> sketch S U_{d+1} -> whitening CGS2 against Q -> Cholesky QR (tau)
+//   -> T column block -> bordering update of H~ (Section 5).
+// At a check: sign-function solve of H~ Y + Y G~^T = E1 b1 b2^T E1^T (Eq. (3.4)),
+// rho (Eq. (3.5)).  After the loop: SVD truncation of Y, W = T^{-1} Y_i,
+// second Arnoldi sweep accumulating X1 = U_d W1, X2 = V_d W2.
+#include "spk_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <ctime>
+#include <map>
+#include <string>
+#include <vector>
+
+using namespace spk;
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct spk_handle {
+  int device = 0;
+  int sm_count = 152;
+  std::string err;
+  std::map<std::string, Buf> bufs;
+  uint32_t* flags = nullptr;
+  double host_wait_s = 600.0;
+};
+
+namespace {
+
+int fail(spk_handle* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(h, SPK_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                    \
+  } while (0)
+
+#define TRY(expr)            \
+  do {                       \
+    int rc_ = (expr);        \
+    if (rc_ != SPK_OK) return rc_; \
+  } while (0)
+
+void* ws_get(spk_handle* h, const std::string& name, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~size_t(255);
+  Buf& b = h->bufs[name];
+  if (b.bytes >= bytes) return b.p;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return nullptr;
+  }
+  b.bytes = bytes;
+  return b.p;
+}
+
+#define WS(var, type, name, count)                                                           \
+  type* var = static_cast<type*>(ws_get(h, name, sizeof(type) * (size_t)(count)));           \
+  if (!var) return fail(h, SPK_ERR_ALLOC, "cannot allocate %s (%zu bytes)", name,            \
+                        sizeof(type) * (size_t)(count));
+
+// Bounded wait on a stream: poll with a wall-clock budget (never blocks forever).
+int wait_stream(spk_handle* h, cudaStream_t st, double budget_s) {
+  if (budget_s <= 0.0) {
+    // zero budget (fault injection): report the expired wait; queued work
+    // completes in stream order and the context stays usable
+    (void)cudaStreamQuery(st);
+    return fail(h, SPK_ERR_TIMEOUT, "bounded wait with a zero budget expired");
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(st);
+    if (e == cudaSuccess) return SPK_OK;
+    if (e != cudaErrorNotReady)
+      return fail(h, SPK_ERR_CUDA, "stream error: %s", cudaGetErrorString(e));
+    const double el =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el >= budget_s) return fail(h, SPK_ERR_TIMEOUT, "device work did not finish in %.1f s", budget_s);
+    if (el > 1e-3) {
+      struct timespec ts{0, 50000};
+      nanosleep(&ts, nullptr);
+    }
+  }
+}
+
+int read_flags(spk_handle* h, cudaStream_t st, uint32_t* out) {
+  CK(cudaMemcpyAsync(out, h->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  TRY(wait_stream(h, st, h->host_wait_s));
+  return SPK_OK;
+}
+
+int flags_to_status(spk_handle* h, uint32_t f) {
+  if (f & kFlagNonfinite) return fail(h, SPK_ERR_NONFINITE, "non-finite value in a reduction");
+  if (f & kFlagBreakdown)
+    return fail(h, SPK_ERR_BREAKDOWN, "rank-deficient block in a Cholesky QR (Gram pivot <= 1e-14 trace)");
+  if (f & kFlagZeroPivot)
+    return fail(h, SPK_ERR_SINGULAR_PROJECTED, "zero pivot in the projected-matrix inversion");
+  return SPK_OK;
+}
+
+// A new block whose Gram matrix has a Cholesky pivot below 1e-14 of its
+// trace (condition number above ~1e7) is reported as a breakdown.
+constexpr double kBreakdownFloor = 1e-14;
+
+int grid_rows(spk_handle* h, int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)h->sm_count * 4));
+}
+
+// --------------------------------------------------------------------------
+// Small dense Sylvester solve H Y + Y G^T = F by the scaled Newton iteration
+// for the matrix sign function of [[H, -F], [0, -G^T]]:
+//   H <- (c H + H^{-1}/c)/2,  G <- (c G + G^{-1}/c)/2,
+//   F <- (c F + H^{-1} F G^{-T} / c)/2,    Y = F_inf / 2,
+// c = |det H det G|^{-1/(2m)} while far from convergence, else 1.
+// Requires the spectra of H and G in the open right half plane (true for
+// the convection-diffusion operators here); a zero pivot is reported.
+// In: Hk, Gk, F (m x m, ld m, overwritten); out: F holds Y.
+int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_newton,
+               cudaStream_t st, int* iters_out) {
+  WS(Hinv, double, "sg_Hinv", (size_t)m * m);
+  WS(Ginv, double, "sg_Ginv", (size_t)m * m);
+  WS(P, double, "sg_P", (size_t)m * m);
+  WS(ipiv, int32_t, "sg_ipiv", m);
+  WS(cvec, double, "sg_cvec", 2 * (size_t)m);
+  WS(scalH, double, "sg_scalH", 8);
+  WS(scalG, double, "sg_scalG", 8);
+  const int sgrid = sign_combine_grid(m);
+  WS(part, double, "sg_part", 4 * (size_t)sgrid);
+  std::vector<double> hpart(4 * (size_t)sgrid);
+  double delta_prev = 1e300;
+  int it = 0;
+  for (it = 0; it < max_newton; ++it) {
+    CK(cudaMemcpyAsync(Hinv, Hk, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(Ginv, Gk, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
+    GjeState gh{ipiv, cvec, scalH, h->flags};
+    gje_invert(Hinv, m, m, gh, st);
+    GjeState gg{ipiv, cvec, scalG, h->flags};
+    gje_invert(Ginv, m, m, gg, st);
+    double ld[2] = {0, 0};
+    CK(cudaMemcpyAsync(&ld[0], scalH, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&ld[1], scalG, sizeof(double), cudaMemcpyDeviceToHost, st));
+    TRY(wait_stream(h, st, h->host_wait_s));
+    CK(cudaGetLastError());
+    uint32_t f = 0;
+    TRY(read_flags(h, st, &f));
+    if (f & kFlagZeroPivot) {
+      *iters_out = it;
+      return fail(h, SPK_ERR_SINGULAR_PROJECTED, "zero pivot in sign iteration %d (m=%d)", it, m);
+    }
+    double c = 1.0;
+    if (delta_prev > 1e-2) {
+      c = std::exp(-(ld[0] + ld[1]) / (2.0 * m));
+      if (!std::isfinite(c) || c <= 0.0) c = 1.0;
+    }
+    // F <- (c/2) F + (1/(2c)) (H^{-1} F) G^{-T}
+    gemm_f64('N', 'N', m, m, m, 1.0, Hinv, m, F, m, 0.0, P, m, st);
+    gemm_f64('N', 'T', m, m, m, 0.5 / c, P, m, Ginv, m, 0.5 * c, F, m, st);
+    sign_combine_launch(Hk, Hinv, m, m, c, part, sgrid, st);
+    sign_combine_launch(Gk, Ginv, m, m, c, part + 2 * sgrid, sgrid, st);
+    CK(cudaMemcpyAsync(hpart.data(), part, sizeof(double) * 4 * sgrid, cudaMemcpyDeviceToHost, st));
+    TRY(wait_stream(h, st, h->host_wait_s));
+    double dH = 0, nH = 0, dG = 0, nG = 0;
+    for (int b = 0; b < sgrid; ++b) {
+      dH += hpart[2 * b];
+      nH += hpart[2 * b + 1];
+      dG += hpart[2 * sgrid + 2 * b];
+      nG += hpart[2 * sgrid + 2 * b + 1];
+    }
+    const double delta = std::sqrt(dH / std::max(nH, 1e-300)) + std::sqrt(dG / std::max(nG, 1e-300));
+    if (!std::isfinite(delta)) {
+      *iters_out = it + 1;
+      return fail(h, SPK_ERR_NONFINITE, "non-finite sign iteration (m=%d)", m);
+    }
+    if (delta < 1e-11 || (delta < 1e-6 && delta > 0.5 * delta_prev)) {
+      ++it;
+      break;
+    }
+    delta_prev = delta;
+  }
+  *iters_out = it;
+  scale_matrix_launch(F, m, m, m, 0.5, st);
+  return SPK_OK;
+}
+
+// Round-robin pairing of N (even) columns for one Jacobi sweep: rounds x pairs.
+void jacobi_schedule(int N, std::vector<int>& pairs, int& rounds, int& npairs) {
+  const int Ne = N + (N & 1);
+  rounds = Ne - 1;
+  npairs = Ne / 2;
+  pairs.assign((size_t)rounds * npairs * 2, 0);
+  std::vector<int> ring(Ne);
+  for (int i = 0; i < Ne; ++i) ring[i] = i;
+  for (int rd = 0; rd < rounds; ++rd) {
+    for (int k = 0; k < npairs; ++k) {
+      int a = ring[k], b = ring[Ne - 1 - k];
+      if (a > b) std::swap(a, b);
+      pairs[((size_t)rd * npairs + k) * 2] = a;
+      pairs[((size_t)rd * npairs + k) * 2 + 1] = b;  // b == N (odd N) marks a dummy
+    }
+    // rotate all but the first
+    int last = ring[Ne - 1];
+    for (int i = Ne - 1; i > 1; --i) ring[i] = ring[i - 1];
+    ring[1] = last;
+  }
+}
+
+// One-sided Jacobi on the columns of A (M x N, ld lda); V (N x N) accumulated
+// when non-null (set to I first).  Stops when every pair is orthogonal to 1e-15.
+int jacobi_svd(spk_handle* h, double* A, int64_t lda, int M, int N, double* V, cudaStream_t st) {
+  std::vector<int> pairs;
+  int rounds = 0, npairs = 0;
+  jacobi_schedule(N, pairs, rounds, npairs);
+  WS(dpairs, int, "jac_pairs", pairs.size());
+  WS(offs, double, "jac_offs", (size_t)rounds * npairs);
+  CK(cudaMemcpyAsync(dpairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, st));
+  if (V) {
+    set_zero_launch(V, (int64_t)N * N, st);
+    std::vector<double> eye((size_t)N * N, 0.0);
+    for (int i = 0; i < N; ++i) eye[(size_t)i * N + i] = 1.0;
+    CK(cudaMemcpyAsync(V, eye.data(), sizeof(double) * N * N, cudaMemcpyHostToDevice, st));
+    TRY(wait_stream(h, st, h->host_wait_s));
+  }
+  std::vector<double> hoffs((size_t)rounds * npairs);
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int rd = 0; rd < rounds; ++rd)
+      jacobi_round_launch(A, lda, M, N, V, N, dpairs + (size_t)rd * npairs * 2, npairs,
+                          offs + (size_t)rd * npairs, st);
+    CK(cudaMemcpyAsync(hoffs.data(), offs, sizeof(double) * hoffs.size(), cudaMemcpyDeviceToHost, st));
+    TRY(wait_stream(h, st, h->host_wait_s));
+    CK(cudaGetLastError());
+    double mx = 0.0;
+    for (double v : hoffs) mx = std::max(mx, v);
+    if (mx < 1e-15) break;
+  }
+  return SPK_OK;
+}
+
+// Low-rank factors of Y (m x m): Y ~= Y1 Y2^T, keeping singular values above
+// trunc_tol * sigma_1 (Algorithm 1 after the loop).  Y1, Y2 (m x ell,
+// column-major, ld m) are workspace buffers returned through *Y1p, *Y2p.
+int truncate_Y(spk_handle* h, const double* Y, int m, double trunc_tol, uint64_t seed,
+               cudaStream_t st, double** Y1p, double** Y2p, int* ell_out) {
+  int k0 = std::min(m, 64);
+  const bool direct = m <= 256;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    if (direct) k0 = m;
+    double* Qz = nullptr;
+    int k1 = m;
+    if (!direct) {
+      WS(Om, double, "tr_Om", (size_t)m * k0);
+      WS(Z, double, "tr_Z", (size_t)m * k0);
+      WS(Z2, double, "tr_Z2", (size_t)m * k0);
+      gaussian_fill_launch(Om, (int64_t)m * k0, seed + 77 + attempt, st);
+      gemm_f64('N', 'N', m, k0, m, 1.0, Y, m, Om, m, 0.0, Z, m, st);
+      gemm_f64('T', 'N', m, k0, m, 1.0, Y, m, Z, m, 0.0, Z2, m, st);
+      gemm_f64('N', 'N', m, k0, m, 1.0, Y, m, Z2, m, 0.0, Z, m, st);
+      TRY(jacobi_svd(h, Z, m, m, k0, nullptr, st));
+      WS(sz, double, "tr_sz", k0);
+      WS(idx, int, "tr_idx", k0);
+      WS(f1, double, "tr_f1", k0);
+      WS(f2, double, "tr_f2", k0);
+      WS(dell, int, "tr_ell", 1);
+      col_norms_launch(Z, m, m, k0, sz, st);
+      select_sv_launch(sz, k0, 1e-14, idx, f1, f2, dell, st);
+      int hk1 = 0;
+      CK(cudaMemcpyAsync(&hk1, dell, sizeof(int), cudaMemcpyDeviceToHost, st));
+      TRY(wait_stream(h, st, h->host_wait_s));
+      if (hk1 <= 0) { *ell_out = 0; return SPK_OK; }
+      k1 = hk1;
+      WS(qz, double, "tr_Qz", (size_t)m * k1);
+      // Qz columns = Z columns / norm  (f2 = sigma^{-1/2}; apply twice via two gathers)
+      WS(fn, double, "tr_fn", k1);
+      // normalisation factors 1/sigma = f2^2
+      {
+        std::vector<double> hf2(k1);
+        CK(cudaMemcpyAsync(hf2.data(), f2, sizeof(double) * k1, cudaMemcpyDeviceToHost, st));
+        TRY(wait_stream(h, st, h->host_wait_s));
+        for (auto& v : hf2) v = v * v;
+        CK(cudaMemcpyAsync(fn, hf2.data(), sizeof(double) * k1, cudaMemcpyHostToDevice, st));
+      }
+      gather_cols_launch(Z, m, m, idx, fn, k1, qz, m, st);
+      Qz = qz;
+    }
+    // Bt = Y^T Qz (m x k1), or Y^T when direct
+    WS(Bt, double, "tr_Bt", (size_t)m * k1);
+    WS(Vb, double, "tr_Vb", (size_t)k1 * k1);
+    if (direct) {
+      // Bt = Y^T
+      WS(eye, double, "tr_eye", (size_t)m * m);
+      set_zero_launch(eye, (int64_t)m * m, st);
+      std::vector<double> he((size_t)m * m, 0.0);
+      for (int i = 0; i < m; ++i) he[(size_t)i * m + i] = 1.0;
+      CK(cudaMemcpyAsync(eye, he.data(), sizeof(double) * he.size(), cudaMemcpyHostToDevice, st));
+      gemm_f64('T', 'N', m, m, m, 1.0, Y, m, eye, m, 0.0, Bt, m, st);
+      TRY(wait_stream(h, st, h->host_wait_s));
+    } else {
+      gemm_f64('T', 'N', m, k1, m, 1.0, Y, m, Qz, m, 0.0, Bt, m, st);
+    }
+    TRY(jacobi_svd(h, Bt, m, m, k1, Vb, st));
+    WS(sg, double, "tr_sg", k1);
+    WS(idx2, int, "tr_idx2", k1);
+    WS(g1, double, "tr_g1", k1);
+    WS(g2, double, "tr_g2", k1);
+    WS(dell2, int, "tr_ell2", 1);
+    col_norms_launch(Bt, m, m, k1, sg, st);
+    select_sv_launch(sg, k1, trunc_tol, idx2, g1, g2, dell2, st);
+    int ell = 0;
+    CK(cudaMemcpyAsync(&ell, dell2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(wait_stream(h, st, h->host_wait_s));
+    if (!direct && ell > k1 - 8 && k0 < m) {
+      k0 = std::min(m, 2 * k0);
+      continue;
+    }
+    WS(Y1, double, "tr_Y1", (size_t)m * std::max(ell, 1));
+    WS(Y2, double, "tr_Y2", (size_t)m * std::max(ell, 1));
+    // Y ~= (Qz Vb) Sigma Ub^T, Bt Vb = Ub Sigma (after the rotations)
+    if (direct) {
+      gather_cols_launch(Vb, k1, k1, idx2, g1, ell, Y1, m, st);
+    } else {
+      WS(QV, double, "tr_QV", (size_t)m * k1);
+      gemm_f64('N', 'N', m, k1, k1, 1.0, Qz, m, Vb, k1, 0.0, QV, m, st);
+      gather_cols_launch(QV, m, m, idx2, g1, ell, Y1, m, st);
+    }
+    gather_cols_launch(Bt, m, m, idx2, g2, ell, Y2, m, st);
+    *Y1p = Y1;
+    *Y2p = Y2;
+    *ell_out = ell;
+    return SPK_OK;
+  }
+  return fail(h, SPK_ERR_ARG, "truncation sample size did not settle");
+}
+
+// ---------------------------------------------------------------------------
+template <typename TB, typename TC, typename TV>
+struct Side {
+  const spk_csr* op = nullptr;
+  int64_t n = 0;
+  int k = 1, r = 1, maxit = 1;
+  const TV* vals = nullptr;
+  TB* win = nullptr;
+  TC* W = nullptr;
+  double* hband = nullptr;   // (maxit+1) x (k+1) x r x r
+  double* r1inv = nullptr;   // (maxit+1) x r x r
+  double* r2inv = nullptr;
+  double* T = nullptr;
+  int64_t ldT = 0;
+  double* Q = nullptr;       // s x ldT
+  double* Ht = nullptr;
+  int64_t ldH = 0;
+  SketchDev sk;
+  TC* sk_scratch = nullptr;
+  double *w = nullptr, *w1 = nullptr, *t1 = nullptr, *t2 = nullptr;
+  double *ell = nullptr, *beta = nullptr, *R1 = nullptr, *R2 = nullptr, *Rinv = nullptr, *tau = nullptr;
+  double* partial = nullptr;
+  double* qpartial = nullptr;
+  int grid = 1;
+
+  TB* block(int j) const { return win + (size_t)(j % (k + 1)) * n * r; }
+  double* hcol(int d) const { return hband + (size_t)d * (k + 1) * r * r; }
+  double* hslot(int d, int q) const { return hcol(d) + (size_t)q * r * r; }
+  double* R1inv(int d) const { return r1inv + (size_t)d * r * r; }
+  double* R2inv(int d) const { return r2inv + (size_t)d * r * r; }
+};
+
+template <typename TB, typename TC, typename TV>
+struct Solver {
+  spk_handle* h;
+  cudaStream_t st;
+  spk_opts o;
+  int r = 1;
+  Side<TB, TC, TV> S[2];
+
+  int alloc_side(int idx, const spk_csr* op, int k, int s_rows, int sketch_id) {
+    auto& sd = S[idx];
+    const std::string p = idx == 0 ? "U_" : "V_";
+    sd.op = op;
+    sd.n = op->nrows;
+    sd.k = k;
+    sd.r = r;
+    sd.maxit = o.maxit;
+    sd.grid = grid_rows(h, sd.n);
+    const int64_t mmax = (int64_t)(o.maxit + 1) * r;
+    sd.ldT = mmax;
+    sd.ldH = mmax;
+    if (std::is_same<TV, double>::value) {
+      sd.vals = reinterpret_cast<const TV*>(op->val_dev);
+    } else {
+      TV* v = static_cast<TV*>(ws_get(h, p + "vals", sizeof(TV) * (size_t)std::max<int64_t>(op->nnz, 1)));
+      if (!v) return fail(h, SPK_ERR_ALLOC, "cannot allocate converted values");
+      convert_values_launch<TV>(op->val_dev, v, op->nnz, st);
+      sd.vals = v;
+    }
+#define SWS(field, type, name, count)                                                     \
+  sd.field = static_cast<type*>(ws_get(h, p + name, sizeof(type) * (size_t)(count)));     \
+  if (!sd.field) return fail(h, SPK_ERR_ALLOC, "cannot allocate %s%s", p.c_str(), name);
+    SWS(win, TB, "win", (size_t)(k + 1) * sd.n * r);
+    SWS(W, TC, "W", (size_t)sd.n * r);
+    SWS(hband, double, "hband", (size_t)(o.maxit + 2) * (k + 1) * r * r);
+    SWS(r1inv, double, "r1inv", (size_t)(o.maxit + 2) * r * r);
+    SWS(r2inv, double, "r2inv", (size_t)(o.maxit + 2) * r * r);
+    SWS(T, double, "T", (size_t)sd.ldT * sd.ldT);
+    SWS(Ht, double, "Ht", (size_t)sd.ldH * sd.ldH);
+    sketch_geometry(sd.sk, sd.n, s_rows, o.sketch_kind == SPK_SKETCH_IDENTITY, (int)sizeof(TC), r);
+    const int64_t s = sd.sk.s;
+    SWS(Q, double, "Q", (size_t)s * sd.ldT);
+    SWS(w, double, "w", (size_t)s * r);
+    SWS(w1, double, "w1", (size_t)s * r);
+    SWS(t1, double, "t1", (size_t)mmax * r);
+    SWS(t2, double, "t2", (size_t)mmax * r);
+    SWS(ell, double, "ell", r * r);
+    SWS(beta, double, "beta", r * r);
+    SWS(R1, double, "R1", r * r);
+    SWS(R2, double, "R2", r * r);
+    SWS(Rinv, double, "Rinv", r * r);
+    SWS(tau, double, "tau", r * r);
+    const int groups = (k + 3) / 4;
+    SWS(partial, double, "partial",
+        (size_t)std::max(std::max(sd.grid, 2 * h->sm_count), 64) * 4 * r * r * std::max(groups, 1));
+    SWS(qpartial, double, "qpartial", (size_t)q_update_chunks((int)mmax) * s * r);
+    SWS(sk_scratch, TC, "skscratch", std::max<int64_t>(1, sd.sk.npad * r));
+#undef SWS
+    if (!sd.sk.identity) {
+      int32_t* rows = static_cast<int32_t*>(ws_get(h, p + "rows", sizeof(int32_t) * s));
+      int8_t* signs = static_cast<int8_t*>(ws_get(h, p + "signs", (size_t)sd.n));
+      const size_t sb = sketch_draws_scratch_bytes(sd.n, s);
+      void* scratch = ws_get(h, "sk_draw_scratch", sb);
+      if (!rows || !signs || !scratch) return fail(h, SPK_ERR_ALLOC, "cannot allocate sketch draws");
+      char e[256] = {0};
+      int rc = sketch_draws_launch(sd.n, (int32_t)s, o.seed, sketch_id, rows, signs, scratch, sb, st, e, sizeof e);
+      if (rc != SPK_OK) return fail(h, rc, "%s", e);
+      sd.sk.rows = rows;
+      sd.sk.signs = signs;
+    }
+    CK(cudaMemsetAsync(sd.T, 0, sizeof(double) * sd.ldT * sd.ldT, st));
+    CK(cudaMemsetAsync(sd.Ht, 0, sizeof(double) * sd.ldH * sd.ldH, st));
+    CK(cudaMemsetAsync(sd.hband, 0, sizeof(double) * (o.maxit + 2) * (k + 1) * r * r, st));
+    return SPK_OK;
+  }
+
+  // CholQR2 of the s x r sketch block w: Q[:, m:m+r] tau = w.
+  void sketch_qr(Side<TB, TC, TV>& sd, int m) {
+    const int64_t s = sd.sk.s;
+    const int g = std::max(1, std::min<int>((int)((s + 255) / 256), h->sm_count * 2));
+    ts_gram_launch(sd.w, s, r, sd.partial, g, st);
+    chol_small_launch(sd.partial, g, r, sd.R1, sd.Rinv, h->flags, 1e-28, st);
+    ts_scale_launch(sd.w, s, r, sd.Rinv, sd.w, s, st);
+    ts_gram_launch(sd.w, s, r, sd.partial, g, st);
+    chol_small_launch(sd.partial, g, r, sd.R2, sd.Rinv, h->flags, 1e-28, st);
+    ts_scale_launch(sd.w, s, r, sd.Rinv, sd.Q + (int64_t)m * s, s, st);
+    combine_small_launch(sd.R2, sd.R1, sd.tau, r, 0, st);
+  }
+
+  int init_side(Side<TB, TC, TV>& sd, const double* C) {
+    // U_1 = C ell^{-1} by Cholesky QR twice (Algorithm 1, first step)
+    convert_block_launch<TC>(C, sd.W, sd.n * r, st);
+    WindowPtrs none{};
+    none.nwin = 0;
+    update_gram_launch<TB, TC>(sd.W, sd.n, r, none, sd.hband, sd.partial, sd.grid, 1, st);
+    chol_small_launch(sd.partial, sd.grid, r, sd.R1, sd.R1inv(0), h->flags, kBreakdownFloor, st);
+    scale_gram_launch<TC>(sd.W, sd.n, r, sd.R1inv(0), sd.partial, sd.grid, st);
+    chol_small_launch(sd.partial, sd.grid, r, sd.R2, sd.R2inv(0), h->flags, 1e-28, st);
+    combine_small_launch(sd.R2, sd.R1, sd.ell, r, 0, st);
+    scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(0), sd.block(1), st);
+    // T_1 = R factor of S U_1 (reading of Algorithm 1's first step), beta = T_1 ell
+    sketch_apply_launch<TB, TC>(sd.sk, sd.block(1), r, sd.w, sd.sk_scratch, st);
+    sketch_qr(sd, 0);
+    t_write_launch(sd.T, sd.ldT, 0, r, nullptr, nullptr, sd.tau, st);
+    combine_small_launch(sd.tau, sd.ell, sd.beta, r, 0, st);
+    return SPK_OK;
+  }
+
+  WindowPtrs window(const Side<TB, TC, TV>& sd, int d, int* first) const {
+    const int i0 = std::max(1, d - sd.k + 1);
+    WindowPtrs w{};
+    w.nwin = d - i0 + 1;
+    for (int q = 0; q < w.nwin; ++q) w.blk[q] = sd.block(i0 + q);
+    *first = i0;
+    return w;
+  }
+
+  // Arnoldi step d for one side, up to and including U_{d+1} (no sketch).
+  void arnoldi_basis(Side<TB, TC, TV>& sd, int d, bool replay) {
+    int i0 = 0;
+    WindowPtrs win = window(sd, d, &i0);
+    const int slot0 = i0 - (d - sd.k + 1);
+    double* hs = sd.hslot(d, slot0);
+    const spk_csr* op = sd.op;
+    if (!replay) {
+      spmm_dots_launch<TB, TC, TV>(op->rowptr_dev, op->col_dev, sd.vals, sd.n, r, sd.block(d), sd.W,
+                                   win, sd.partial, sd.grid, st);
+      for (int g = 0; g < win.nwin; g += 4) {
+        const int nq = std::min(4, win.nwin - g);
+        reduce_partials_launch(sd.partial + (size_t)(g / 4) * sd.grid * 4 * r * r, sd.grid,
+                               4 * r * r, nq * r * r, hs + (size_t)g * r * r, st);
+      }
+      update_gram_launch<TB, TC>(sd.W, sd.n, r, win, hs, sd.partial, sd.grid, 1, st);
+      chol_small_launch(sd.partial, sd.grid, r, sd.R1, sd.R1inv(d), h->flags, kBreakdownFloor, st);
+      scale_gram_launch<TC>(sd.W, sd.n, r, sd.R1inv(d), sd.partial, sd.grid, st);
+      chol_small_launch(sd.partial, sd.grid, r, sd.R2, sd.R2inv(d), h->flags, 1e-28, st);
+      combine_small_launch(sd.R2, sd.R1, sd.hslot(d, sd.k), r, 0, st);
+    } else {
+      WindowPtrs none{};
+      none.nwin = 0;
+      spmm_dots_launch<TB, TC, TV>(op->rowptr_dev, op->col_dev, sd.vals, sd.n, r, sd.block(d), sd.W,
+                                   none, sd.partial, sd.grid, st);
+      update_gram_launch<TB, TC>(sd.W, sd.n, r, win, hs, sd.partial, sd.grid, 0, st);
+      scale_gram_launch<TC>(sd.W, sd.n, r, sd.R1inv(d), sd.partial, sd.grid, st);
+    }
+    scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(d), sd.block(d + 1), st);
+  }
+
+  // Sketch of U_{d+1}, QR update of S U_{d+1}, T column, bordering update of H~.
+  void whiten_and_border(Side<TB, TC, TV>& sd, int d) {
+    const int m = d * r;
+    const int64_t s = sd.sk.s;
+    sketch_apply_launch<TB, TC>(sd.sk, sd.block(d + 1), r, sd.w, sd.sk_scratch, st);
+    const int nch = q_update_chunks(m);
+    qt_dot_launch(sd.Q, s, s, m, sd.w, r, sd.t1, st);
+    q_update_launch(sd.Q, s, s, m, sd.t1, r, sd.w, sd.w1, sd.qpartial, nch, st);
+    qt_dot_launch(sd.Q, s, s, m, sd.w1, r, sd.t2, st);
+    q_update_launch(sd.Q, s, s, m, sd.t2, r, sd.w1, sd.w, sd.qpartial, nch, st);
+    sketch_qr(sd, m);
+    t_write_launch(sd.T, sd.ldT, m, r, sd.t1, sd.t2, sd.tau, st);
+    // bordering (Section 5): Hhat_d from H~_{d-1}, then the correction -> H~_d
+    const int mp = m - r;
+    int i0 = 0;
+    (void)window(sd, d, &i0);
+    const int slot0 = i0 - (d - sd.k + 1);
+    if (d == 1) {
+      border_small_launch(sd.Ht, sd.ldH, 0, r, sd.T, sd.ldT, nullptr, sd.hslot(1, slot0), st);
+    } else {
+      const int nslots = d - i0;  // blocks i0 .. d-1
+      border_col_launch(sd.Ht, sd.ldH, mp, r, sd.T, sd.ldT, sd.hslot(d, slot0), i0, nslots,
+                        sd.hslot(d, slot0 + nslots), st);
+      border_small_launch(sd.Ht, sd.ldH, mp, r, sd.T, sd.ldT, sd.hslot(d - 1, sd.k),
+                          sd.hslot(d, slot0 + nslots), st);
+    }
+    border_correct_launch(sd.Ht, sd.ldH, m, r, sd.T, sd.ldT, sd.hslot(d, sd.k), st);
+  }
+
+  int check(int d, double* rho3, int* newton_iters) {
+    const int m = d * r;
+    WS(Hk, double, "pj_Hk", (size_t)m * m);
+    WS(Gk, double, "pj_Gk", (size_t)m * m);
+    WS(F, double, "pj_F", (size_t)m * m);
+    WS(out3, double, "pj_out3", 4);
+    copy_matrix_launch(S[0].Ht, S[0].ldH, Hk, m, m, m, st);
+    copy_matrix_launch(S[1].Ht, S[1].ldH, Gk, m, m, m, st);
+    set_zero_launch(F, (int64_t)m * m, st);
+    fill_rhs_launch(F, m, m, r, S[0].beta, S[1].beta, st);
+    if (o.inject & SPK_INJECT_SINGULAR)
+      return fail(h, SPK_ERR_SINGULAR_PROJECTED, "injected: singular projected equation");
+    TRY(sign_solve(h, m, Hk, Gk, F, o.max_newton, st, newton_iters));
+    rho_launch(F, m, m, r, S[0].T, S[0].ldT, S[1].T, S[1].ldT, S[0].hslot(d, S[0].k),
+               S[1].hslot(d, S[1].k), S[0].beta, S[1].beta, out3, st);
+    CK(cudaMemcpyAsync(rho3, out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TRY(wait_stream(h, st, (o.inject & SPK_INJECT_TIMEOUT) ? 0.0 : h->host_wait_s));
+    CK(cudaGetLastError());
+    return SPK_OK;
+  }
+
+  int recover(int d, const double* Y, spk_result* out) {
+    const int m = d * r;
+    double *Y1 = nullptr, *Y2 = nullptr;
+    int ell = 0;
+    TRY(truncate_Y(h, Y, m, o.trunc_tol, o.seed, st, &Y1, &Y2, &ell));
+    out->rank = ell;
+    out->mem_solution_vectors = 2 * (int64_t)ell;
+    if (ell == 0) return SPK_OK;
+    // W_i = T_i^{-1} Y_i  (T_U, T_V leading m x m)
+    trsm_upper_left_launch(S[0].T, S[0].ldT, m, Y1, m, ell, st);
+    trsm_upper_left_launch(S[1].T, S[1].ldT, m, Y2, m, ell, st);
+    double* Wf[2] = {Y1, Y2};
+    for (int side = 0; side < 2; ++side) {
+      auto& sd = S[side];
+      double* X = nullptr;
+      if (cudaMalloc(&X, sizeof(double) * sd.n * ell) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, SPK_ERR_ALLOC, "cannot allocate factor X%d", side + 1);
+      }
+      if (side == 0) out->X1_dev = X; else out->X2_dev = X;
+      CK(cudaMemsetAsync(X, 0, sizeof(double) * sd.n * ell, st));
+      // second sweep: U_1 from C, then U_{j+1} from the stored coefficients
+      int last = 0;
+      for (int j = 1; j <= d; ++j) {
+        if (j - last == sd.k || j == d) {
+          WindowPtrs blocks{};
+          blocks.nwin = j - last;
+          for (int q = 0; q < blocks.nwin; ++q) blocks.blk[q] = sd.block(last + 1 + q);
+          x_accumulate_launch<TB>(X, sd.n, ell, r, blocks, Wf[side] + (size_t)last * r, m, st);
+          last = j;
+        }
+        if (j == d) break;
+        arnoldi_basis(sd, j, true);
+      }
+    }
+    return SPK_OK;
+  }
+
+  int replay_start(Side<TB, TC, TV>& sd, const double* C) {
+    convert_block_launch<TC>(C, sd.W, sd.n * r, st);
+    scale_gram_launch<TC>(sd.W, sd.n, r, sd.R1inv(0), sd.partial, sd.grid, st);
+    scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(0), sd.block(1), st);
+    return SPK_OK;
+  }
+
+  int run(const spk_csr* A, const spk_csr* BT, const double* C1, const double* C2,
+          spk_result* out) {
+    cudaEvent_t e0, e1, ec0, ec1, er0, er1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&ec0);
+    cudaEventCreate(&ec1);
+    cudaEventCreate(&er0);
+    cudaEventCreate(&er1);
+    int rc = run_inner(A, BT, C1, C2, out, e0, e1, ec0, ec1, er0, er1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(ec0);
+    cudaEventDestroy(ec1);
+    cudaEventDestroy(er0);
+    cudaEventDestroy(er1);
+    return rc;
+  }
+
+  int run_inner(const spk_csr* A, const spk_csr* BT, const double* C1, const double* C2,
+                spk_result* out, cudaEvent_t e0, cudaEvent_t e1, cudaEvent_t ec0, cudaEvent_t ec1,
+                cudaEvent_t er0, cudaEvent_t er1) {
+    CK(cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), st));
+    // optional host-side fault injection on a private copy of C1
+    const double* C1use = C1;
+    if (o.inject & (SPK_INJECT_NAN_C1 | SPK_INJECT_RANK_DEFICIENT)) {
+      WS(c1c, double, "inj_C1", (size_t)A->nrows * r);
+      CK(cudaMemcpyAsync(c1c, C1, sizeof(double) * A->nrows * r, cudaMemcpyDeviceToDevice, st));
+      if (o.inject & SPK_INJECT_NAN_C1) {
+        const double nanv = std::nan("");
+        CK(cudaMemcpyAsync(c1c, &nanv, sizeof(double), cudaMemcpyHostToDevice, st));
+      }
+      if ((o.inject & SPK_INJECT_RANK_DEFICIENT) && r > 1) {
+        // column 1 := column 0 (row-major, strided copy)
+        CK(cudaMemcpy2DAsync(c1c + 1, sizeof(double) * r, C1, sizeof(double) * r, sizeof(double),
+                             A->nrows, cudaMemcpyDeviceToDevice, st));
+      }
+      TRY(wait_stream(h, st, h->host_wait_s));
+      C1use = c1c;
+    }
+    const int s_req = o.s;
+    TRY(alloc_side(0, A, o.k_left, s_req, 0));
+    TRY(alloc_side(1, BT, o.k_right, s_req, o.same_sketch ? 0 : 1));
+    cudaEventRecord(e0, st);
+    TRY(init_side(S[0], C1use));
+    TRY(init_side(S[1], C2));
+    uint32_t f = 0;
+    TRY(read_flags(h, st, &f));
+    TRY(flags_to_status(h, f));
+
+    std::vector<int32_t> hd;
+    std::vector<double> hrel;
+    double rho3[3] = {0, 0, 0};
+    int newton = 0;
+    int d = 0;
+    bool converged = false;
+    double ms_proj = 0.0;
+    int next_check = o.fixed_d > 0 ? o.fixed_d : (o.check_schedule == SPK_CHECK_ADAPTIVE ? o.p : o.p);
+    const int dmax = o.fixed_d > 0 ? std::min(o.fixed_d, o.maxit) : o.maxit;
+    for (d = 1; d <= dmax; ++d) {
+      for (int side = 0; side < 2; ++side) {
+        arnoldi_basis(S[side], d, false);
+        whiten_and_border(S[side], d);
+      }
+      const bool last = d == dmax;
+      bool do_check = last;
+      if (o.fixed_d <= 0) {
+        if (o.check_schedule == SPK_CHECK_EVERY_P) do_check = do_check || (d % o.p == 0);
+        else do_check = do_check || d >= next_check;
+      }
+      if (!do_check) continue;
+      TRY(read_flags(h, st, &f));
+      CK(cudaGetLastError());
+      TRY(flags_to_status(h, f));
+      cudaEventRecord(ec0, st);
+      TRY(check(d, rho3, &newton));
+      cudaEventRecord(ec1, st);
+      TRY(wait_stream(h, st, h->host_wait_s));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ec0, ec1);
+      ms_proj += ms;
+      hd.push_back(d);
+      hrel.push_back(rho3[1]);
+      if (!std::isfinite(rho3[1])) return fail(h, SPK_ERR_NONFINITE, "non-finite residual estimate at d=%d", d);
+      if (o.fixed_d <= 0 && rho3[1] < o.tol) {
+        converged = true;
+        break;
+      }
+      if (o.check_schedule == SPK_CHECK_ADAPTIVE && o.fixed_d <= 0) {
+        // geometric warm-up, then extrapolate log(rho) linearly in d
+        int nxt = 2 * d;
+        const size_t nh = hrel.size();
+        if (nh >= 2 && hrel[nh - 1] < hrel[nh - 2] && hrel[nh - 1] > 0) {
+          const double slope = (std::log(hrel[nh - 1]) - std::log(hrel[nh - 2])) /
+                               (double)(hd[nh - 1] - hd[nh - 2]);
+          if (slope < 0) {
+            const double need = (std::log(o.tol) - std::log(hrel[nh - 1])) / slope;
+            int pred = d + (int)std::ceil(need * 1.03) + 1;
+            pred = ((pred + o.p - 1) / o.p) * o.p;
+            nxt = std::min(nxt, std::max(pred, d + o.p));
+          }
+        }
+        next_check = std::max(d + 1, std::min(nxt, dmax));
+      }
+    }
+    if (d > dmax) d = dmax;
+    cudaEventRecord(e1, st);
+    TRY(read_flags(h, st, &f));
+    TRY(flags_to_status(h, f));
+    // Y of the last check is in pj_F
+    double* Y = static_cast<double*>(h->bufs["pj_F"].p);
+    cudaEventRecord(er0, st);
+    TRY(replay_start(S[0], C1use));
+    TRY(replay_start(S[1], C2));
+    TRY(recover(d, Y, out));
+    cudaEventRecord(er1, st);
+    TRY(wait_stream(h, st, h->host_wait_s));
+    CK(cudaGetLastError());
+    TRY(read_flags(h, st, &f));
+    TRY(flags_to_status(h, f));
+    float ms_loop = 0.f, ms_rec = 0.f;
+    cudaEventElapsedTime(&ms_loop, e0, e1);
+    cudaEventElapsedTime(&ms_rec, er0, er1);
+    out->iters = d;
+    out->converged = converged ? 1 : 0;
+    out->rel_rho = rho3[1];
+    out->rho = rho3[0];
+    out->newton_iters = newton;
+    out->n_hist = (int)hd.size();
+    out->hist_d_host = (int32_t*)malloc(sizeof(int32_t) * std::max<size_t>(1, hd.size()));
+    out->hist_rel_host = (double*)malloc(sizeof(double) * std::max<size_t>(1, hrel.size()));
+    for (size_t i = 0; i < hd.size(); ++i) {
+      out->hist_d_host[i] = hd[i];
+      out->hist_rel_host[i] = hrel[i];
+    }
+    out->mem_basis_vectors = (int64_t)(o.k_left + 1 + o.k_right + 1) * r;
+    out->ms_project = ms_proj;
+    out->ms_arnoldi = std::max(0.0, (double)ms_loop - ms_proj);
+    out->ms_recover = ms_rec;
+    out->status = (converged || o.fixed_d > 0) ? SPK_OK : SPK_ERR_NOT_CONVERGED;
+    return out->status;
+  }
+};
+
+int validate(spk_handle* h, const spk_csr* A, const spk_csr* BT, const double* C1, const double* C2,
+             int r, const spk_opts* o) {
+  if (!h) return SPK_ERR_ARG;
+  if (!A || !BT || !C1 || !C2 || !o) return fail(h, SPK_ERR_ARG, "null argument");
+  if (r < 1 || r > kMaxR) return fail(h, SPK_ERR_ARG, "block width r=%d outside [1, %d]", r, kMaxR);
+  if (A->nrows != A->ncols || BT->nrows != BT->ncols || A->nrows < 1 || BT->nrows < 1)
+    return fail(h, SPK_ERR_ARG, "operators must be square and non-empty");
+  if (!A->rowptr_dev || !A->col_dev || !A->val_dev || !BT->rowptr_dev || !BT->col_dev || !BT->val_dev)
+    return fail(h, SPK_ERR_ARG, "null CSR array");
+  if (o->k_left < 1 || o->k_right < 1 || o->k_left > kMaxWin || o->k_right > kMaxWin)
+    return fail(h, SPK_ERR_ARG, "truncation k must lie in [1, %d]", kMaxWin);
+  if (o->maxit < 1 || o->p < 1) return fail(h, SPK_ERR_ARG, "maxit and p must be >= 1");
+  if (o->max_newton < 1) return fail(h, SPK_ERR_ARG, "max_newton must be >= 1");
+  if (o->same_sketch && A->nrows != BT->nrows)
+    return fail(h, SPK_ERR_ARG, "same_sketch needs n1 == n2");
+  const int64_t mmax = (int64_t)(o->maxit + 1) * r;
+  if (o->sketch_kind == SPK_SKETCH_IDENTITY) {
+    if (A->nrows < mmax || BT->nrows < mmax)
+      return fail(h, SPK_ERR_ARG, "identity sketch needs n >= (maxit+1) r");
+  } else if (o->sketch_kind == SPK_SKETCH_SRHT) {
+    if (o->s < mmax)
+      return fail(h, SPK_ERR_ARG, "sketch rows s=%d must be >= (maxit+1) r = %lld", o->s, (long long)mmax);
+  } else {
+    return fail(h, SPK_ERR_ARG, "unknown sketch kind");
+  }
+  if (o->precision < SPK_PREC_FP64 || o->precision > SPK_PREC_MIXED_BF16)
+    return fail(h, SPK_ERR_ARG, "unknown precision");
+  return SPK_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+int spk_version(void) { return 100; }
+
+void spk_opts_default(spk_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->k_left = 2;
+  o->k_right = 2;
+  o->s = 600;
+  o->maxit = 300;
+  o->p = 1;
+  o->sketch_kind = SPK_SKETCH_SRHT;
+  o->precision = SPK_PREC_FP64;
+  o->check_schedule = SPK_CHECK_EVERY_P;
+  o->max_newton = 100;
+  o->tol = 1e-8;
+  o->trunc_tol = 1e-12;
+  o->seed = 0;
+}
+
+const char* spk_status_string(int s) {
+  switch (s) {
+    case SPK_OK: return "ok";
+    case SPK_ERR_ARG: return "invalid argument";
+    case SPK_ERR_CUDA: return "CUDA error";
+    case SPK_ERR_ALLOC: return "device allocation failed";
+    case SPK_ERR_BREAKDOWN: return "rank-deficient block (Cholesky breakdown)";
+    case SPK_ERR_SINGULAR_PROJECTED: return "projected equation not solvable";
+    case SPK_ERR_NONFINITE: return "non-finite value";
+    case SPK_ERR_NOT_CONVERGED: return "not converged within maxit";
+    case SPK_ERR_TIMEOUT: return "bounded wait expired";
+    case SPK_ERR_UNSUPPORTED: return "unsupported option";
+    default: return "unknown status";
+  }
+}
+
+int spk_create(spk_handle** out, int device) {
+  if (!out) return SPK_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return SPK_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return SPK_ERR_CUDA;
+  spk_handle* h = new spk_handle();
+  h->device = device;
+  cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&h->flags, sizeof(uint32_t)) != cudaSuccess) {
+    delete h;
+    return SPK_ERR_ALLOC;
+  }
+  *out = h;
+  return SPK_OK;
+}
+
+void spk_destroy(spk_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  for (auto& kv : h->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  if (h->flags) cudaFree(h->flags);
+  delete h;
+}
+
+const char* spk_last_error(spk_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+void spk_result_free(spk_result* res) {
+  if (!res) return;
+  if (res->X1_dev) cudaFree(res->X1_dev);
+  if (res->X2_dev) cudaFree(res->X2_dev);
+  free(res->hist_d_host);
+  free(res->hist_rel_host);
+  res->X1_dev = res->X2_dev = nullptr;
+  res->hist_d_host = nullptr;
+  res->hist_rel_host = nullptr;
+}
+
+int spk_solve(spk_handle* h, const spk_csr* A, const spk_csr* BT, const double* C1,
+              const double* C2, int r, const spk_opts* opts, void* stream, spk_result* out) {
+  if (!out) return SPK_ERR_ARG;
+  memset(out, 0, sizeof *out);
+  out->n1 = A ? A->nrows : 0;
+  out->n2 = BT ? BT->nrows : 0;
+  int rc = validate(h, A, BT, C1, C2, r, opts);
+  if (rc != SPK_OK) {
+    out->status = rc;
+    return rc;
+  }
+  if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, SPK_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  switch (opts->precision) {
+    case SPK_PREC_FP64: {
+      Solver<double, double, double> s{h, st, *opts, r};
+      rc = s.run(A, BT, C1, C2, out);
+      break;
+    }
+    case SPK_PREC_MIXED_FP32: {
+      Solver<float, float, float> s{h, st, *opts, r};
+      rc = s.run(A, BT, C1, C2, out);
+      break;
+    }
+    default: {
+      Solver<__nv_bfloat16, float, float> s{h, st, *opts, r};
+      rc = s.run(A, BT, C1, C2, out);
+      break;
+    }
+  }
+  if (rc != SPK_OK && rc != SPK_ERR_NOT_CONVERGED) {
+    spk_result_free(out);
+    out->rank = 0;
+  }
+  out->status = rc;
+  return rc;
+}
+
+int spk_solve_adjoint(spk_handle* h, const spk_csr* AT, const spk_csr* B, const double* G1,
+                      const double* G2, int q, const spk_opts* opts, void* stream,
+                      spk_result* out) {
+  // A^T L + L B^T = G1 G2^T is Eq. (1.1) with coefficients (A^T, B^T): its
+  // right Krylov space is K((B^T)^T, G2) = K(B, G2).
+  return spk_solve(h, AT, B, G1, G2, q, opts, stream, out);
+}
+
+int spk_adjoint_gradients(spk_handle* h, const spk_result* X, const spk_result* L,
+                          const double* C1, const double* C2, int r, const spk_csr* A_theta,
+                          const spk_csr* B_theta, double* dC1, double* dC2, double* dtheta,
+                          void* stream) {
+  if (!h || !X || !L || !C1 || !C2 || !dC1 || !dC2) return SPK_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int lx = X->rank, ll = L->rank;
+  const int n1 = X->n1, n2 = X->n2;
+  if (L->n1 != n1 || L->n2 != n2) return fail(h, SPK_ERR_ARG, "solution and adjoint sizes differ");
+  if (ll == 0 || lx == 0) {
+    CK(cudaMemsetAsync(dC1, 0, sizeof(double) * n1 * r, st));
+    CK(cudaMemsetAsync(dC2, 0, sizeof(double) * n2 * r, st));
+    if (dtheta) *dtheta = 0.0;
+    return wait_stream(h, st, h->host_wait_s);
+  }
+  // Row-major n x c  ==  column-major c x n with leading dimension c.
+  WS(t1, double, "ag_t1", (size_t)ll * r);
+  // dC1 = L1 (L2^T C2)
+  gemm_f64('N', 'T', ll, r, n2, 1.0, L->X2_dev, ll, C2, r, 0.0, t1, ll, st);
+  gemm_f64('T', 'N', r, n1, ll, 1.0, t1, ll, L->X1_dev, ll, 0.0, dC1, r, st);
+  // dC2 = L2 (L1^T C1)
+  gemm_f64('N', 'T', ll, r, n1, 1.0, L->X1_dev, ll, C1, r, 0.0, t1, ll, st);
+  gemm_f64('T', 'N', r, n2, ll, 1.0, t1, ll, L->X2_dev, ll, 0.0, dC2, r, st);
+  if (dtheta) {
+    double val = 0.0;
+    const int mx = std::max(lx, ll);
+    WS(M1, double, "ag_M1", (size_t)mx * mx);
+    WS(M2, double, "ag_M2", (size_t)mx * mx);
+    WS(sc, double, "ag_sc", 4);
+    if (A_theta) {
+      WS(AX, double, "ag_AX", (size_t)n1 * lx);
+      spmm_wide_launch(A_theta->rowptr_dev, A_theta->col_dev, A_theta->val_dev, n1, lx, X->X1_dev, AX, st);
+      // M1 = L1^T (A_theta X1)  (ll x lx);  M2 = X2^T L2 (lx x ll)
+      gemm_f64('N', 'T', ll, lx, n1, 1.0, L->X1_dev, ll, AX, lx, 0.0, M1, ll, st);
+      gemm_f64('N', 'T', lx, ll, n2, 1.0, X->X2_dev, lx, L->X2_dev, ll, 0.0, M2, lx, st);
+      if (ll == lx) val += trace_product(M1, M2, ll, sc, st);
+      else {
+        // general: trace(M1 M2) with M1 ll x lx, M2 lx x ll -> sum_ij M1[i,j] M2[j,i]
+        WS(P, double, "ag_P", (size_t)ll * ll);
+        gemm_f64('N', 'N', ll, ll, lx, 1.0, M1, ll, M2, lx, 0.0, P, ll, st);
+        WS(I, double, "ag_I", (size_t)ll * ll);
+        std::vector<double> eye((size_t)ll * ll, 0.0);
+        for (int i = 0; i < ll; ++i) eye[(size_t)i * ll + i] = 1.0;
+        CK(cudaMemcpyAsync(I, eye.data(), sizeof(double) * eye.size(), cudaMemcpyHostToDevice, st));
+        val += trace_product(P, I, ll, sc, st);
+      }
+    }
+    if (B_theta) {
+      WS(BL, double, "ag_BL", (size_t)n2 * ll);
+      spmm_wide_launch(B_theta->rowptr_dev, B_theta->col_dev, B_theta->val_dev, n2, ll, L->X2_dev, BL, st);
+      // M1 = L1^T X1 (ll x lx); M2 = X2^T (B_theta L2) (lx x ll)
+      gemm_f64('N', 'T', ll, lx, n1, 1.0, L->X1_dev, ll, X->X1_dev, lx, 0.0, M1, ll, st);
+      gemm_f64('N', 'T', lx, ll, n2, 1.0, X->X2_dev, lx, BL, ll, 0.0, M2, lx, st);
+      WS(P2, double, "ag_P2", (size_t)ll * ll);
+      gemm_f64('N', 'N', ll, ll, lx, 1.0, M1, ll, M2, lx, 0.0, P2, ll, st);
+      WS(I2, double, "ag_I2", (size_t)ll * ll);
+      std::vector<double> eye((size_t)ll * ll, 0.0);
+      for (int i = 0; i < ll; ++i) eye[(size_t)i * ll + i] = 1.0;
+      CK(cudaMemcpyAsync(I2, eye.data(), sizeof(double) * eye.size(), cudaMemcpyHostToDevice, st));
+      val += trace_product(P2, I2, ll, sc, st);
+    }
+    *dtheta = -val;
+  }
+  TRY(wait_stream(h, st, h->host_wait_s));
+  CK(cudaGetLastError());
+  return SPK_OK;
+}
+
+int spk_sketch_draws(spk_handle* h, int64_t n, int32_t s, uint64_t seed, int32_t sketch_id,
+                     int32_t* rows, int8_t* signs, void* stream) {
+  if (!h || !rows || !signs || n < 1) return SPK_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t sb = sketch_draws_scratch_bytes(n, s);
+  void* scratch = ws_get(h, "sk_draw_scratch", sb);
+  if (!scratch) return fail(h, SPK_ERR_ALLOC, "cannot allocate sketch scratch");
+  char e[256] = {0};
+  int rc = sketch_draws_launch(n, s, seed, sketch_id, rows, signs, scratch, sb, st, e, sizeof e);
+  if (rc != SPK_OK) return fail(h, rc, "%s", e);
+  return wait_stream(h, st, h->host_wait_s);
+}
+
+int spk_sketch_apply(spk_handle* h, int64_t n, int32_t s, uint64_t seed, int32_t sketch_id,
+                     const double* X, int32_t r, double* SX, void* stream) {
+  if (!h || !X || !SX || n < 1 || r < 1 || r > kMaxR) return SPK_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SketchDev sk;
+  sketch_geometry(sk, n, s, 0, (int)sizeof(double), r);
+  int32_t* rows = static_cast<int32_t*>(ws_get(h, "sa_rows", sizeof(int32_t) * s));
+  int8_t* signs = static_cast<int8_t*>(ws_get(h, "sa_signs", (size_t)n));
+  double* scratch = static_cast<double*>(ws_get(h, "sa_scratch", sketch_apply_scratch_bytes(sk, r)));
+  if (!rows || !signs || !scratch) return fail(h, SPK_ERR_ALLOC, "cannot allocate sketch buffers");
+  int rc = spk_sketch_draws(h, n, s, seed, sketch_id, rows, signs, stream);
+  if (rc != SPK_OK) return rc;
+  sk.rows = rows;
+  sk.signs = signs;
+  sketch_apply_launch<double, double>(sk, X, r, SX, scratch, st);
+  TRY(wait_stream(h, st, h->host_wait_s));
+  CK(cudaGetLastError());
+  return SPK_OK;
+}
+
+int spk_spmm(spk_handle* h, const spk_csr* A, const double* X, int32_t r, double* Y, void* stream) {
+  if (!h || !A || !X || !Y || r < 1) return SPK_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (r <= kMaxR) {
+    WindowPtrs none{};
+    none.nwin = 0;
+    spmm_dots_launch<double, double, double>(A->rowptr_dev, A->col_dev, A->val_dev, A->nrows, r, X,
+                                             Y, none, nullptr, grid_rows(h, A->nrows), st);
+  } else {
+    spmm_wide_launch(A->rowptr_dev, A->col_dev, A->val_dev, A->nrows, r, X, Y, st);
+  }
+  TRY(wait_stream(h, st, h->host_wait_s));
+  CK(cudaGetLastError());
+  return SPK_OK;
+}
+
+int spk_sylvester_dense(spk_handle* h, int32_t m, const double* H, const double* G,
+                        const double* F, double* Y, int32_t* newton_iters, void* stream) {
+  if (!h || m < 1 || !H || !G || !F || !Y) return SPK_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WS(Hk, double, "sd_Hk", (size_t)m * m);
+  WS(Gk, double, "sd_Gk", (size_t)m * m);
+  CK(cudaMemcpyAsync(Hk, H, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(Gk, G, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(Y, F, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), st));
+  int it = 0;
+  int rc = sign_solve(h, m, Hk, Gk, Y, 100, st, &it);
+  if (newton_iters) *newton_iters = it;
+  if (rc != SPK_OK) return rc;
+  TRY(wait_stream(h, st, h->host_wait_s));
+  CK(cudaGetLastError());
+  return SPK_OK;
+}
+
+int spk_inspect(spk_handle* h, const char* name, double* dst, int64_t count, int64_t* avail) {
+  if (!h || !name) return SPK_ERR_ARG;
+  static const char* allowed[] = {"U_T", "V_T", "U_Ht", "V_Ht", "U_hband", "V_hband", "U_beta", "V_beta"};
+  bool ok = false;
+  for (const char* a : allowed) ok = ok || strcmp(a, name) == 0;
+  auto it = h->bufs.find(name);
+  if (!ok || it == h->bufs.end() || !it->second.p) return fail(h, SPK_ERR_ARG, "no buffer %s", name);
+  const int64_t n = (int64_t)(it->second.bytes / sizeof(double));
+  if (avail) *avail = n;
+  if (dst && count > 0) {
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(dst, it->second.p, sizeof(double) * std::min(n, count), cudaMemcpyDeviceToHost));
+  }
+  return SPK_OK;
+}
+
+}  // extern "C"

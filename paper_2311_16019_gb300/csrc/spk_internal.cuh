@@ -1,0 +1,170 @@
+// Internal declarations of libspk (not part of the C ABI).
+//
+// Layout conventions used by every kernel:
+//   block vectors  n x r   row-major, element (i, c) at [i * r + c]
+//   dense matrices m x m   column-major with an explicit leading dimension
+//   T (whitening factor), Q (sketched basis), H~ (projected matrix): FP64
+//   column-major; the window of basis blocks is a ring of k+1 blocks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/spk.h"
+
+namespace spk {
+
+constexpr int kMaxR = 4;      // block width r supported by the fused kernels
+constexpr int kMaxWin = 8;    // largest truncation window k
+
+// Device-side status word bits (written by kernels, read by the host).
+enum : uint32_t {
+  kFlagBreakdown = 1u << 0,
+  kFlagNonfinite = 1u << 1,
+  kFlagZeroPivot = 1u << 2,
+};
+
+// ---------------------------------------------------------------- storage
+template <typename T> struct Store;
+template <> struct Store<double> {
+  __device__ __forceinline__ static double ld(const double* p) { return *p; }
+  __device__ __forceinline__ static void st(double* p, double v) { *p = v; }
+};
+template <> struct Store<float> {
+  __device__ __forceinline__ static float ld(const float* p) { return *p; }
+  __device__ __forceinline__ static void st(float* p, float v) { *p = v; }
+};
+template <> struct Store<__nv_bfloat16> {
+  __device__ __forceinline__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  __device__ __forceinline__ static void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- sketch
+struct SketchDev {
+  int64_t n = 0;        // rows of the sketched blocks
+  int64_t npad = 0;     // n' = 2^ceil(log2 n)
+  int32_t s = 0;        // sketch rows
+  int32_t n2 = 1;       // first-level transform length (power of two)
+  int32_t log2n2 = 0;
+  int64_t n1 = 1;       // number of first-level chunks, npad / n2
+  int32_t identity = 0; // S = I (s = n)
+  double scale = 1.0;   // 1/sqrt(s) (SRHT) or 1 (identity)
+  int32_t* rows = nullptr;   // s selected rows, ascending
+  int8_t* signs = nullptr;   // n Rademacher signs
+};
+
+// Launchers (k_sketch.cu)
+int sketch_draws_launch(int64_t n, int32_t s, uint64_t seed, int32_t sketch_id,
+                        int32_t* rows, int8_t* signs, void* scratch, size_t scratch_bytes,
+                        cudaStream_t st, char* err, size_t errlen);
+size_t sketch_draws_scratch_bytes(int64_t n, int32_t s);
+void sketch_geometry(SketchDev& sk, int64_t n, int32_t s, int identity, int elem_bytes, int r);
+size_t sketch_apply_scratch_bytes(const SketchDev& sk, int r);
+// SX (s x r column-major, FP64) = S X, X row-major n x r of type TB.
+template <typename TB, typename TC>
+void sketch_apply_launch(const SketchDev& sk, const TB* X, int r, double* SX, TC* scratch,
+                         cudaStream_t st);
+
+// ---------------------------------------------------------------- Arnoldi
+struct WindowPtrs {
+  const void* blk[kMaxWin];   // U_i for the k window blocks, oldest first
+  int nwin;
+};
+
+template <typename TB, typename TC, typename TV>
+void spmm_dots_launch(const int32_t* rowptr, const int32_t* col, const TV* val, int64_t n, int r,
+                      const TB* U, TC* W, WindowPtrs win, double* partial, int grid, cudaStream_t st);
+void reduce_partials_launch(const double* partial, int nparts, int stride, int count,
+                            double* out, cudaStream_t st);
+template <typename TB, typename TC>
+void update_gram_launch(TC* W, int64_t n, int r, WindowPtrs win, const double* h, double* partial,
+                        int grid, int want_gram, cudaStream_t st);
+void chol_small_launch(const double* partial, int nparts, int r, double* R, double* Rinv,
+                       uint32_t* flags, double rel_floor, cudaStream_t st);
+template <typename TC>
+void scale_gram_launch(TC* W, int64_t n, int r, const double* Rinv, double* partial, int grid,
+                       cudaStream_t st);
+template <typename TB, typename TC>
+void scale_store_launch(const TC* W, int64_t n, int r, const double* Rinv, TB* dst,
+                        cudaStream_t st);
+template <typename TB>
+void x_accumulate_launch(double* X, int64_t n, int ell, int r, WindowPtrs blocks,
+                         const double* Wrows, int64_t ldw, cudaStream_t st);
+void spmm_wide_launch(const int32_t* rowptr, const int32_t* col, const double* val, int64_t n,
+                      int w, const double* X, double* Y, cudaStream_t st);
+template <typename TV>
+void convert_values_launch(const double* src, TV* dst, int64_t count, cudaStream_t st);
+template <typename TB>
+void convert_block_launch(const double* src, TB* dst, int64_t count, cudaStream_t st);
+void combine_small_launch(const double* A, const double* B, double* C, int r, int mode,
+                          cudaStream_t st);
+
+// ---------------------------------------------------------------- whitening
+void qt_dot_launch(const double* Q, int64_t ldq, int64_t s, int m, const double* w, int r,
+                   double* t, cudaStream_t st);
+void q_update_launch(const double* Q, int64_t ldq, int64_t s, int m, const double* t, int r,
+                     const double* w_in, double* w_out, double* partial, int nchunk,
+                     cudaStream_t st);
+void ts_gram_launch(const double* w, int64_t s, int r, double* partial, int grid, cudaStream_t st);
+void ts_scale_launch(double* w, int64_t s, int r, const double* Rinv, double* out,
+                     int64_t ldo, cudaStream_t st);
+int q_update_chunks(int m);
+void t_write_launch(double* T, int64_t ldT, int m, int r, const double* t1, const double* t2,
+                    const double* tau, cudaStream_t st);
+
+// ---------------------------------------------------------------- projected
+void border_col_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, int64_t ldT,
+                       const double* hslots, int first_block, int nslots, const double* h_dd,
+                       cudaStream_t st);
+void border_small_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, int64_t ldT,
+                         const double* h_sub, const double* h_dd, cudaStream_t st);
+void border_correct_launch(double* Ht, int64_t ldH, int m, int r, const double* T, int64_t ldT,
+                           const double* h_next, cudaStream_t st);
+void rho_launch(const double* Y, int64_t ldY, int m, int r, const double* TU, int64_t ldTU,
+                const double* TV, int64_t ldTV, const double* hU, const double* hV,
+                const double* betaU, const double* betaV, double* out3, cudaStream_t st);
+void fill_rhs_launch(double* F, int64_t ldF, int m, int r, const double* betaU,
+                     const double* betaV, cudaStream_t st);
+
+// ---------------------------------------------------------------- dense FP64
+void gemm_f64(char ta, char tb, int M, int N, int K, double alpha, const double* A, int64_t lda,
+              const double* B, int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st);
+void copy_matrix_launch(const double* A, int64_t lda, double* B, int64_t ldb, int M, int N,
+                        cudaStream_t st);
+void set_zero_launch(double* A, int64_t count, cudaStream_t st);
+struct GjeState {
+  int32_t* ipiv;   // m
+  double* cvec;    // m
+  double* scal;    // [0] logdet, [1] pivot, [2..] scratch
+  uint32_t* flags;
+};
+void gje_invert(double* A, int64_t lda, int m, GjeState gs, cudaStream_t st);
+int sign_combine_grid(int m);
+void sign_combine_launch(double* Hk, const double* Hinv, int64_t ld, int m, double c,
+                         double* partial, int grid, cudaStream_t st);
+void scale_matrix_launch(double* A, int64_t ld, int M, int N, double a, cudaStream_t st);
+void trsm_upper_left_launch(const double* T, int64_t ldT, int m, double* X, int64_t ldX, int ncol,
+                            cudaStream_t st);
+void gaussian_fill_launch(double* A, int64_t count, uint64_t seed, cudaStream_t st);
+// one-sided Jacobi on the columns of A (M x N, column-major), accumulating V (N x N)
+void jacobi_round_launch(double* A, int64_t lda, int M, int N, double* V, int64_t ldv,
+                         const int* pairs, int npairs, double* offmax, cudaStream_t st);
+void col_norms_launch(const double* A, int64_t lda, int M, int N, double* out, cudaStream_t st);
+// singular value selection: idx[0..ell) = columns by decreasing sigma with
+// sigma > tol * sigma_max; f1 = sigma^{1/2}, f2 = sigma^{-1/2}; ell to *ell_out
+void select_sv_launch(const double* sigma, int N, double tol, int* idx, double* f1, double* f2,
+                      int* ell_out, cudaStream_t st);
+// out[:, t] = A[:, idx[t]] * f[t]
+void gather_cols_launch(const double* A, int64_t lda, int M, const int* idx, const double* f,
+                        int ncols, double* out, int64_t ldo, cudaStream_t st);
+double trace_product(const double* A, const double* B, int n, double* scratch, cudaStream_t st);
+
+}  // namespace spk

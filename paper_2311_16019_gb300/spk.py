@@ -1,0 +1,347 @@
+"""ctypes binding of libspk (include/spk.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module
+moves tensors to the device, fills the C structs, calls the C ABI and wraps
+library-owned device buffers as torch tensors (copied before release).
+There is no CPU fallback: if the library or a GPU is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libspk.so")
+
+SPK_OK = 0
+SPK_ERR_ARG = -1
+SPK_ERR_CUDA = -2
+SPK_ERR_ALLOC = -3
+SPK_ERR_BREAKDOWN = -4
+SPK_ERR_SINGULAR_PROJECTED = -5
+SPK_ERR_NONFINITE = -6
+SPK_ERR_NOT_CONVERGED = -7
+SPK_ERR_TIMEOUT = -8
+SPK_ERR_UNSUPPORTED = -9
+
+SKETCH = {"srht": 0, "identity": 1}
+PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_bf16": 2}
+CHECK = {"every_p": 0, "adaptive": 1}
+INJECT_NAN_C1, INJECT_RANK_DEFICIENT, INJECT_TIMEOUT, INJECT_SINGULAR = 1, 2, 4, 8
+
+
+class Csr(C.Structure):
+    _fields_ = [("nrows", C.c_int32), ("ncols", C.c_int32), ("nnz", C.c_int64),
+                ("rowptr_dev", C.c_void_p), ("col_dev", C.c_void_p), ("val_dev", C.c_void_p)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("k_left", C.c_int32), ("k_right", C.c_int32), ("s", C.c_int32),
+                ("maxit", C.c_int32), ("p", C.c_int32), ("sketch_kind", C.c_int32),
+                ("precision", C.c_int32), ("check_schedule", C.c_int32),
+                ("same_sketch", C.c_int32), ("fixed_d", C.c_int32), ("max_newton", C.c_int32),
+                ("inject", C.c_uint32), ("tol", C.c_double), ("trunc_tol", C.c_double),
+                ("seed", C.c_uint64), ("reserved", C.c_int32 * 8)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("rank", C.c_int32),
+                ("n1", C.c_int32), ("n2", C.c_int32), ("n_hist", C.c_int32),
+                ("converged", C.c_int32), ("newton_iters", C.c_int32),
+                ("rel_rho", C.c_double), ("rho", C.c_double),
+                ("X1_dev", C.c_void_p), ("X2_dev", C.c_void_p),
+                ("hist_d_host", C.POINTER(C.c_int32)), ("hist_rel_host", C.POINTER(C.c_double)),
+                ("mem_basis_vectors", C.c_int64), ("mem_solution_vectors", C.c_int64),
+                ("ms_arnoldi", C.c_double), ("ms_project", C.c_double), ("ms_recover", C.c_double),
+                ("reserved", C.c_int32 * 8)]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libspk.so (built in-tree by paper_2311_16019_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_2311_16019_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+    P = C.POINTER
+    sig = {
+        "spk_create": (i32, [P(vp), C.c_int]),
+        "spk_destroy": (None, [vp]),
+        "spk_last_error": (C.c_char_p, [vp]),
+        "spk_status_string": (C.c_char_p, [C.c_int]),
+        "spk_version": (C.c_int, []),
+        "spk_opts_default": (None, [P(Opts)]),
+        "spk_solve": (i32, [vp, P(Csr), P(Csr), vp, vp, C.c_int, P(Opts), vp, P(Result)]),
+        "spk_solve_adjoint": (i32, [vp, P(Csr), P(Csr), vp, vp, C.c_int, P(Opts), vp, P(Result)]),
+        "spk_adjoint_gradients": (i32, [vp, P(Result), P(Result), vp, vp, C.c_int, P(Csr), P(Csr),
+                                        vp, vp, P(dbl), vp]),
+        "spk_result_free": (None, [P(Result)]),
+        "spk_sketch_draws": (i32, [vp, i64, i32, u64, i32, vp, vp, vp]),
+        "spk_sketch_apply": (i32, [vp, i64, i32, u64, i32, vp, i32, vp, vp]),
+        "spk_spmm": (i32, [vp, P(Csr), vp, i32, vp, vp]),
+        "spk_sylvester_dense": (i32, [vp, i32, vp, vp, vp, vp, P(i32), vp]),
+        "spk_inspect": (i32, [vp, C.c_char_p, vp, i64, P(i64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SpkError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libspk needs a CUDA GPU; none is visible")
+    return torch
+
+
+class DeviceCSR:
+    """A CSR matrix held in device memory (int32 indices, float64 values)."""
+
+    def __init__(self, M, device="cuda"):
+        torch = _torch()
+        M = M.tocsr()
+        M.sort_indices()
+        self.shape = M.shape
+        self.rowptr = torch.as_tensor(M.indptr.astype(np.int32), device=device)
+        self.col = torch.as_tensor(M.indices.astype(np.int32), device=device)
+        self.val = torch.as_tensor(M.data.astype(np.float64), device=device)
+        self.c = Csr(M.shape[0], M.shape[1], M.nnz, self.rowptr.data_ptr(), self.col.data_ptr(),
+                     self.val.data_ptr())
+
+
+class _CAI:
+    def __init__(self, ptr: int, shape, typestr="<f8"):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Handle:
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        rc = self.lib.spk_create(C.byref(h), device)
+        if rc != SPK_OK:
+            raise SpkError(rc, "spk_create failed")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.spk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def error(self) -> str:
+        return self.lib.spk_last_error(self.h).decode()
+
+
+_handles: dict = {}
+
+
+def handle(device: int = 0) -> Handle:
+    if device not in _handles:
+        _handles[device] = Handle(device)
+    return _handles[device]
+
+
+@dataclasses.dataclass
+class SolveResult:
+    status: int
+    iters: int
+    rank: int
+    converged: bool
+    rel_rho: float
+    rho: float
+    X1: object          # torch (n1 x rank) float64 on the device
+    X2: object
+    hist_d: list
+    hist_rel: list
+    newton_iters: int
+    mem_basis_vectors: int
+    mem_solution_vectors: int
+    ms_arnoldi: float
+    ms_project: float
+    ms_recover: float
+
+
+def make_opts(*, k=2, k_right=None, s=600, maxit=300, p=1, tol=1e-8, trunc_tol=1e-12, seed=0,
+              sketch="srht", precision="fp64", check="every_p", same_sketch=False, fixed_d=0,
+              max_newton=100, inject=0) -> Opts:
+    o = Opts()
+    load().spk_opts_default(C.byref(o))
+    o.k_left = k
+    o.k_right = k if k_right is None else k_right
+    o.s = s
+    o.maxit = maxit
+    o.p = p
+    o.tol = tol
+    o.trunc_tol = trunc_tol
+    o.seed = seed
+    o.sketch_kind = SKETCH[sketch]
+    o.precision = PRECISION[precision]
+    o.check_schedule = CHECK[check]
+    o.same_sketch = int(bool(same_sketch))
+    o.fixed_d = fixed_d
+    o.max_newton = max_newton
+    o.inject = inject
+    return o
+
+
+def _result_to_py(lib, res: Result, keep_status=(SPK_OK, SPK_ERR_NOT_CONVERGED)) -> SolveResult:
+    torch = _torch()
+    X1 = X2 = None
+    if res.rank > 0 and res.X1_dev:
+        X1 = torch.as_tensor(_CAI(res.X1_dev, (res.n1, res.rank)), device="cuda").clone()
+        X2 = torch.as_tensor(_CAI(res.X2_dev, (res.n2, res.rank)), device="cuda").clone()
+    hd = [res.hist_d_host[i] for i in range(res.n_hist)] if res.hist_d_host else []
+    hr = [res.hist_rel_host[i] for i in range(res.n_hist)] if res.hist_rel_host else []
+    return SolveResult(res.status, res.iters, res.rank, bool(res.converged), res.rel_rho, res.rho,
+                       X1, X2, hd, hr, res.newton_iters, res.mem_basis_vectors,
+                       res.mem_solution_vectors, res.ms_arnoldi, res.ms_project, res.ms_recover)
+
+
+def _block(C_, device="cuda"):
+    torch = _torch()
+    t = torch.as_tensor(np.ascontiguousarray(C_), dtype=torch.float64, device=device) \
+        if not hasattr(C_, "is_cuda") else C_.to(device=device, dtype=torch.float64)
+    if t.dim() == 1:
+        t = t[:, None]
+    return t.contiguous()
+
+
+def solve(A, BT, C1, C2, *, device: int = 0, stream=None, raise_on_error: bool = True,
+          keep_raw: bool = False, **opts):
+    """s-PKSM solve of A X + X B = C1 C2^T; BT = B^T (CSR, scipy or DeviceCSR).
+
+    Returns SolveResult with X = X1 X2^T.  With keep_raw the library-owned
+    Result struct is returned as well (the caller then frees it with
+    free_raw); used by the adjoint gradients.
+    """
+    torch = _torch()
+    h = handle(device)
+    dA = A if isinstance(A, DeviceCSR) else DeviceCSR(A)
+    dB = BT if isinstance(BT, DeviceCSR) else DeviceCSR(BT)
+    c1 = _block(C1)
+    c2 = _block(C2)
+    o = make_opts(**opts)
+    res = Result()
+    torch.cuda.synchronize()
+    rc = h.lib.spk_solve(h.h, C.byref(dA.c), C.byref(dB.c), C.c_void_p(c1.data_ptr()),
+                         C.c_void_p(c2.data_ptr()), c1.shape[1], C.byref(o), _stream_ptr(stream),
+                         C.byref(res))
+    if rc not in (SPK_OK, SPK_ERR_NOT_CONVERGED):
+        msg = h.error()
+        h.lib.spk_result_free(C.byref(res))
+        if raise_on_error:
+            raise SpkError(rc, msg)
+        return SolveResult(rc, 0, 0, False, float("nan"), float("nan"), None, None, [], [], 0,
+                           0, 0, 0.0, 0.0, 0.0)
+    out = _result_to_py(h.lib, res)
+    if keep_raw:
+        return out, res
+    h.lib.spk_result_free(C.byref(res))
+    return out
+
+
+def free_raw(res: Result, device: int = 0):
+    handle(device).lib.spk_result_free(C.byref(res))
+
+
+def sketch_draws(n: int, s: int, seed: int, sketch_id: int, device: int = 0):
+    torch = _torch()
+    h = handle(device)
+    rows = torch.empty(s, dtype=torch.int32, device="cuda")
+    signs = torch.empty(n, dtype=torch.int8, device="cuda")
+    rc = h.lib.spk_sketch_draws(h.h, n, s, seed, sketch_id, C.c_void_p(rows.data_ptr()),
+                                C.c_void_p(signs.data_ptr()), _stream_ptr())
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+    return rows, signs
+
+
+def sketch_apply(X, s: int, seed: int, sketch_id: int, device: int = 0):
+    torch = _torch()
+    h = handle(device)
+    x = _block(X)
+    n, r = x.shape
+    SX = torch.empty((r, s), dtype=torch.float64, device="cuda")  # column-major s x r
+    rc = h.lib.spk_sketch_apply(h.h, n, s, seed, sketch_id, C.c_void_p(x.data_ptr()), r,
+                                C.c_void_p(SX.data_ptr()), _stream_ptr())
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+    return SX.t()
+
+
+def spmm(A, X, device: int = 0):
+    torch = _torch()
+    h = handle(device)
+    dA = A if isinstance(A, DeviceCSR) else DeviceCSR(A)
+    x = _block(X)
+    Y = torch.empty((dA.shape[0], x.shape[1]), dtype=torch.float64, device="cuda")
+    rc = h.lib.spk_spmm(h.h, C.byref(dA.c), C.c_void_p(x.data_ptr()), x.shape[1],
+                        C.c_void_p(Y.data_ptr()), _stream_ptr())
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+    return Y
+
+
+def sylvester_dense(H, G, F, device: int = 0):
+    """Y with H Y + Y G^T = F (m x m), by the library's sign-function solver."""
+    torch = _torch()
+    h = handle(device)
+    # column-major buffers: pass transposed contiguous copies
+    cm = lambda M: torch.as_tensor(np.asarray(M, dtype=np.float64).T.copy(), device="cuda")
+    Hd, Gd, Fd = cm(H), cm(G), cm(F)
+    m = Hd.shape[0]
+    Y = torch.empty_like(Fd)
+    it = C.c_int32(0)
+    rc = h.lib.spk_sylvester_dense(h.h, m, C.c_void_p(Hd.data_ptr()), C.c_void_p(Gd.data_ptr()),
+                                   C.c_void_p(Fd.data_ptr()), C.c_void_p(Y.data_ptr()),
+                                   C.byref(it), _stream_ptr())
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+    return Y.t().cpu().numpy(), it.value
+
+
+def inspect(name: str, device: int = 0) -> np.ndarray:
+    """Copy of an internal FP64 buffer of the last solve (see spk_inspect)."""
+    h = handle(device)
+    avail = C.c_int64(0)
+    rc = h.lib.spk_inspect(h.h, name.encode(), None, 0, C.byref(avail))
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+    out = np.empty(avail.value, dtype=np.float64)
+    rc = h.lib.spk_inspect(h.h, name.encode(), out.ctypes.data_as(C.c_void_p), avail.value,
+                           C.byref(avail))
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+    return out

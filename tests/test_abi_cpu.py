@@ -1,0 +1,93 @@
+"""The C-ABI library builds, loads and exports every symbol include/spk.h
+declares; its structs match the binding's layout (no GPU compute)."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "spk.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2311_16019_gb300 import build, spk
+    build.build()
+    return spk.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spk_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_layout_matches_binding(lib):
+    from paper_2311_16019_gb300 import spk
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "spk.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(spk_csr), sizeof(spk_opts), sizeof(spk_result),
+         offsetof(spk_opts, tol), offsetof(spk_result, X1_dev), offsetof(spk_result, ms_recover));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        got = [int(x) for x in subprocess.check_output([exe]).split()]
+    want = [ctypes.sizeof(spk.Csr), ctypes.sizeof(spk.Opts), ctypes.sizeof(spk.Result),
+            spk.Opts.tol.offset, spk.Result.X1_dev.offset, spk.Result.ms_recover.offset]
+    assert got == want
+
+
+def test_host_only_entry_points(lib):
+    from paper_2311_16019_gb300 import spk
+    o = spk.Opts()
+    lib.spk_opts_default(ctypes.byref(o))
+    assert o.k_left == 2 and o.tol == 1e-8 and o.max_newton > 0
+    assert lib.spk_status_string(spk.SPK_ERR_NOT_CONVERGED).decode().startswith("not converged")
+    assert lib.spk_version() >= 100
+
+
+def test_create_without_gpu_reports_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    h = ctypes.c_void_p()
+    assert lib.spk_create(ctypes.byref(h), 0) == -2  # SPK_ERR_CUDA, no abort
+    assert not h.value
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The binding raises when no GPU is visible instead of computing on the CPU."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    from paper_2311_16019_gb300 import inputs as I, spk
+    P = I.workload("lap16_r1")
+    with pytest.raises(RuntimeError):
+        spk.solve(P.A, P.BT, P.C1, P.C2, k=2, s=64, maxit=10)
+
+
+def test_package_does_not_import_oracle():
+    for dirpath, _, files in os.walk(os.path.join(ROOT, "paper_2311_16019_gb300")):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", txt, flags=re.M), f
+                assert "oracle/" not in txt, f

@@ -1,0 +1,193 @@
+"""GPU parity: libspk (through the C ABI) against the CPU oracle, element by
+element on the same seeded inputs.  Bit-exact for the sketch's integer draws;
+1e-10 relative Frobenius error for X at a fixed iteration count (FP64)."""
+import numpy as np
+import pytest
+import scipy.linalg as sl
+import scipy.sparse as sp
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2311_16019_gb300 import inputs as I  # noqa: E402
+from oracle import spkms as SP, sketch as SK, measure as M, arnoldi as AR  # noqa: E402
+
+TOL_X = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2311_16019_gb300 import build, spk
+    build.build()
+    return spk.load()
+
+
+def spk():
+    from paper_2311_16019_gb300 import spk as s
+    return s
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.mark.parametrize("n,s,seed,sid", [(1, 1, 0, 0), (5, 3, 1, 0), (1000, 200, 3, 1),
+                                          (1024, 1024, 2, 0), (4097, 100, 9, 1),
+                                          (262144, 12000, 1, 0), (884736, 3200, 2, 1)])
+def test_sketch_draws_bit_exact(n, s, seed, sid):
+    rows, signs = spk().sketch_draws(n, s, seed, sid)
+    orows, osigns = SK.srht_draws(n, s, seed, sid)
+    assert np.array_equal(host(rows).astype(np.int64), orows)
+    assert np.array_equal(host(signs).astype(np.int8), osigns)
+
+
+@pytest.mark.parametrize("n,r", [(3000, 3), (4096, 1), (70000, 4), (8193, 2)])
+def test_sketch_apply_exact_on_integers(n, r):
+    s = 500
+    X = np.random.default_rng(n).integers(-2000, 2000, size=(n, r)).astype(np.float64)
+    got = host(spk().sketch_apply(X, s, seed=4, sketch_id=1))
+    want = SK.srht_apply(X, s, seed=4, sketch_id=1)
+    assert np.array_equal(got, want)
+
+
+def test_sketch_apply_float():
+    n, r, s = 50000, 4, 2000
+    X = np.random.default_rng(1).standard_normal((n, r))
+    got = host(spk().sketch_apply(X, s, seed=5, sketch_id=0))
+    want = SK.srht_apply(X, s, seed=5, sketch_id=0)
+    assert np.linalg.norm(got - want) < 1e-13 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 7])
+def test_spmm(r):
+    P = I.workload("cd2d_40_r2")
+    X = np.random.default_rng(r).standard_normal((P.n1, r))
+    got = host(spk().spmm(P.A, X))
+    want = P.A @ X
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+
+
+def _rhp_matrix(m, seed, nonnormal=0.3):
+    rng = np.random.default_rng(seed)
+    lam = np.sort(rng.uniform(1.0, 200.0, m))
+    Qm, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    T = np.diag(lam) + nonnormal * np.triu(rng.standard_normal((m, m)), 1) * np.sqrt(lam)[None, :]
+    return Qm @ T @ Qm.T
+
+
+@pytest.mark.parametrize("m", [1, 8, 65, 200])
+def test_sylvester_dense_against_bartels_stewart(m):
+    H = _rhp_matrix(m, 1)
+    G = _rhp_matrix(m, 2)
+    F = np.zeros((m, m))
+    F[:2, :2] = np.random.default_rng(3).standard_normal((min(2, m), min(2, m)))
+    Y, it = spk().sylvester_dense(H, G, F)
+    Yref = sl.solve_sylvester(H, G.T, F)
+    assert np.linalg.norm(Y - Yref) <= 1e-11 * np.linalg.norm(Yref)
+    assert it < 60
+
+
+CASES = [
+    # workload, k, s, d, sketch
+    ("lap16_r1", 2, 64, 12, "srht"),
+    ("cd2d_24_r2", 2, 120, 10, "srht"),
+    ("cd2d_24_r2", 3, 300, 25, "srht"),
+    ("cd2d_20_r3", 2, 200, 15, "srht"),
+    ("cd2d_20_r4", 4, 256, 15, "srht"),
+    ("cd2d_20_r4", 1, 256, 8, "srht"),
+    ("cd2d_16_r2", 2, 256, 12, "identity"),
+    ("cd2d_33_r1", 3, 400, 30, "srht"),
+]
+
+
+@pytest.mark.parametrize("name,k,s,d,sketch", CASES)
+def test_fixed_d_parity(name, k, s, d, sketch):
+    P = I.workload(name)
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=k, s=s, maxit=d, p=1, tol=0.0, seed=7,
+                    sketch=sketch, fixed_d=d)
+    o = SP.spkms(P.A, P.BT, P.C1, P.C2, k=k, s=s, tol=0.0, maxit=d, p=d, seed=7, sketch=sketch)
+    assert g.iters == d
+    err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
+    assert err < TOL_X, err
+    assert g.rho == pytest.approx(o["rho"], rel=1e-8)
+    assert g.rank == o["rank"] or abs(g.rank - o["rank"]) <= 1
+    assert M.probe_errors(host(g.X1), host(g.X2), o["X1"], o["X2"]) < 1e-9
+
+
+def test_lap32_converged_same_d_and_parity():
+    """The 32 x 32 Laplacian workload (n = 1024, r = 1, k = 2, s = 600,
+    tol 1e-8, p = 1): same stopping iteration, X within 1e-10 of the oracle."""
+    P = I.workload("lap32_r1")
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=2, s=600, maxit=300, p=1, tol=1e-8, seed=0)
+    assert g.converged and g.status == 0
+    o = SP.spkms(P.A, P.BT, P.C1, P.C2, k=2, s=600, tol=0.0, maxit=g.iters, p=g.iters, seed=0)
+    err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
+    assert err < TOL_X, err
+    o2 = SP.spkms(P.A, P.BT, P.C1, P.C2, k=2, s=600, tol=1e-8, maxit=300, p=1, seed=0,
+                  recover=False)
+    assert abs(o2["d"] - g.iters) <= 1
+    assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 3e-8
+    assert g.hist_d == list(range(1, g.iters + 1))
+    assert all(np.isfinite(g.hist_rel))
+
+
+def test_diagonal_closed_form_gpu():
+    m = 6
+    P = I.diagonal_problem(48, m, 2, seed=3)
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=2, s=64, maxit=m, p=1, tol=0.0, seed=0,
+                    fixed_d=m, trunc_tol=1e-14)
+    a, b = P.meta["a"], P.meta["b"]
+    X = (P.C1 @ P.C2.T) / (a[:, None] + b[None, :])
+    Xg = host(g.X1) @ host(g.X2).T
+    assert np.linalg.norm(Xg - X) < 1e-10 * np.linalg.norm(X)
+
+
+def test_symmetry_gpu():
+    P = I.workload("lap16_r1")
+    g = spk().solve(P.A, P.BT, P.C1, P.C1, k=2, s=128, maxit=40, p=1, tol=0.0, fixed_d=40,
+                    same_sketch=True)
+    X = host(g.X1) @ host(g.X2).T
+    assert np.abs(X - X.T).max() < 1e-12 * np.abs(X).max()
+
+
+def test_not_converged_returns_factors():
+    P = I.workload("cd2d_24_r2")
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=2, s=120, maxit=5, p=2, tol=1e-14)
+    from paper_2311_16019_gb300.spk import SPK_ERR_NOT_CONVERGED
+    assert g.status == SPK_ERR_NOT_CONVERGED and not g.converged
+    assert g.iters == 5 and g.hist_d == [2, 4, 5] and g.rank > 0
+
+
+def test_invalid_arguments_are_errors():
+    from paper_2311_16019_gb300.spk import SpkError, SPK_ERR_ARG
+    P = I.workload("lap16_r1")
+    with pytest.raises(SpkError) as e:
+        spk().solve(P.A, P.BT, P.C1, P.C2, k=2, s=10, maxit=20)   # s < (maxit+1) r
+    assert e.value.code == SPK_ERR_ARG
+    with pytest.raises(SpkError):
+        spk().solve(P.A, P.BT, P.C1, P.C2, k=0, s=100, maxit=20)
+    with pytest.raises(SpkError):
+        spk().solve(P.A, P.BT, np.ones((P.n1, 5)), np.ones((P.n2, 5)), k=2, s=200, maxit=20)
+
+
+@pytest.mark.parametrize("flag,code", [(1, -6), (2, -4), (8, -5), (4, -8)])
+def test_fault_injection_statuses(flag, code):
+    from paper_2311_16019_gb300.spk import SpkError
+    P = I.workload("cd2d_24_r2")
+    with pytest.raises(SpkError) as e:
+        spk().solve(P.A, P.BT, P.C1, P.C2, k=2, s=120, maxit=6, p=3, tol=0.0, inject=flag)
+    assert e.value.code == code
+    # the context is still usable afterwards
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=2, s=120, maxit=6, p=3, tol=0.0, fixed_d=6)
+    assert g.rank > 0
+
+
+def test_adaptive_schedule_converges():
+    P = I.workload("lap32_r1")
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=2, s=600, maxit=300, p=1, tol=1e-8, seed=0,
+                    check="adaptive")
+    assert g.converged and len(g.hist_d) < 20
+    assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 3e-8
