@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the s-PKSM solver (libspk) on GB300.
+
+Metric: solves per second to relative residual 1e-8 (rho / ||beta1 beta2^T||
+< 1e-8, the stopping test of Algorithm 1) on the 2-D convection-diffusion
+workload: A = -Lap + 10 (x, y).grad, B = -Lap + 10 (y, -x).grad, upwind
+5-point stencil on a 512 x 512 grid (n = 262144, CSR), r = 4, k = 4, C1, C2
+i.i.d. N(0,1) (seed 1), sketch s = 12000 rows (2 x the maximal basis size
+r * maxit), maxit = 1500, checks every p = 20 iterations on the adaptive
+schedule.  Both the FP64 form (the JSON `value`) and the mixed form (FP32
+basis and SpMM, FP64 whitening / projected solve / residual) are timed.
+
+One step = one whole solve (every step of the hot path: basis, sketch,
+whitening, projected solves, truncation, two-pass recovery) from
+device-resident inputs.  `e2e` repeats the measurement through the public
+API with pinned host buffers: the host->device copy of the CSR operators and
+C1, C2 and the device->host copy of X1, X2 are inside the timed region.
+
+N > 1 (torchrun): every rank solves its own replica (the method has no
+data-parallel exchange; replicas only) and `value` = all ranks' solves / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "cd2d_512_r4"
+SOLVER = dict(k=4, s=12000, maxit=1500, p=20, tol=1e-8, seed=0, check="adaptive",
+              trunc_tol=1e-12)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="spk", choices=["spk", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--maxit", type=int, default=SOLVER["maxit"])
+    ap.add_argument("--s", type=int, default=SOLVER["s"])
+    ap.add_argument("--forms", default="fp64,mixed_fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-iters", type=int, default=40)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------- helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), d.get("bf16_tflops"), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, value: float) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def pick_roofline(prof: dict, hbm_gbs: float, fp64_tflops: float):
+    """Dominant family by GPU time; bound by its algorithmic intensity."""
+    if not prof:
+        return None, {}
+    fam = max(prof, key=lambda k: prof[k]["ms"])
+    p = prof[fam]
+    ms_per_launch_group = p["ms"] / max(1, p["groups"])
+    secs = p["ms"] * 1e-3
+    balance = fp64_tflops * 1e12 / (hbm_gbs * 1e9)   # flop per byte
+    intensity = p["flops"] / max(p["bytes"], 1.0)
+    if intensity > balance:
+        achieved = p["flops"] / secs / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
+                "frac": achieved / fp64_tflops}
+    else:
+        achieved = p["bytes"] / secs / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": achieved / hbm_gbs}
+    roof.update({"kernel": fam, "traffic": None, "launches": p["launches"],
+                 "avg_launch_ms": p["ms"] / max(1, p["launches"]),
+                 "avg_group_ms": ms_per_launch_group,
+                 "algorithmic_bytes_per_launch": p["bytes"] / max(1, p["launches"]),
+                 "algorithmic_flops_per_launch": p["flops"] / max(1, p["launches"])})
+    table = {k: {"ms": round(v["ms"], 3), "share": round(v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values())), 4),
+                 "launches": v["launches"],
+                 "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
+                 "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4)}
+             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]) if v["ms"] > 0}
+    return roof, table
+
+
+# --------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(P, opts, iters: int, hist_d, r: int):
+    """Time the oracle (FP64 NumPy/SciPy, as it stands) on a bounded sample of
+    the workload and extrapolate to one full solve with the GPU's schedule.
+
+    Sample: `iters` Arnoldi + sketch + whitening iterations of the oracle
+    (per-iteration times fitted by a + b d, since the whitening cost grows
+    with d) and one projected Sylvester solve at d = iters (cost scaled by
+    (m / m0)^3).  Full solve = sum over d <= D of (a + b d) + sum over the
+    GPU run's check iterations of the scaled projected-solve time.
+    """
+    import numpy as np
+    import scipy.linalg as sl
+    from oracle import spkms as SP
+
+    U = SP._init_side(P.A, P.C1, opts["k"], SP.Sketch(P.n1, opts["s"], opts["seed"], 0), False)
+    V = SP._init_side(P.BT, P.C2, opts["k"], SP.Sketch(P.n2, opts["s"], opts["seed"], 1), False)
+    ts = []
+    t_all = time.perf_counter()
+    for d in range(1, iters + 1):
+        t0 = time.perf_counter()
+        SP._arnoldi_step(U, d)
+        SP._arnoldi_step(V, d)
+        ts.append(time.perf_counter() - t0)
+    m0 = iters * r
+    Ht, _ = SP.projected_matrix(U, iters)
+    Gt, _ = SP.projected_matrix(V, iters)
+    F = np.zeros((m0, m0))
+    F[:r, :r] = U.beta @ V.beta.T
+    t0 = time.perf_counter()
+    sl.solve_sylvester(Ht, Gt.T, F)
+    tproj = time.perf_counter() - t0
+    sample_s = time.perf_counter() - t_all
+    dd = np.arange(1, iters + 1, dtype=np.float64)
+    b, a = np.polyfit(dd, np.array(ts), 1)
+    D = max(hist_d) if hist_d else iters
+    t_iters = a * D + b * D * (D + 1) / 2.0
+    t_checks = sum(tproj * ((c * r) / m0) ** 3 for c in (hist_d or [D]))
+    total = t_iters + t_checks
+    return {"solves_per_s": 1.0 / total, "seconds_per_solve": total, "sample_seconds": sample_s,
+            "iters_sampled": iters, "extrapolated_to_d": int(D), "checks": len(hist_d or [D]),
+            "t_iter_first_last": [float(ts[0]), float(ts[-1])], "t_proj_m0": tproj, "m0": m0}
+
+
+# --------------------------------------------------------------------- main arms
+def run_reference(args, rank, world, pg):
+    if rank != 0:
+        return
+    from paper_2311_16019_gb300 import inputs as I
+    P = I.workload(args.workload)
+    opts = dict(SOLVER, s=args.s, maxit=args.maxit)
+    # schedule to extrapolate to: the oracle's own convergence is unknown at
+    # this size, so use the checks of a geometric schedule up to the GPU's
+    # typical stopping iteration for this workload (1100 for 512^2, r = 4).
+    D = {"cd2d_512_r4": 1100}.get(args.workload, 300)
+    hist = [20 * 2 ** i for i in range(8) if 20 * 2 ** i < D] + [D]
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        res = oracle_sample(P, opts, args.cpu_sample_iters, hist, P.r)
+        if step >= args.warmup:
+            times.append(res["solves_per_s"])
+    value = statistics.median(times)
+    line = {"impl": "reference", "metric": "solves/s to rel. residual 1e-8 (FP64)",
+            "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, **opts},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": f"{args.cpu_sample_iters} oracle "
+                             f"iterations + one projected solve per step, extrapolated to d={D}"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_spk(args, rank, world, local, pg):
+    import numpy as np
+    import torch
+    from paper_2311_16019_gb300 import build, inputs as I, spk
+
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    barrier(pg)
+    spk.load()
+    P = I.workload(args.workload)
+    opts = dict(SOLVER, s=args.s, maxit=args.maxit)
+    dA, dB = spk.DeviceCSR(P.A), spk.DeviceCSR(P.BT)
+    c1 = torch.as_tensor(P.C1, device="cuda")
+    c2 = torch.as_tensor(P.C2, device="cuda")
+    hbm, bf16, peak_src = measured_peaks()
+    fp64 = spk.fp64_peak(local)
+    forms = [f for f in args.forms.split(",") if f]
+    per_form = {}
+    sampler = ClockSampler(local)
+    first = None
+    for form in forms:
+        last = None
+        for _ in range(args.warmup):
+            last = spk.solve(dA, dB, c1, c2, precision=form, device=local, **opts)
+        torch.cuda.synchronize()
+        barrier(pg)
+        spk.profile_enable(form == forms[0], local)
+        launches0 = spk.launch_count()
+        if form == forms[0]:
+            sampler.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier(pg)
+        ev0.record()
+        results = []
+        for _ in range(args.steps):
+            results.append(spk.solve(dA, dB, c1, c2, precision=form, device=local, **opts))
+        ev1.record()
+        torch.cuda.synchronize()
+        barrier(pg)
+        ms = ev0.elapsed_time(ev1)
+        launches = spk.launch_count() - launches0
+        clocks = sampler.stop() if form == forms[0] else None
+        prof = spk.profile_read(local) if form == forms[0] else None
+        spk.profile_enable(False, local)
+        ms_max = max_over_ranks(pg, ms)
+        g = results[-1]
+        X1, X2 = g.X1.cpu().numpy(), g.X2.cpu().numpy()
+        from oracle import measure as M
+        tres = M.true_residual(P.A, P.B, P.C1, P.C2, X1, X2)
+        per_form[form] = dict(ms_per_step=ms_max / args.steps,
+                              solves_per_s=world * args.steps / (ms_max * 1e-3),
+                              iters=g.iters, rank=g.rank, converged=g.converged,
+                              rel_rho=g.rel_rho, true_rel_residual=tres, checks=g.hist_d,
+                              ms_phases=dict(arnoldi=g.ms_arnoldi, project=g.ms_project,
+                                             recover=g.ms_recover),
+                              gpu_launches=launches, clocks=clocks, prof=prof, X=(X1, X2))
+        if first is None:
+            first = form
+    base = per_form[first]
+    # error of the mixed form against the FP64 GPU form
+    from oracle import measure as M
+    for f, v in per_form.items():
+        if f != first:
+            v["rel_err_vs_fp64"] = M.rel_error(v["X"][0], v["X"][1], base["X"][0], base["X"][1])
+    # end-to-end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hostA = [torch.as_tensor(a).pin_memory() for a in
+                 (P.A.indptr, P.A.indices, P.A.data, P.BT.indptr, P.BT.indices, P.BT.data)]
+        hostC = [torch.as_tensor(P.C1).pin_memory(), torch.as_tensor(P.C2).pin_memory()]
+        h2d = sum(t.numel() * t.element_size() for t in hostA + hostC)
+        d2h = 0
+        torch.cuda.synchronize()
+        barrier(pg)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            dev = [t.to("cuda", non_blocking=True) for t in hostA + hostC]
+            A_ = spk.DeviceCSR.__new__(spk.DeviceCSR)
+            A_.shape, A_.rowptr, A_.col, A_.val = P.A.shape, dev[0], dev[1], dev[2]
+            A_.c = spk.Csr(P.n1, P.n1, P.A.nnz, dev[0].data_ptr(), dev[1].data_ptr(), dev[2].data_ptr())
+            B_ = spk.DeviceCSR.__new__(spk.DeviceCSR)
+            B_.shape, B_.rowptr, B_.col, B_.val = P.BT.shape, dev[3], dev[4], dev[5]
+            B_.c = spk.Csr(P.n2, P.n2, P.BT.nnz, dev[3].data_ptr(), dev[4].data_ptr(), dev[5].data_ptr())
+            g = spk.solve(A_, B_, dev[6], dev[7], precision=first, device=local, **opts)
+            o1 = torch.empty(g.X1.shape, dtype=torch.float64).pin_memory()
+            o2 = torch.empty(g.X2.shape, dtype=torch.float64).pin_memory()
+            o1.copy_(g.X1, non_blocking=True)
+            o2.copy_(g.X2, non_blocking=True)
+            d2h = o1.numel() * 8 + o2.numel() * 8
+        torch.cuda.synchronize()
+        barrier(pg)
+        secs = max_over_ranks(pg, time.perf_counter() - t0)
+        e2e = {"value": world * args.steps / secs, "unit": "solves/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    roof, table = pick_roofline(base["prof"] or {}, hbm, fp64)
+    if roof is not None:
+        roof["peak_source"] = f"{peak_src} (HBM GB/s from MEASURED_PEAKS.json); FP64 TFLOP/s measured live"
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        s = oracle_sample(P, opts, args.cpu_sample_iters, base["checks"], P.r)
+        cpu = {"value": s["solves_per_s"], "unit": "solves/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": (f"{s['iters_sampled']} oracle iterations ({s['sample_seconds']:.1f} s) "
+                          f"+ one projected solve at m={s['m0']}, extrapolated to d={s['extrapolated_to_d']} "
+                          f"with the GPU run's {s['checks']} checks (a + b d per iteration, m^3 per check)")}
+    if rank == 0:
+        forms_out = {f: {k: v for k, v in d.items() if k not in ("X", "prof", "clocks")}
+                     for f, d in per_form.items()}
+        line = {
+            "metric": "solves/s to rel. residual 1e-8 (FP64 form; mixed form beside it)",
+            "value": base["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if first == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": P.n1, "nnz": int(P.A.nnz), "r": P.r,
+                       **{k: v for k, v in opts.items()}, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set (Q, T, H~ > 1 GB) larger than L2; no flush"},
+            "forms": forms_out,
+            "clocks": base["clocks"], "gpu_launches": base["gpu_launches"],
+            "e2e": e2e, "roofline": roof, "kernels": table, "fp64_tflops_measured": fp64,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local, pg = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world, pg)
+    else:
+        run_spk(args, rank, world, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

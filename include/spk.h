@@ -174,12 +174,33 @@ int spk_sylvester_dense(spk_handle* h, int32_t m, const double* H_dev,
                         const double* G_dev, const double* F_dev, double* Y_dev,
                         int32_t* newton_iters_host, void* stream);
 
+/* ---- measurement --------------------------------------------------------
+ * spk_launch_count: number of CUDA kernel launches issued by the library
+ * since it was loaded (all handles).                                      */
+int64_t spk_launch_count(void);
+/* spk_profile_enable: turn per-family timing on/off for this handle and reset
+ * the counters.  When on, CUDA events are recorded on the launching stream
+ * around every group of launches of a kernel family; spk_profile_read
+ * returns, for family index 0..14 (SPK_ERR_ARG beyond), its name, total GPU
+ * milliseconds, kernel launches, timed groups, and the ALGORITHMIC bytes and
+ * flops of those launches (the minimum the step must move/compute).      */
+int spk_profile_enable(spk_handle* h, int on);
+int spk_profile_read(spk_handle* h, int family, const char** name, double* ms,
+                     int64_t* launches, int64_t* groups, double* bytes, double* flops);
+/* spk_fp64_peak: measured FP64 FMA rate of the handle's device (TFLOP/s),
+ * from a kernel of independent FMA chains on every SM (no paper counterpart;
+ * the denominator of the FP64-ALU roofline).                              */
+int spk_fp64_peak(spk_handle* h, double* tflops, void* stream);
+
 /* Copy an internal FP64 buffer of the handle's last solve to the host, for
  * element-wise parity tests of single steps: "U_T"/"V_T" (whitening factors
  * T_U, T_V, (maxit+1) r square, column-major), "U_Ht"/"V_Ht" (projected
  * matrices H~, G~, same layout), "U_hband"/"V_hband" (Hessenberg blocks:
  * per iteration d, k+1 blocks r x r row-major; block q is h_{d-k+1+q, d},
- * block k is h_{d+1,d}), "U_beta"/"V_beta" (r x r).  count = doubles wanted;
+ * block k is h_{d+1,d}), "U_beta"/"V_beta" (r x r), "pj_F" (the projected
+ * solution Y of the last check, m x m column-major), "tr_Y1"/"tr_Y2" (the
+ * recovery coefficients W1 = T_U^{-1} Y1, W2 = T_V^{-1} Y2, m x rank
+ * column-major).  count = doubles wanted;
  * *avail_out receives the buffer's size in doubles.  SPK_ERR_ARG if the
  * name is unknown.                                                        */
 int spk_inspect(spk_handle* h, const char* name, double* dst_host, int64_t count,

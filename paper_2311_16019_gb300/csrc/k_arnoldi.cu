@@ -345,6 +345,7 @@ void spmm_dots_launch(const int32_t* rowptr, const int32_t* col, const TV* val, 
   g0.nwin = std::min(win.nwin, kFuse);
   const bool dots = win.nwin > 0;
 #define SPK_SPMM(RR)                                                                           \
+  count_launches(1);                                                                           \
   if (dots)                                                                                    \
     k_spmm_dots<TB, TC, TV, RR, true><<<grid, 256, 0, st>>>(rowptr, col, val, n, U, W, g0, partial); \
   else                                                                                         \
@@ -362,16 +363,17 @@ void spmm_dots_launch(const int32_t* rowptr, const int32_t* col, const TV* val, 
     for (int q = 0; q < gw.nwin; ++q) gw.blk[q] = win.blk[g + q];
     double* part = partial + (int64_t)(g / kFuse) * grid * kFuse * r * r;
     switch (r) {
-      case 1: k_dots<TB, TC, 1><<<grid, 256, 0, st>>>(W, n, gw, part); break;
-      case 2: k_dots<TB, TC, 2><<<grid, 256, 0, st>>>(W, n, gw, part); break;
-      case 3: k_dots<TB, TC, 3><<<grid, 256, 0, st>>>(W, n, gw, part); break;
-      default: k_dots<TB, TC, 4><<<grid, 256, 0, st>>>(W, n, gw, part); break;
+      case 1: count_launches(1); k_dots<TB, TC, 1><<<grid, 256, 0, st>>>(W, n, gw, part); break;
+      case 2: count_launches(1); k_dots<TB, TC, 2><<<grid, 256, 0, st>>>(W, n, gw, part); break;
+      case 3: count_launches(1); k_dots<TB, TC, 3><<<grid, 256, 0, st>>>(W, n, gw, part); break;
+      default: count_launches(1); k_dots<TB, TC, 4><<<grid, 256, 0, st>>>(W, n, gw, part); break;
     }
   }
 }
 
 void reduce_partials_launch(const double* partial, int nparts, int stride, int count,
                             double* out, cudaStream_t st) {
+  count_launches(1);
   k_reduce_partials<<<(count + 127) / 128, 128, 0, st>>>(partial, nparts, stride, count, out);
 }
 
@@ -379,15 +381,16 @@ template <typename TB, typename TC>
 void update_gram_launch(TC* W, int64_t n, int r, WindowPtrs win, const double* h, double* partial,
                         int grid, int want_gram, cudaStream_t st) {
   switch (r) {
-    case 1: k_update_gram<TB, TC, 1><<<grid, 256, 0, st>>>(W, n, win, h, partial, want_gram); break;
-    case 2: k_update_gram<TB, TC, 2><<<grid, 256, 0, st>>>(W, n, win, h, partial, want_gram); break;
-    case 3: k_update_gram<TB, TC, 3><<<grid, 256, 0, st>>>(W, n, win, h, partial, want_gram); break;
-    default: k_update_gram<TB, TC, 4><<<grid, 256, 0, st>>>(W, n, win, h, partial, want_gram); break;
+    case 1: count_launches(1); k_update_gram<TB, TC, 1><<<grid, 256, 0, st>>>(W, n, win, h, partial, want_gram); break;
+    case 2: count_launches(1); k_update_gram<TB, TC, 2><<<grid, 256, 0, st>>>(W, n, win, h, partial, want_gram); break;
+    case 3: count_launches(1); k_update_gram<TB, TC, 3><<<grid, 256, 0, st>>>(W, n, win, h, partial, want_gram); break;
+    default: count_launches(1); k_update_gram<TB, TC, 4><<<grid, 256, 0, st>>>(W, n, win, h, partial, want_gram); break;
   }
 }
 
 void chol_small_launch(const double* partial, int nparts, int r, double* R, double* Rinv,
                        uint32_t* flags, double rel_floor, cudaStream_t st) {
+  count_launches(1);
   k_chol_small<<<1, 32, 0, st>>>(partial, nparts, r, R, Rinv, flags, rel_floor);
 }
 
@@ -395,10 +398,10 @@ template <typename TC>
 void scale_gram_launch(TC* W, int64_t n, int r, const double* Rinv, double* partial, int grid,
                        cudaStream_t st) {
   switch (r) {
-    case 1: k_scale_gram<TC, 1><<<grid, 256, 0, st>>>(W, n, Rinv, partial); break;
-    case 2: k_scale_gram<TC, 2><<<grid, 256, 0, st>>>(W, n, Rinv, partial); break;
-    case 3: k_scale_gram<TC, 3><<<grid, 256, 0, st>>>(W, n, Rinv, partial); break;
-    default: k_scale_gram<TC, 4><<<grid, 256, 0, st>>>(W, n, Rinv, partial); break;
+    case 1: count_launches(1); k_scale_gram<TC, 1><<<grid, 256, 0, st>>>(W, n, Rinv, partial); break;
+    case 2: count_launches(1); k_scale_gram<TC, 2><<<grid, 256, 0, st>>>(W, n, Rinv, partial); break;
+    case 3: count_launches(1); k_scale_gram<TC, 3><<<grid, 256, 0, st>>>(W, n, Rinv, partial); break;
+    default: count_launches(1); k_scale_gram<TC, 4><<<grid, 256, 0, st>>>(W, n, Rinv, partial); break;
   }
 }
 
@@ -407,10 +410,10 @@ void scale_store_launch(const TC* W, int64_t n, int r, const double* Rinv, TB* d
                         cudaStream_t st) {
   const int grid = default_grid(n);
   switch (r) {
-    case 1: k_scale_store<TB, TC, 1><<<grid, 256, 0, st>>>(W, n, Rinv, dst); break;
-    case 2: k_scale_store<TB, TC, 2><<<grid, 256, 0, st>>>(W, n, Rinv, dst); break;
-    case 3: k_scale_store<TB, TC, 3><<<grid, 256, 0, st>>>(W, n, Rinv, dst); break;
-    default: k_scale_store<TB, TC, 4><<<grid, 256, 0, st>>>(W, n, Rinv, dst); break;
+    case 1: count_launches(1); k_scale_store<TB, TC, 1><<<grid, 256, 0, st>>>(W, n, Rinv, dst); break;
+    case 2: count_launches(1); k_scale_store<TB, TC, 2><<<grid, 256, 0, st>>>(W, n, Rinv, dst); break;
+    case 3: count_launches(1); k_scale_store<TB, TC, 3><<<grid, 256, 0, st>>>(W, n, Rinv, dst); break;
+    default: count_launches(1); k_scale_store<TB, TC, 4><<<grid, 256, 0, st>>>(W, n, Rinv, dst); break;
   }
 }
 
@@ -418,26 +421,31 @@ template <typename TB>
 void x_accumulate_launch(double* X, int64_t n, int ell, int r, WindowPtrs blocks,
                          const double* Wrows, int64_t ldw, cudaStream_t st) {
   if (ell <= 0 || blocks.nwin <= 0) return;
+  count_launches(1);
   k_x_accumulate<TB><<<default_grid(n * ell), 256, 0, st>>>(X, n, ell, r, blocks, Wrows, ldw);
 }
 
 void spmm_wide_launch(const int32_t* rowptr, const int32_t* col, const double* val, int64_t n,
                       int w, const double* X, double* Y, cudaStream_t st) {
   if (w <= 0 || n <= 0) return;
+  count_launches(1);
   k_spmm_wide<<<default_grid(n * w), 256, 0, st>>>(rowptr, col, val, n, w, X, Y);
 }
 
 template <typename TV>
 void convert_values_launch(const double* src, TV* dst, int64_t count, cudaStream_t st) {
+  count_launches(1);
   k_convert<TV><<<default_grid(count), 256, 0, st>>>(src, dst, count);
 }
 template <typename TB>
 void convert_block_launch(const double* src, TB* dst, int64_t count, cudaStream_t st) {
+  count_launches(1);
   k_convert<TB><<<default_grid(count), 256, 0, st>>>(src, dst, count);
 }
 
 void combine_small_launch(const double* A, const double* B, double* C, int r, int mode,
                           cudaStream_t st) {
+  count_launches(1);
   k_combine_small<<<1, 32, 0, st>>>(A, B, C, r, mode);
 }
 

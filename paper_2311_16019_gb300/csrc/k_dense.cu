@@ -415,6 +415,21 @@ __global__ void k_trace_product(const double* __restrict__ A, const double* __re
   }
 }
 
+// FP64 FMA throughput probe: 8 independent dependency chains per thread.
+__global__ void __launch_bounds__(256) k_fp64_fma(double* out, int iters, double b, double c) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = threadIdx.x * 1e-3 + k;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == 12345.678) out[0] = s;  // keeps the chains live
+}
+
 int grid_for(int64_t work, int block) {
   int64_t g = (work + block - 1) / block;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
@@ -426,30 +441,37 @@ void gemm_f64(char ta, char tb, int M, int N, int K, double alpha, const double*
               const double* B, int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st) {
   if (M <= 0 || N <= 0) return;
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  count_launches(1);
   k_gemm<<<grid, 256, 0, st>>>(ta == 'T', tb == 'T', M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
 void copy_matrix_launch(const double* A, int64_t lda, double* B, int64_t ldb, int M, int N,
                         cudaStream_t st) {
   if (M <= 0 || N <= 0) return;
+  count_launches(1);
   k_copy_matrix<<<grid_for((int64_t)M * N, 256), 256, 0, st>>>(A, lda, B, ldb, M, N);
 }
 
 void set_zero_launch(double* A, int64_t count, cudaStream_t st) {
   if (count <= 0) return;
+  count_launches(1);
   k_set_zero<<<grid_for(count, 256), 256, 0, st>>>(A, count);
 }
 
 void scale_matrix_launch(double* A, int64_t ld, int M, int N, double a, cudaStream_t st) {
   if (M <= 0 || N <= 0) return;
+  count_launches(1);
   k_scale_matrix<<<grid_for((int64_t)M * N, 256), 256, 0, st>>>(A, ld, M, N, a);
 }
 
 void gje_invert(double* A, int64_t lda, int m, GjeState gs, cudaStream_t st) {
   if (m <= 0) return;
+  count_launches(1);
   k_gje_first<<<1, kGjeThreads, 0, st>>>(A, lda, m, gs);
   const int blocks = (m + kGjeCols - 1) / kGjeCols;
+  count_launches(m);
   for (int j = 0; j < m; ++j) k_gje_step<<<blocks, kGjeThreads, 0, st>>>(A, lda, m, j, gs);
+  count_launches(1);
   k_gje_colperm<<<grid_for(m, 128), 128, 0, st>>>(A, lda, m, gs.ipiv);
 }
 
@@ -457,41 +479,69 @@ int sign_combine_grid(int m) { return grid_for((int64_t)m * m, 256) > 304 ? 304 
 
 void sign_combine_launch(double* Hk, const double* Hinv, int64_t ld, int m, double c,
                          double* partial, int grid, cudaStream_t st) {
+  count_launches(1);
   k_sign_combine<<<grid, 256, 0, st>>>(Hk, Hinv, ld, m, c, partial);
 }
 
 void trsm_upper_left_launch(const double* T, int64_t ldT, int m, double* X, int64_t ldX, int ncol,
                             cudaStream_t st) {
   if (ncol <= 0 || m <= 0) return;
+  count_launches(1);
   k_trsm_upper_left<<<ncol, 256, 0, st>>>(T, ldT, m, X, ldX);
 }
 
 void gaussian_fill_launch(double* A, int64_t count, uint64_t seed, cudaStream_t st) {
+  count_launches(1);
   k_gaussian<<<grid_for(count, 256), 256, 0, st>>>(A, count, seed);
 }
 
 void jacobi_round_launch(double* A, int64_t lda, int M, int N, double* V, int64_t ldv,
                          const int* pairs, int npairs, double* offs, cudaStream_t st) {
+  count_launches(1);
   k_jacobi_pair<<<npairs, 256, 0, st>>>(A, lda, M, N, V, ldv, pairs, offs);
 }
 
 void col_norms_launch(const double* A, int64_t lda, int M, int N, double* out, cudaStream_t st) {
   if (N <= 0) return;
+  count_launches(1);
   k_col_norms<<<N, 256, 0, st>>>(A, lda, M, out);
+}
+
+double fp64_fma_probe(int sm_count, double* scratch, cudaStream_t st) {
+  const int blocks = sm_count * 8, iters = 1 << 14;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  count_launches(1);
+  k_fp64_fma<<<blocks, 256, 0, st>>>(scratch, 256, 0.999999, 1e-7);  // warm-up
+  cudaEventRecord(a, st);
+  count_launches(1);
+  k_fp64_fma<<<blocks, 256, 0, st>>>(scratch, iters, 0.999999, 1e-7);
+  cudaEventRecord(b, st);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  const double flops = 2.0 * 8.0 * iters * (double)blocks * 256.0;
+  return flops / (ms * 1e-3) / 1e12;
 }
 
 void select_sv_launch(const double* sigma, int N, double tol, int* idx, double* f1, double* f2,
                       int* ell_out, cudaStream_t st) {
+  count_launches(1);
   k_select_sv<<<1, 256, 0, st>>>(sigma, N, tol, idx, f1, f2, ell_out);
 }
 
 void gather_cols_launch(const double* A, int64_t lda, int M, const int* idx, const double* f,
                         int ncols, double* out, int64_t ldo, cudaStream_t st) {
   if (ncols <= 0 || M <= 0) return;
+  count_launches(1);
   k_gather_cols<<<grid_for((int64_t)M * ncols, 256), 256, 0, st>>>(A, lda, M, idx, f, ncols, out, ldo);
 }
 
 double trace_product(const double* A, const double* B, int n, double* scratch, cudaStream_t st) {
+  count_launches(1);
   k_trace_product<<<1, 256, 0, st>>>(A, B, n, scratch);
   double h = 0.0;
   cudaMemcpyAsync(&h, scratch, sizeof(double), cudaMemcpyDeviceToHost, st);

@@ -226,29 +226,34 @@ void border_col_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, 
                        const double* hslots, int first_block, int nslots, const double* h_dd,
                        cudaStream_t st) {
   if (mp <= 0) return;
+  count_launches(1);
   k_border_col<<<(mp + 127) / 128, 128, 0, st>>>(Ht, ldH, mp, r, T, ldT, hslots, first_block,
                                                  nslots, h_dd);
 }
 
 void border_small_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, int64_t ldT,
                          const double* h_sub, const double* h_dd, cudaStream_t st) {
+  count_launches(1);
   k_border_small<<<1, 32, 0, st>>>(Ht, ldH, mp, r, T, ldT, h_sub, h_dd);
 }
 
 void border_correct_launch(double* Ht, int64_t ldH, int m, int r, const double* T, int64_t ldT,
                            const double* h_next, cudaStream_t st) {
+  count_launches(1);
   k_border_correct<<<(m + 127) / 128, 128, 0, st>>>(Ht, ldH, m, r, T, ldT, h_next);
 }
 
 void rho_launch(const double* Y, int64_t ldY, int m, int r, const double* TU, int64_t ldTU,
                 const double* TV, int64_t ldTV, const double* hU, const double* hV,
                 const double* betaU, const double* betaV, double* out3, cudaStream_t st) {
+  count_launches(1);
   k_rho<<<1, 256, 0, st>>>(Y, ldY, m, r, TU, ldTU, TV, ldTV, hU, hV, betaU, betaV, out3);
 }
 
 void fill_rhs_launch(double* F, int64_t ldF, int m, int r, const double* betaU,
                      const double* betaV, cudaStream_t st) {
   (void)m;
+  count_launches(1);
   k_fill_rhs<<<1, 32, 0, st>>>(F, ldF, r, betaU, betaV);
 }
 

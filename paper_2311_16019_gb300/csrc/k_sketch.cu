@@ -196,6 +196,7 @@ int sketch_draws_launch(int64_t n, int32_t s, uint64_t seed, int32_t sketch_id, 
   }
   const uint64_t x0r = seed + (uint64_t)(1 + 2 * sketch_id + 0) * kStream;
   const uint64_t x0s = seed + (uint64_t)(1 + 2 * sketch_id + 1) * kStream;
+  count_launches(1);
   k_sign_draws<<<grid_for(n, 256), 256, 0, st>>>(n, x0s, signs);
   const size_t cap = cand_cap(npad, s);
   if (scratch_bytes < sketch_draws_scratch_bytes(n, s)) {
@@ -214,6 +215,7 @@ int sketch_draws_launch(int64_t n, int32_t s, uint64_t seed, int32_t sketch_id, 
     if (frac >= 1.0) thr = ~0ull;
     else thr = (uint64_t)(frac * 18446744073709551616.0);
     if (cudaMemsetAsync(cnt, 0, sizeof(int32_t), st) != cudaSuccess) return SPK_ERR_CUDA;
+    count_launches(1);
     k_candidates<<<grid_for(npad, 256), 256, 0, st>>>(npad, x0r, thr, (int32_t)cap, cnt, cidx, ckey);
     int32_t hcnt = 0;
     if (cudaMemcpyAsync(&hcnt, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -222,7 +224,9 @@ int sketch_draws_launch(int64_t n, int32_t s, uint64_t seed, int32_t sketch_id, 
     if (hcnt < s) { frac = frac * 1.5 + 1e-12; continue; }
     if ((size_t)hcnt > cap) { frac = frac * 0.8; continue; }
     const int g = grid_for(hcnt, 256);
+    count_launches(1);
     k_rank_keys<<<g, 256, 0, st>>>(cnt, ckey, s, sel);
+    count_launches(1);
     k_place_rows<<<g, 256, 0, st>>>(cnt, cidx, sel, rows);
     return cudaGetLastError() == cudaSuccess ? SPK_OK : SPK_ERR_CUDA;
   }
@@ -265,6 +269,7 @@ template <typename TB, typename TC>
 void sketch_apply_launch(const SketchDev& sk, const TB* X, int r, double* SX, TC* scratch,
                          cudaStream_t st) {
   if (sk.identity) {
+    count_launches(1);
     k_identity_sketch<TB><<<grid_for(sk.n * r, 256), 256, 0, st>>>(X, sk.n, r, sk.scale, SX);
     return;
   }
@@ -276,10 +281,12 @@ void sketch_apply_launch(const SketchDev& sk, const TB* X, int r, double* SX, TC
     attr_set = true;
   }
   int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(32, (int64_t)sk.n2 * r / 2));
+  count_launches(1);
   k_fwht_chunks<TB, TC><<<(unsigned)sk.n1, threads, smem, st>>>(X, sk.n, r, sk.signs, sk.n2,
                                                                  sk.log2n2, sk.n1, scratch);
   const int warps_per_block = 8;
   const int blocks = (sk.s + warps_per_block - 1) / warps_per_block;
+  count_launches(1);
   k_gather_rows<TC><<<blocks, warps_per_block * 32, 0, st>>>(scratch, sk.n1, r, sk.n2, sk.log2n2,
                                                              sk.rows, sk.s, sk.scale, SX);
 }

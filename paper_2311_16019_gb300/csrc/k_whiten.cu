@@ -174,10 +174,10 @@ void qt_dot_launch(const double* Q, int64_t ldq, int64_t s, int m, const double*
   if (m <= 0) return;
   const int blocks = (m + 7) / 8;
   switch (r) {
-    case 1: k_qt_dot<1><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
-    case 2: k_qt_dot<2><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
-    case 3: k_qt_dot<3><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
-    default: k_qt_dot<4><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
+    case 1: count_launches(1); k_qt_dot<1><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
+    case 2: count_launches(1); k_qt_dot<2><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
+    case 3: count_launches(1); k_qt_dot<3><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
+    default: count_launches(1); k_qt_dot<4><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
   }
 }
 
@@ -192,19 +192,27 @@ void q_update_launch(const double* Q, int64_t ldq, int64_t s, int m, const doubl
   const int g2 = grid_for(s, 256);
   switch (r) {
     case 1:
+      count_launches(1);
       k_q_times_t<1><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, t, partial);
+      count_launches(1);
       k_q_update_finish<1><<<g2, 256, 0, st>>>(w_in, w_out, partial, s, nchunk);
       break;
     case 2:
+      count_launches(1);
       k_q_times_t<2><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, t, partial);
+      count_launches(1);
       k_q_update_finish<2><<<g2, 256, 0, st>>>(w_in, w_out, partial, s, nchunk);
       break;
     case 3:
+      count_launches(1);
       k_q_times_t<3><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, t, partial);
+      count_launches(1);
       k_q_update_finish<3><<<g2, 256, 0, st>>>(w_in, w_out, partial, s, nchunk);
       break;
     default:
+      count_launches(1);
       k_q_times_t<4><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, t, partial);
+      count_launches(1);
       k_q_update_finish<4><<<g2, 256, 0, st>>>(w_in, w_out, partial, s, nchunk);
       break;
   }
@@ -214,10 +222,10 @@ int q_update_chunks(int m) { return std::max(1, (m + kColChunk - 1) / kColChunk)
 
 void ts_gram_launch(const double* w, int64_t s, int r, double* partial, int grid, cudaStream_t st) {
   switch (r) {
-    case 1: k_ts_gram<1><<<grid, 256, 0, st>>>(w, s, partial); break;
-    case 2: k_ts_gram<2><<<grid, 256, 0, st>>>(w, s, partial); break;
-    case 3: k_ts_gram<3><<<grid, 256, 0, st>>>(w, s, partial); break;
-    default: k_ts_gram<4><<<grid, 256, 0, st>>>(w, s, partial); break;
+    case 1: count_launches(1); k_ts_gram<1><<<grid, 256, 0, st>>>(w, s, partial); break;
+    case 2: count_launches(1); k_ts_gram<2><<<grid, 256, 0, st>>>(w, s, partial); break;
+    case 3: count_launches(1); k_ts_gram<3><<<grid, 256, 0, st>>>(w, s, partial); break;
+    default: count_launches(1); k_ts_gram<4><<<grid, 256, 0, st>>>(w, s, partial); break;
   }
 }
 
@@ -225,15 +233,16 @@ void ts_scale_launch(double* w, int64_t s, int r, const double* Rinv, double* ou
                      cudaStream_t st) {
   const int g = grid_for(s, 256);
   switch (r) {
-    case 1: k_ts_scale<1><<<g, 256, 0, st>>>(w, s, Rinv, out, ldo); break;
-    case 2: k_ts_scale<2><<<g, 256, 0, st>>>(w, s, Rinv, out, ldo); break;
-    case 3: k_ts_scale<3><<<g, 256, 0, st>>>(w, s, Rinv, out, ldo); break;
-    default: k_ts_scale<4><<<g, 256, 0, st>>>(w, s, Rinv, out, ldo); break;
+    case 1: count_launches(1); k_ts_scale<1><<<g, 256, 0, st>>>(w, s, Rinv, out, ldo); break;
+    case 2: count_launches(1); k_ts_scale<2><<<g, 256, 0, st>>>(w, s, Rinv, out, ldo); break;
+    case 3: count_launches(1); k_ts_scale<3><<<g, 256, 0, st>>>(w, s, Rinv, out, ldo); break;
+    default: count_launches(1); k_ts_scale<4><<<g, 256, 0, st>>>(w, s, Rinv, out, ldo); break;
   }
 }
 
 void t_write_launch(double* T, int64_t ldT, int m, int r, const double* t1, const double* t2,
                     const double* tau, cudaStream_t st) {
+  count_launches(1);
   k_t_write<<<grid_for((int64_t)(m + r) * r, 256), 256, 0, st>>>(T, ldT, m, r, t1, t2, tau);
 }
 

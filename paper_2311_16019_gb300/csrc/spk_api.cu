@@ -26,9 +26,70 @@
 
 using namespace spk;
 
+#include <atomic>
+namespace spk {
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace spk
+
 struct Buf {
   void* p = nullptr;
   size_t bytes = 0;
+};
+
+// Kernel families timed by the optional profiler (CUDA events recorded on
+// the launching stream around each group of launches).
+enum ProfFam {
+  F_SPMM, F_UPDATE, F_SCALE, F_SKETCH, F_QTDOT, F_QUPDATE, F_TSQR, F_BORDER,
+  F_GJE, F_GEMM, F_SIGNCOMB, F_RHO, F_TRUNC, F_TRSM, F_XACC, F_COUNT
+};
+static const char* kFamNames[F_COUNT] = {
+  "spmm_dots", "gs_update", "cholqr_scale", "sketch_srht", "whiten_qt_dot", "whiten_q_update",
+  "whiten_cholqr", "border_update", "gje_step", "gemm_f64", "sign_combine", "rho", "truncate_svd",
+  "trsm", "x_accumulate"};
+
+struct ProfAcc {
+  double ms = 0, bytes = 0, flops = 0;
+  int64_t launches = 0, groups = 0;
+};
+
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> free_ev;
+  struct Pending { int f; cudaEvent_t a, b; int64_t launches; double bytes, flops; };
+  std::vector<Pending> pend;
+  ProfAcc acc[F_COUNT];
+  cudaEvent_t get() {
+    if (free_ev.empty()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      return e;
+    }
+    cudaEvent_t e = free_ev.back();
+    free_ev.pop_back();
+    return e;
+  }
+  void resolve() {
+    for (auto& p : pend) {
+      cudaEventSynchronize(p.b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, p.a, p.b);
+      auto& a = acc[p.f];
+      a.ms += ms;
+      a.bytes += p.bytes;
+      a.flops += p.flops;
+      a.launches += p.launches;
+      a.groups += 1;
+      free_ev.push_back(p.a);
+      free_ev.push_back(p.b);
+    }
+    pend.clear();
+  }
+  ~Profiler() {
+    for (auto e : free_ev) cudaEventDestroy(e);
+    for (auto& p : pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  }
 };
 
 struct spk_handle {
@@ -38,7 +99,34 @@ struct spk_handle {
   std::map<std::string, Buf> bufs;
   uint32_t* flags = nullptr;
   double host_wait_s = 600.0;
+  Profiler prof;
 };
+
+namespace {
+// RAII timing of one group of launches of one family.
+struct ProfScope {
+  spk_handle* h;
+  int f;
+  cudaStream_t st;
+  int64_t launches;
+  double bytes, flops;
+  cudaEvent_t a = nullptr;
+  ProfScope(spk_handle* h_, int f_, cudaStream_t st_, int64_t l, double by, double fl)
+      : h(h_), f(f_), st(st_), launches(l), bytes(by), flops(fl) {
+    if (h->prof.on) {
+      a = h->prof.get();
+      cudaEventRecord(a, st);
+    }
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = h->prof.get();
+    cudaEventRecord(b, st);
+    h->prof.pend.push_back({f, a, b, launches, bytes, flops});
+    if (h->prof.pend.size() > 8192) h->prof.resolve();
+  }
+};
+}  // namespace
 
 namespace {
 
@@ -162,10 +250,14 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
   for (it = 0; it < max_newton; ++it) {
     CK(cudaMemcpyAsync(Hinv, Hk, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(Ginv, Gk, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
-    GjeState gh{ipiv, cvec, scalH, h->flags};
-    gje_invert(Hinv, m, m, gh, st);
-    GjeState gg{ipiv, cvec, scalG, h->flags};
-    gje_invert(Ginv, m, m, gg, st);
+    {
+      const double mm2 = (double)m * m;
+      ProfScope ps(h, F_GJE, st, 2 * (m + 2), 2 * 16.0 * mm2 * m, 2 * 2.0 * mm2 * m);
+      GjeState gh{ipiv, cvec, scalH, h->flags};
+      gje_invert(Hinv, m, m, gh, st);
+      GjeState gg{ipiv, cvec, scalG, h->flags};
+      gje_invert(Ginv, m, m, gg, st);
+    }
     double ld[2] = {0, 0};
     CK(cudaMemcpyAsync(&ld[0], scalH, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&ld[1], scalG, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -183,10 +275,18 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
       if (!std::isfinite(c) || c <= 0.0) c = 1.0;
     }
     // F <- (c/2) F + (1/(2c)) (H^{-1} F) G^{-T}
-    gemm_f64('N', 'N', m, m, m, 1.0, Hinv, m, F, m, 0.0, P, m, st);
-    gemm_f64('N', 'T', m, m, m, 0.5 / c, P, m, Ginv, m, 0.5 * c, F, m, st);
-    sign_combine_launch(Hk, Hinv, m, m, c, part, sgrid, st);
-    sign_combine_launch(Gk, Ginv, m, m, c, part + 2 * sgrid, sgrid, st);
+    {
+      const double mm2 = (double)m * m;
+      ProfScope ps(h, F_GEMM, st, 2, 7 * 8.0 * mm2, 4.0 * mm2 * m);
+      gemm_f64('N', 'N', m, m, m, 1.0, Hinv, m, F, m, 0.0, P, m, st);
+      gemm_f64('N', 'T', m, m, m, 0.5 / c, P, m, Ginv, m, 0.5 * c, F, m, st);
+    }
+    {
+      const double mm2 = (double)m * m;
+      ProfScope ps(h, F_SIGNCOMB, st, 2, 2 * 3 * 8.0 * mm2, 2 * 3.0 * mm2);
+      sign_combine_launch(Hk, Hinv, m, m, c, part, sgrid, st);
+      sign_combine_launch(Gk, Ginv, m, m, c, part + 2 * sgrid, sgrid, st);
+    }
     CK(cudaMemcpyAsync(hpart.data(), part, sizeof(double) * 4 * sgrid, cudaMemcpyDeviceToHost, st));
     TRY(wait_stream(h, st, h->host_wait_s));
     double dH = 0, nH = 0, dG = 0, nG = 0;
@@ -251,7 +351,7 @@ int jacobi_svd(spk_handle* h, double* A, int64_t lda, int M, int N, double* V, c
     TRY(wait_stream(h, st, h->host_wait_s));
   }
   std::vector<double> hoffs((size_t)rounds * npairs);
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  for (int sweep = 0; sweep < 30; ++sweep) {
     for (int rd = 0; rd < rounds; ++rd)
       jacobi_round_launch(A, lda, M, N, V, N, dpairs + (size_t)rd * npairs * 2, npairs,
                           offs + (size_t)rd * npairs, st);
@@ -260,104 +360,120 @@ int jacobi_svd(spk_handle* h, double* A, int64_t lda, int M, int N, double* V, c
     CK(cudaGetLastError());
     double mx = 0.0;
     for (double v : hoffs) mx = std::max(mx, v);
-    if (mx < 1e-15) break;
+    if (mx < 1e-14) break;
   }
   return SPK_OK;
 }
 
 // Low-rank factors of Y (m x m): Y ~= Y1 Y2^T, keeping singular values above
-// trunc_tol * sigma_1 (Algorithm 1 after the loop).  Y1, Y2 (m x ell,
-// column-major, ld m) are workspace buffers returned through *Y1p, *Y2p.
+// trunc_tol * sigma_1 (Algorithm 1 after the loop).  An adaptive blocked
+// randomized range finder (Gaussian blocks of 64 columns, each projected twice
+// against the basis found so far and orthogonalised by one-sided Jacobi) runs
+// until a fresh block's projected norms fall below 0.01 * trunc_tol * ||Y||;
+// then B = Q^T Y is factored by one-sided Jacobi: Y ~= (Q V) Sigma U_b^T.
+// Y1 = (Q V) Sigma^{1/2}, Y2 = U_b Sigma^{1/2} (m x ell, column-major, ld m),
+// returned as workspace buffers.
 int truncate_Y(spk_handle* h, const double* Y, int m, double trunc_tol, uint64_t seed,
                cudaStream_t st, double** Y1p, double** Y2p, int* ell_out) {
-  int k0 = std::min(m, 64);
-  const bool direct = m <= 256;
-  for (int attempt = 0; attempt < 8; ++attempt) {
-    if (direct) k0 = m;
-    double* Qz = nullptr;
-    int k1 = m;
-    if (!direct) {
-      WS(Om, double, "tr_Om", (size_t)m * k0);
-      WS(Z, double, "tr_Z", (size_t)m * k0);
-      WS(Z2, double, "tr_Z2", (size_t)m * k0);
-      gaussian_fill_launch(Om, (int64_t)m * k0, seed + 77 + attempt, st);
-      gemm_f64('N', 'N', m, k0, m, 1.0, Y, m, Om, m, 0.0, Z, m, st);
-      gemm_f64('T', 'N', m, k0, m, 1.0, Y, m, Z, m, 0.0, Z2, m, st);
-      gemm_f64('N', 'N', m, k0, m, 1.0, Y, m, Z2, m, 0.0, Z, m, st);
-      TRY(jacobi_svd(h, Z, m, m, k0, nullptr, st));
-      WS(sz, double, "tr_sz", k0);
-      WS(idx, int, "tr_idx", k0);
-      WS(f1, double, "tr_f1", k0);
-      WS(f2, double, "tr_f2", k0);
-      WS(dell, int, "tr_ell", 1);
-      col_norms_launch(Z, m, m, k0, sz, st);
-      select_sv_launch(sz, k0, 1e-14, idx, f1, f2, dell, st);
-      int hk1 = 0;
-      CK(cudaMemcpyAsync(&hk1, dell, sizeof(int), cudaMemcpyDeviceToHost, st));
-      TRY(wait_stream(h, st, h->host_wait_s));
-      if (hk1 <= 0) { *ell_out = 0; return SPK_OK; }
-      k1 = hk1;
-      WS(qz, double, "tr_Qz", (size_t)m * k1);
-      // Qz columns = Z columns / norm  (f2 = sigma^{-1/2}; apply twice via two gathers)
-      WS(fn, double, "tr_fn", k1);
-      // normalisation factors 1/sigma = f2^2
-      {
-        std::vector<double> hf2(k1);
-        CK(cudaMemcpyAsync(hf2.data(), f2, sizeof(double) * k1, cudaMemcpyDeviceToHost, st));
-        TRY(wait_stream(h, st, h->host_wait_s));
-        for (auto& v : hf2) v = v * v;
-        CK(cudaMemcpyAsync(fn, hf2.data(), sizeof(double) * k1, cudaMemcpyHostToDevice, st));
-      }
-      gather_cols_launch(Z, m, m, idx, fn, k1, qz, m, st);
-      Qz = qz;
+  const int kcap = std::min(m, 2048);
+  const int bsz = std::min(m, 64);
+  WS(Q, double, "tr_Q", (size_t)m * kcap);
+  WS(Z, double, "tr_Z", (size_t)m * bsz);
+  WS(C, double, "tr_C", (size_t)kcap * bsz);
+  WS(nrm, double, "tr_nrm", bsz);
+  WS(idx, int, "tr_idx", std::max(bsz, kcap));
+  WS(f1, double, "tr_f1", std::max(bsz, kcap));
+  WS(f2, double, "tr_f2", std::max(bsz, kcap));
+  WS(dcount, int, "tr_cnt", 1);
+  std::vector<double> hn(bsz);
+  int k = 0;
+  double scale = 0.0;
+  for (int blk = 0; k < kcap; ++blk) {
+    const int b = std::min(bsz, kcap - k);
+    WS(Om, double, "tr_Om", (size_t)m * bsz);
+    gaussian_fill_launch(Om, (int64_t)m * b, seed + 7919ull * (blk + 1), st);
+    gemm_f64('N', 'N', m, b, m, 1.0, Y, m, Om, m, 0.0, Z, m, st);
+    for (int pass = 0; pass < 2 && k > 0; ++pass) {   // Z -= Q (Q^T Z), twice
+      gemm_f64('T', 'N', k, b, m, 1.0, Q, m, Z, m, 0.0, C, k, st);
+      gemm_f64('N', 'N', m, b, k, -1.0, Q, m, C, k, 1.0, Z, m, st);
     }
-    // Bt = Y^T Qz (m x k1), or Y^T when direct
-    WS(Bt, double, "tr_Bt", (size_t)m * k1);
-    WS(Vb, double, "tr_Vb", (size_t)k1 * k1);
-    if (direct) {
-      // Bt = Y^T
-      WS(eye, double, "tr_eye", (size_t)m * m);
-      set_zero_launch(eye, (int64_t)m * m, st);
-      std::vector<double> he((size_t)m * m, 0.0);
-      for (int i = 0; i < m; ++i) he[(size_t)i * m + i] = 1.0;
-      CK(cudaMemcpyAsync(eye, he.data(), sizeof(double) * he.size(), cudaMemcpyHostToDevice, st));
-      gemm_f64('T', 'N', m, m, m, 1.0, Y, m, eye, m, 0.0, Bt, m, st);
-      TRY(wait_stream(h, st, h->host_wait_s));
-    } else {
-      gemm_f64('T', 'N', m, k1, m, 1.0, Y, m, Qz, m, 0.0, Bt, m, st);
-    }
-    TRY(jacobi_svd(h, Bt, m, m, k1, Vb, st));
-    WS(sg, double, "tr_sg", k1);
-    WS(idx2, int, "tr_idx2", k1);
-    WS(g1, double, "tr_g1", k1);
-    WS(g2, double, "tr_g2", k1);
-    WS(dell2, int, "tr_ell2", 1);
-    col_norms_launch(Bt, m, m, k1, sg, st);
-    select_sv_launch(sg, k1, trunc_tol, idx2, g1, g2, dell2, st);
-    int ell = 0;
-    CK(cudaMemcpyAsync(&ell, dell2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    col_norms_launch(Z, m, m, b, nrm, st);
+    CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
     TRY(wait_stream(h, st, h->host_wait_s));
-    if (!direct && ell > k1 - 8 && k0 < m) {
-      k0 = std::min(m, 2 * k0);
-      continue;
+    double mx = 0.0;
+    for (int j = 0; j < b; ++j) mx = std::max(mx, hn[j]);
+    if (blk == 0) scale = mx;
+    if (!(scale > 0.0) || !std::isfinite(mx)) break;
+    if (blk > 0 && mx <= 1e-2 * trunc_tol * scale) break;
+    TRY(jacobi_svd(h, Z, m, m, b, nullptr, st));
+    col_norms_launch(Z, m, m, b, nrm, st);
+    // keep directions above 1e-3 * trunc_tol of the scale, normalised
+    select_sv_launch(nrm, b, 1e-3 * trunc_tol * scale / std::max(mx, 1e-300), idx, f1, f2, dcount, st);
+    int kb = 0;
+    CK(cudaMemcpyAsync(&kb, dcount, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
+    TRY(wait_stream(h, st, h->host_wait_s));
+    if (kb <= 0) break;
+    // 1/sigma factors (f2 holds sigma^{-1/2}: square it on the device side of the gather)
+    std::vector<double> hf(kb);
+    std::vector<int> hidx(kb);
+    CK(cudaMemcpyAsync(hidx.data(), idx, sizeof(int) * kb, cudaMemcpyDeviceToHost, st));
+    TRY(wait_stream(h, st, h->host_wait_s));
+    for (int t = 0; t < kb; ++t) hf[t] = 1.0 / hn[hidx[t]];
+    CK(cudaMemcpyAsync(f1, hf.data(), sizeof(double) * kb, cudaMemcpyHostToDevice, st));
+    WS(Zn, double, "tr_Zn", (size_t)m * bsz);
+    gather_cols_launch(Z, m, m, idx, f1, kb, Zn, m, st);
+    // the normalised block is projected against Q twice more and
+    // re-orthogonalised: its pre-normalisation remainder can be ~1e-12 of the
+    // sample, so projections before normalising leave O(u / 1e-12) overlap
+    for (int pass = 0; pass < 2 && k > 0; ++pass) {
+      gemm_f64('T', 'N', k, kb, m, 1.0, Q, m, Zn, m, 0.0, C, k, st);
+      gemm_f64('N', 'N', m, kb, k, -1.0, Q, m, C, k, 1.0, Zn, m, st);
     }
-    WS(Y1, double, "tr_Y1", (size_t)m * std::max(ell, 1));
-    WS(Y2, double, "tr_Y2", (size_t)m * std::max(ell, 1));
-    // Y ~= (Qz Vb) Sigma Ub^T, Bt Vb = Ub Sigma (after the rotations)
-    if (direct) {
-      gather_cols_launch(Vb, k1, k1, idx2, g1, ell, Y1, m, st);
-    } else {
-      WS(QV, double, "tr_QV", (size_t)m * k1);
-      gemm_f64('N', 'N', m, k1, k1, 1.0, Qz, m, Vb, k1, 0.0, QV, m, st);
-      gather_cols_launch(QV, m, m, idx2, g1, ell, Y1, m, st);
+    TRY(jacobi_svd(h, Zn, m, m, kb, nullptr, st));
+    col_norms_launch(Zn, m, m, kb, nrm, st);
+    CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * kb, cudaMemcpyDeviceToHost, st));
+    TRY(wait_stream(h, st, h->host_wait_s));
+    for (int t = 0; t < kb; ++t) {
+      hidx[t] = t;
+      hf[t] = hn[t] > 0.0 ? 1.0 / hn[t] : 0.0;
     }
-    gather_cols_launch(Bt, m, m, idx2, g2, ell, Y2, m, st);
-    *Y1p = Y1;
-    *Y2p = Y2;
-    *ell_out = ell;
+    CK(cudaMemcpyAsync(idx, hidx.data(), sizeof(int) * kb, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(f1, hf.data(), sizeof(double) * kb, cudaMemcpyHostToDevice, st));
+    gather_cols_launch(Zn, m, m, idx, f1, kb, Q + (size_t)k * m, m, st);
+    TRY(wait_stream(h, st, h->host_wait_s));
+    k += kb;
+    if (kb < b) break;   // the sample did not fill: the range is exhausted
+  }
+  if (k == 0) {
+    *ell_out = 0;
     return SPK_OK;
   }
-  return fail(h, SPK_ERR_ARG, "truncation sample size did not settle");
+  // B^T = Y^T Q (m x k); one-sided Jacobi with V accumulation
+  WS(Bt, double, "tr_Bt", (size_t)m * k);
+  WS(Vb, double, "tr_Vb", (size_t)k * k);
+  gemm_f64('T', 'N', m, k, m, 1.0, Y, m, Q, m, 0.0, Bt, m, st);
+  TRY(jacobi_svd(h, Bt, m, m, k, Vb, st));
+  WS(sg, double, "tr_sg", k);
+  WS(idx2, int, "tr_idx2", k);
+  WS(g1, double, "tr_g1", k);
+  WS(g2, double, "tr_g2", k);
+  WS(dell2, int, "tr_ell2", 1);
+  col_norms_launch(Bt, m, m, k, sg, st);
+  select_sv_launch(sg, k, trunc_tol, idx2, g1, g2, dell2, st);
+  int ell = 0;
+  CK(cudaMemcpyAsync(&ell, dell2, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TRY(wait_stream(h, st, h->host_wait_s));
+  WS(Y1, double, "tr_Y1", (size_t)m * std::max(ell, 1));
+  WS(Y2, double, "tr_Y2", (size_t)m * std::max(ell, 1));
+  WS(QV, double, "tr_QV", (size_t)m * k);
+  gemm_f64('N', 'N', m, k, k, 1.0, Q, m, Vb, k, 0.0, QV, m, st);
+  gather_cols_launch(QV, m, m, idx2, g1, ell, Y1, m, st);
+  gather_cols_launch(Bt, m, m, idx2, g2, ell, Y2, m, st);
+  *Y1p = Y1;
+  *Y2p = Y2;
+  *ell_out = ell;
+  return SPK_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -515,42 +631,85 @@ struct Solver {
     const int slot0 = i0 - (d - sd.k + 1);
     double* hs = sd.hslot(d, slot0);
     const spk_csr* op = sd.op;
+    const double nr = (double)sd.n * r, bB = sizeof(TB), bC = sizeof(TC), bV = sizeof(TV);
+    const double csr_bytes = (double)op->nnz * (bV + 4) + (double)(sd.n + 1) * 4;
     if (!replay) {
-      spmm_dots_launch<TB, TC, TV>(op->rowptr_dev, op->col_dev, sd.vals, sd.n, r, sd.block(d), sd.W,
-                                   win, sd.partial, sd.grid, st);
-      for (int g = 0; g < win.nwin; g += 4) {
-        const int nq = std::min(4, win.nwin - g);
-        reduce_partials_launch(sd.partial + (size_t)(g / 4) * sd.grid * 4 * r * r, sd.grid,
-                               4 * r * r, nq * r * r, hs + (size_t)g * r * r, st);
+      {
+        ProfScope ps(h, F_SPMM, st, 1 + (win.nwin - 1) / 4 + (win.nwin + 3) / 4,
+                     csr_bytes + nr * (bB + bC) + win.nwin * nr * bB,
+                     2.0 * op->nnz * r + 2.0 * win.nwin * nr * r);
+        spmm_dots_launch<TB, TC, TV>(op->rowptr_dev, op->col_dev, sd.vals, sd.n, r, sd.block(d), sd.W,
+                                     win, sd.partial, sd.grid, st);
+        for (int g = 0; g < win.nwin; g += 4) {
+          const int nq = std::min(4, win.nwin - g);
+          reduce_partials_launch(sd.partial + (size_t)(g / 4) * sd.grid * 4 * r * r, sd.grid,
+                                 4 * r * r, nq * r * r, hs + (size_t)g * r * r, st);
+        }
       }
-      update_gram_launch<TB, TC>(sd.W, sd.n, r, win, hs, sd.partial, sd.grid, 1, st);
-      chol_small_launch(sd.partial, sd.grid, r, sd.R1, sd.R1inv(d), h->flags, kBreakdownFloor, st);
+      {
+        ProfScope ps(h, F_UPDATE, st, 2, 2 * nr * bC + win.nwin * nr * bB,
+                     2.0 * win.nwin * nr * r + 2.0 * nr * r);
+        update_gram_launch<TB, TC>(sd.W, sd.n, r, win, hs, sd.partial, sd.grid, 1, st);
+        chol_small_launch(sd.partial, sd.grid, r, sd.R1, sd.R1inv(d), h->flags, kBreakdownFloor, st);
+      }
+      ProfScope ps(h, F_SCALE, st, 4, 3 * nr * bC + nr * bB, 4.0 * nr * r);
       scale_gram_launch<TC>(sd.W, sd.n, r, sd.R1inv(d), sd.partial, sd.grid, st);
       chol_small_launch(sd.partial, sd.grid, r, sd.R2, sd.R2inv(d), h->flags, 1e-28, st);
       combine_small_launch(sd.R2, sd.R1, sd.hslot(d, sd.k), r, 0, st);
+      scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(d), sd.block(d + 1), st);
     } else {
       WindowPtrs none{};
       none.nwin = 0;
-      spmm_dots_launch<TB, TC, TV>(op->rowptr_dev, op->col_dev, sd.vals, sd.n, r, sd.block(d), sd.W,
-                                   none, sd.partial, sd.grid, st);
-      update_gram_launch<TB, TC>(sd.W, sd.n, r, win, hs, sd.partial, sd.grid, 0, st);
+      {
+        ProfScope ps(h, F_SPMM, st, 1, csr_bytes + nr * (bB + bC), 2.0 * op->nnz * r);
+        spmm_dots_launch<TB, TC, TV>(op->rowptr_dev, op->col_dev, sd.vals, sd.n, r, sd.block(d),
+                                     sd.W, none, sd.partial, sd.grid, st);
+      }
+      {
+        ProfScope ps(h, F_UPDATE, st, 1, 2 * nr * bC + win.nwin * nr * bB, 2.0 * win.nwin * nr * r);
+        update_gram_launch<TB, TC>(sd.W, sd.n, r, win, hs, sd.partial, sd.grid, 0, st);
+      }
+      ProfScope ps(h, F_SCALE, st, 2, 3 * nr * bC + nr * bB, 2.0 * nr * r);
       scale_gram_launch<TC>(sd.W, sd.n, r, sd.R1inv(d), sd.partial, sd.grid, st);
+      scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(d), sd.block(d + 1), st);
     }
-    scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(d), sd.block(d + 1), st);
   }
 
   // Sketch of U_{d+1}, QR update of S U_{d+1}, T column, bordering update of H~.
   void whiten_and_border(Side<TB, TC, TV>& sd, int d) {
     const int m = d * r;
     const int64_t s = sd.sk.s;
-    sketch_apply_launch<TB, TC>(sd.sk, sd.block(d + 1), r, sd.w, sd.sk_scratch, st);
+    const double sr8 = 8.0 * s * r, sm8 = 8.0 * s * m;
+    {
+      ProfScope ps(h, F_SKETCH, st, sd.sk.identity ? 1 : 2,
+                   (double)sd.n * r * sizeof(TB) + (double)sd.n + sr8,
+                   sd.sk.identity ? 0.0 : (double)sd.sk.npad * r * sd.sk.log2n2 + (double)s * sd.sk.n1 * r);
+      sketch_apply_launch<TB, TC>(sd.sk, sd.block(d + 1), r, sd.w, sd.sk_scratch, st);
+    }
     const int nch = q_update_chunks(m);
-    qt_dot_launch(sd.Q, s, s, m, sd.w, r, sd.t1, st);
-    q_update_launch(sd.Q, s, s, m, sd.t1, r, sd.w, sd.w1, sd.qpartial, nch, st);
-    qt_dot_launch(sd.Q, s, s, m, sd.w1, r, sd.t2, st);
-    q_update_launch(sd.Q, s, s, m, sd.t2, r, sd.w1, sd.w, sd.qpartial, nch, st);
-    sketch_qr(sd, m);
-    t_write_launch(sd.T, sd.ldT, m, r, sd.t1, sd.t2, sd.tau, st);
+    {
+      ProfScope ps(h, F_QTDOT, st, 1, sm8 + sr8 + 8.0 * m * r, 2.0 * s * m * r);
+      qt_dot_launch(sd.Q, s, s, m, sd.w, r, sd.t1, st);
+    }
+    {
+      ProfScope ps(h, F_QUPDATE, st, 2, sm8 + 2 * sr8 + 8.0 * m * r, 2.0 * s * m * r);
+      q_update_launch(sd.Q, s, s, m, sd.t1, r, sd.w, sd.w1, sd.qpartial, nch, st);
+    }
+    {
+      ProfScope ps(h, F_QTDOT, st, 1, sm8 + sr8 + 8.0 * m * r, 2.0 * s * m * r);
+      qt_dot_launch(sd.Q, s, s, m, sd.w1, r, sd.t2, st);
+    }
+    {
+      ProfScope ps(h, F_QUPDATE, st, 2, sm8 + 2 * sr8 + 8.0 * m * r, 2.0 * s * m * r);
+      q_update_launch(sd.Q, s, s, m, sd.t2, r, sd.w1, sd.w, sd.qpartial, nch, st);
+    }
+    {
+      ProfScope ps(h, F_TSQR, st, 8, 6 * sr8, 6.0 * s * r * r);
+      sketch_qr(sd, m);
+      t_write_launch(sd.T, sd.ldT, m, r, sd.t1, sd.t2, sd.tau, st);
+    }
+    ProfScope psb(h, F_BORDER, st, d == 1 ? 2 : 3, 8.0 * (double)(m - r) * (m - r) + 16.0 * m * r,
+                  2.0 * (double)(m - r) * (m - r) * r);
     // bordering (Section 5): Hhat_d from H~_{d-1}, then the correction -> H~_d
     const int mp = m - r;
     int i0 = 0;
@@ -581,8 +740,11 @@ struct Solver {
     if (o.inject & SPK_INJECT_SINGULAR)
       return fail(h, SPK_ERR_SINGULAR_PROJECTED, "injected: singular projected equation");
     TRY(sign_solve(h, m, Hk, Gk, F, o.max_newton, st, newton_iters));
-    rho_launch(F, m, m, r, S[0].T, S[0].ldT, S[1].T, S[1].ldT, S[0].hslot(d, S[0].k),
-               S[1].hslot(d, S[1].k), S[0].beta, S[1].beta, out3, st);
+    {
+      ProfScope ps(h, F_RHO, st, 1, 16.0 * m * r, 8.0 * m * r * r);
+      rho_launch(F, m, m, r, S[0].T, S[0].ldT, S[1].T, S[1].ldT, S[0].hslot(d, S[0].k),
+                 S[1].hslot(d, S[1].k), S[0].beta, S[1].beta, out3, st);
+    }
     CK(cudaMemcpyAsync(rho3, out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     TRY(wait_stream(h, st, (o.inject & SPK_INJECT_TIMEOUT) ? 0.0 : h->host_wait_s));
     CK(cudaGetLastError());
@@ -593,13 +755,19 @@ struct Solver {
     const int m = d * r;
     double *Y1 = nullptr, *Y2 = nullptr;
     int ell = 0;
-    TRY(truncate_Y(h, Y, m, o.trunc_tol, o.seed, st, &Y1, &Y2, &ell));
+    {
+      ProfScope ps(h, F_TRUNC, st, 0, 8.0 * m * m, 0.0);
+      TRY(truncate_Y(h, Y, m, o.trunc_tol, o.seed, st, &Y1, &Y2, &ell));
+    }
     out->rank = ell;
     out->mem_solution_vectors = 2 * (int64_t)ell;
     if (ell == 0) return SPK_OK;
     // W_i = T_i^{-1} Y_i  (T_U, T_V leading m x m)
-    trsm_upper_left_launch(S[0].T, S[0].ldT, m, Y1, m, ell, st);
-    trsm_upper_left_launch(S[1].T, S[1].ldT, m, Y2, m, ell, st);
+    {
+      ProfScope ps(h, F_TRSM, st, 2, 2 * 8.0 * ((double)m * m / 2 + 2.0 * m * ell), 2.0 * m * m * ell);
+      trsm_upper_left_launch(S[0].T, S[0].ldT, m, Y1, m, ell, st);
+      trsm_upper_left_launch(S[1].T, S[1].ldT, m, Y2, m, ell, st);
+    }
     double* Wf[2] = {Y1, Y2};
     for (int side = 0; side < 2; ++side) {
       auto& sd = S[side];
@@ -617,6 +785,9 @@ struct Solver {
           WindowPtrs blocks{};
           blocks.nwin = j - last;
           for (int q = 0; q < blocks.nwin; ++q) blocks.blk[q] = sd.block(last + 1 + q);
+          ProfScope ps(h, F_XACC, st, 1,
+                       (double)sd.n * (2.0 * 8 * ell + blocks.nwin * r * sizeof(TB)),
+                       2.0 * sd.n * ell * r * blocks.nwin);
           x_accumulate_launch<TB>(X, sd.n, ell, r, blocks, Wf[side] + (size_t)last * r, m, st);
           last = j;
         }
@@ -754,6 +925,7 @@ struct Solver {
     CK(cudaGetLastError());
     TRY(read_flags(h, st, &f));
     TRY(flags_to_status(h, f));
+    h->prof.resolve();
     float ms_loop = 0.f, ms_rec = 0.f;
     cudaEventElapsedTime(&ms_loop, e0, e1);
     cudaEventElapsedTime(&ms_rec, er0, er1);
@@ -1072,9 +1244,43 @@ int spk_sylvester_dense(spk_handle* h, int32_t m, const double* H, const double*
   return SPK_OK;
 }
 
+int64_t spk_launch_count(void) { return launch_count(); }
+
+int spk_profile_enable(spk_handle* h, int on) {
+  if (!h) return SPK_ERR_ARG;
+  h->prof.resolve();
+  h->prof.on = on != 0;
+  for (auto& a : h->prof.acc) a = ProfAcc();
+  return SPK_OK;
+}
+
+int spk_profile_read(spk_handle* h, int family, const char** name, double* ms, int64_t* launches,
+                     int64_t* groups, double* bytes, double* flops) {
+  if (!h || family < 0 || family >= F_COUNT) return SPK_ERR_ARG;
+  h->prof.resolve();
+  const ProfAcc& a = h->prof.acc[family];
+  if (name) *name = kFamNames[family];
+  if (ms) *ms = a.ms;
+  if (launches) *launches = a.launches;
+  if (groups) *groups = a.groups;
+  if (bytes) *bytes = a.bytes;
+  if (flops) *flops = a.flops;
+  return SPK_OK;
+}
+
+int spk_fp64_peak(spk_handle* h, double* tflops, void* stream) {
+  if (!h || !tflops) return SPK_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  WS(scr, double, "fp64_probe", 4);
+  *tflops = fp64_fma_probe(h->sm_count, scr, st);
+  CK(cudaGetLastError());
+  return SPK_OK;
+}
+
 int spk_inspect(spk_handle* h, const char* name, double* dst, int64_t count, int64_t* avail) {
   if (!h || !name) return SPK_ERR_ARG;
-  static const char* allowed[] = {"U_T", "V_T", "U_Ht", "V_Ht", "U_hband", "V_hband", "U_beta", "V_beta"};
+  static const char* allowed[] = {"U_T", "V_T", "U_Ht", "V_Ht", "U_hband", "V_hband", "U_beta",
+                                  "V_beta", "pj_F", "tr_Y1", "tr_Y2"};
   bool ok = false;
   for (const char* a : allowed) ok = ok || strcmp(a, name) == 0;
   auto it = h->bufs.find(name);

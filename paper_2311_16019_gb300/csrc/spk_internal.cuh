@@ -25,6 +25,10 @@ enum : uint32_t {
   kFlagZeroPivot = 1u << 2,
 };
 
+// Number of kernel launches issued by the library since it was loaded.
+void count_launches(int64_t n);
+int64_t launch_count();
+
 // ---------------------------------------------------------------- storage
 template <typename T> struct Store;
 template <> struct Store<double> {
@@ -165,6 +169,8 @@ void select_sv_launch(const double* sigma, int N, double tol, int* idx, double* 
 // out[:, t] = A[:, idx[t]] * f[t]
 void gather_cols_launch(const double* A, int64_t lda, int M, const int* idx, const double* f,
                         int ncols, double* out, int64_t ldo, cudaStream_t st);
+// Measured FP64 FMA rate of the device in TFLOP/s (dependent-chain probe).
+double fp64_fma_probe(int sm_count, double* scratch, cudaStream_t st);
 double trace_product(const double* A, const double* B, int n, double* scratch, cudaStream_t st);
 
 }  // namespace spk

@@ -90,6 +90,10 @@ def load() -> C.CDLL:
         "spk_spmm": (i32, [vp, P(Csr), vp, i32, vp, vp]),
         "spk_sylvester_dense": (i32, [vp, i32, vp, vp, vp, vp, P(i32), vp]),
         "spk_inspect": (i32, [vp, C.c_char_p, vp, i64, P(i64)]),
+        "spk_launch_count": (i64, []),
+        "spk_profile_enable": (i32, [vp, C.c_int]),
+        "spk_profile_read": (i32, [vp, C.c_int, P(C.c_char_p), P(dbl), P(i64), P(i64), P(dbl), P(dbl)]),
+        "spk_fp64_peak": (i32, [vp, P(dbl), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -345,3 +349,40 @@ def inspect(name: str, device: int = 0) -> np.ndarray:
     if rc != SPK_OK:
         raise SpkError(rc, h.error())
     return out
+
+
+def launch_count() -> int:
+    return int(load().spk_launch_count())
+
+
+def profile_enable(on: bool = True, device: int = 0):
+    h = handle(device)
+    h.lib.spk_profile_enable(h.h, int(on))
+
+
+def profile_read(device: int = 0) -> dict:
+    """{family: dict(ms, launches, groups, bytes, flops)} of the enabled profiler."""
+    h = handle(device)
+    out = {}
+    f = 0
+    while True:
+        name = C.c_char_p()
+        ms, by, fl = C.c_double(), C.c_double(), C.c_double()
+        la, gr = C.c_int64(), C.c_int64()
+        rc = h.lib.spk_profile_read(h.h, f, C.byref(name), C.byref(ms), C.byref(la), C.byref(gr),
+                                    C.byref(by), C.byref(fl))
+        if rc != SPK_OK:
+            break
+        out[name.value.decode()] = dict(ms=ms.value, launches=la.value, groups=gr.value,
+                                        bytes=by.value, flops=fl.value)
+        f += 1
+    return out
+
+
+def fp64_peak(device: int = 0) -> float:
+    h = handle(device)
+    v = C.c_double()
+    rc = h.lib.spk_fp64_peak(h.h, C.byref(v), _stream_ptr())
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+    return v.value

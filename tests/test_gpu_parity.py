@@ -191,3 +191,18 @@ def test_adaptive_schedule_converges():
                     check="adaptive")
     assert g.converged and len(g.hist_d) < 20
     assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 3e-8
+
+
+def test_converged_conv_diff_r4_randomized_truncation():
+    """64 x 64 conv-diff, r = 4, k = 4, checks every 20: projected size
+    m = 480 > 256 takes the randomized range-finder truncation.  Same d as the
+    oracle, X within 1e-8 of it (kappa(T) ~ 1e12 here), true residual at tol."""
+    P = I.workload("cd2d_64_r4")
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=4, s=3200, maxit=400, p=20, tol=1e-8, seed=0)
+    assert g.converged
+    o = SP.spkms(P.A, P.BT, P.C1, P.C2, k=4, s=3200, tol=1e-8, maxit=400, p=20, seed=0)
+    assert o["d"] == g.iters
+    err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
+    assert err < 1e-8, err
+    assert abs(g.rank - o["rank"]) <= 2
+    assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 2e-8
