@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=40)
+    ap.add_argument("--kernel-case", default=None, choices=["gje"],
+                    help="run one small isolated case of a kernel family (for ncu captures)")
+    ap.add_argument("--m", type=int, default=4200, help="size of the dense case")
     return ap.parse_args()
 
 
@@ -385,8 +388,34 @@ def run_spk(args, rank, world, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def run_kernel_case(args):
+    """Dense sign-function solve of H Y + Y G^T = F, m x m (default 4200: the
+    matrices exceed L2), as a small isolated case of the inversion kernels."""
+    import numpy as np
+    import torch
+    from paper_2311_16019_gb300 import build, spk
+    build.build()
+    rng = np.random.default_rng(11)
+    m = args.m
+    def rhp():
+        A = rng.standard_normal((m, m)) * (0.3 / np.sqrt(m))
+        A[np.diag_indices(m)] += rng.uniform(1.0, 100.0, m)
+        return A
+    H, G = rhp(), rhp()
+    F = np.zeros((m, m))
+    F[:4, :4] = rng.standard_normal((4, 4))
+    t0 = time.perf_counter()
+    Y, it = spk.sylvester_dense(H, G, F)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": args.kernel_case, "m": m, "newton_iters": it,
+                      "seconds": time.perf_counter() - t0}), flush=True)
+
+
 def main():
     args = parse()
+    if args.kernel_case:
+        run_kernel_case(args)
+        return
     rank, world, local, pg = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world, pg)

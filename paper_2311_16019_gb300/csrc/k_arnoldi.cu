@@ -278,20 +278,39 @@ __global__ void __launch_bounds__(256) k_scale_store(const TC* __restrict__ W, i
 }
 
 // X (n x ell, row-major FP64) += sum_q U_q Wrows[q r .. q r + r-1, :]
+// (Wrows column-major with leading dimension ldw).  CTA tile: 64 columns of
+// X by kXRows rows; the W chunk and the U rows are staged in shared memory,
+// X is read and written once, coalesced along its columns.
+constexpr int kXCols = 64, kXRows = 32;
 template <typename TB>
-__global__ void k_x_accumulate(double* __restrict__ X, int64_t n, int ell, int r, WindowPtrs blocks,
-                               const double* __restrict__ Wrows, int64_t ldw) {
-  const int64_t total = n * ell;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / ell;
-    const int c = (int)(e - i * ell);
-    double s = X[e];
-    for (int q = 0; q < blocks.nwin; ++q) {
-      const TB* u = static_cast<const TB*>(blocks.blk[q]) + i * r;
-      for (int a = 0; a < r; ++a) s = fma((double)Store<TB>::ld(u + a), Wrows[(q * r + a) + c * ldw], s);
-    }
-    X[e] = s;
+__global__ void __launch_bounds__(256) k_x_accumulate(double* __restrict__ X, int64_t n, int ell, int r,
+                                                      WindowPtrs blocks,
+                                                      const double* __restrict__ Wrows, int64_t ldw) {
+  __shared__ double Ws[kMaxWin * kMaxR][kXCols];
+  __shared__ double Us[kXRows][kMaxWin * kMaxR + 1];
+  const int kr = blocks.nwin * r;
+  const int c0 = blockIdx.y * kXCols;
+  const int64_t i0 = (int64_t)blockIdx.x * kXRows;
+  const int tx = threadIdx.x & (kXCols - 1), ty = threadIdx.x / kXCols;  // 64 x 4
+  for (int e = threadIdx.x; e < kr * kXCols; e += blockDim.x) {
+    const int qa = e / kXCols, c = e - qa * kXCols;
+    Ws[qa][c] = (c0 + c < ell) ? Wrows[qa + (int64_t)(c0 + c) * ldw] : 0.0;
+  }
+  for (int e = threadIdx.x; e < kXRows * kr; e += blockDim.x) {
+    const int ri = e / kr, qa = e - ri * kr;
+    const int q = qa / r, a = qa - q * r;
+    const int64_t i = i0 + ri;
+    Us[ri][qa] = (i < n) ? (double)Store<TB>::ld(static_cast<const TB*>(blocks.blk[q]) + i * r + a) : 0.0;
+  }
+  __syncthreads();
+  const int c = c0 + tx;
+  if (c >= ell) return;
+  for (int ri = ty; ri < kXRows; ri += 4) {
+    const int64_t i = i0 + ri;
+    if (i >= n) break;
+    double s = X[i * ell + c];
+    for (int qa = 0; qa < kr; ++qa) s = fma(Us[ri][qa], Ws[qa][tx], s);
+    X[i * ell + c] = s;
   }
 }
 
@@ -421,8 +440,9 @@ template <typename TB>
 void x_accumulate_launch(double* X, int64_t n, int ell, int r, WindowPtrs blocks,
                          const double* Wrows, int64_t ldw, cudaStream_t st) {
   if (ell <= 0 || blocks.nwin <= 0) return;
+  dim3 grid((unsigned)((n + kXRows - 1) / kXRows), (unsigned)((ell + kXCols - 1) / kXCols));
   count_launches(1);
-  k_x_accumulate<TB><<<default_grid(n * ell), 256, 0, st>>>(X, n, ell, r, blocks, Wrows, ldw);
+  k_x_accumulate<TB><<<grid, 256, 0, st>>>(X, n, ell, r, blocks, Wrows, ldw);
 }
 
 void spmm_wide_launch(const int32_t* rowptr, const int32_t* col, const double* val, int64_t n,

@@ -107,8 +107,10 @@ __global__ void k_scale_matrix(double* A, int64_t ld, int M, int N, double a) {
 }
 
 // ---- Gauss-Jordan inversion
-constexpr int kGjeCols = 8;     // columns per CTA
+constexpr int kGjeCols = 8;     // columns per CTA (unblocked path)
 constexpr int kGjeThreads = 256;
+constexpr int kGjeNb = 64;      // panel width of the blocked path
+constexpr int kGjeBlockedMin = 256;
 
 // Block argmax of |A[i + col*ld]| over i in [j, m), ties to the smaller index.
 __device__ void block_argmax(const double* A, int64_t ld, int m, int j, int col, int* p_out,
@@ -161,10 +163,70 @@ __device__ void gje_prepare_pivot(double* A, int64_t ld, int m, int j, GjeState 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kGjeThreads) k_gje_first(double* A, int64_t ld, int m, GjeState gs) {
-  if (threadIdx.x == 0) gs.scal[0] = 0.0;
+__global__ void __launch_bounds__(kGjeThreads) k_gje_first(double* A, int64_t ld, int m, int j,
+                                                             GjeState gs) {
+  if (j == 0 && threadIdx.x == 0) gs.scal[0] = 0.0;
   __syncthreads();
-  gje_prepare_pivot(A, ld, m, 0, gs);
+  gje_prepare_pivot(A, ld, m, j, gs);
+}
+
+// Blocked variant, one pivot step j restricted to the panel columns
+// [k0, k0 + nb): CTA b sweeps column k0 + b (row exchange j <-> p included);
+// the CTA of column j+1 prepares the next pivot when j+1 is in the panel.
+__global__ void __launch_bounds__(kGjeThreads) k_gje_panel_step(double* A, int64_t ld, int m, int j,
+                                                                int k0, int nb, GjeState gs) {
+  const int p = gs.ipiv[j];
+  const double piv = gs.scal[2 + (j & 1)];
+  const double rpiv = 1.0 / piv;
+  const double* c = gs.cvec + (int64_t)(j & 1) * m;
+  const int l = k0 + blockIdx.x;
+  double* col = A + (int64_t)l * ld;
+  const double aj = col[p];
+  const double ap = col[j];
+  __syncthreads();
+  if (l == j) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] = (i == j) ? rpiv : -c[i] * rpiv;
+  } else {
+    const double f = aj * rpiv;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double v;
+      if (i == j) v = f;
+      else {
+        const double base = (i == p) ? ap : col[i];
+        v = fma(-c[i], f, base);
+      }
+      col[i] = v;
+    }
+  }
+  __syncthreads();
+  if (l == j + 1 && j + 1 < k0 + nb) gje_prepare_pivot(A, ld, m, j + 1, gs);
+}
+
+// After a panel: for every column outside it, apply the panel's row
+// exchanges in order, save the pivot rows to Bsave (nb x m, column-major)
+// and zero them; panel columns get zero columns in Bsave.
+__global__ void k_gje_prep(double* A, int64_t ld, int m, int k0, int nb,
+                           const int32_t* __restrict__ ipiv, double* __restrict__ Bsave) {
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < m; l += gridDim.x * blockDim.x) {
+    double* col = A + (int64_t)l * ld;
+    double* b = Bsave + (int64_t)l * nb;
+    if (l >= k0 && l < k0 + nb) {
+      for (int q = 0; q < nb; ++q) b[q] = 0.0;
+      continue;
+    }
+    for (int q = 0; q < nb; ++q) {
+      const int j = k0 + q, p = ipiv[j];
+      if (p != j) {
+        const double t = col[j];
+        col[j] = col[p];
+        col[p] = t;
+      }
+    }
+    for (int q = 0; q < nb; ++q) {
+      b[q] = col[k0 + q];
+      col[k0 + q] = 0.0;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(kGjeThreads) k_gje_step(double* A, int64_t ld, int m, int j, GjeState gs) {
@@ -415,6 +477,19 @@ __global__ void k_trace_product(const double* __restrict__ A, const double* __re
   }
 }
 
+// out[j] = sum_i |A[i + j*lda]| (column absolute sums, for the 1-norm)
+__global__ void k_col_abs_sums(const double* __restrict__ A, int64_t lda, int M, int N,
+                               double* __restrict__ out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= N) return;
+  const double* a = A + (int64_t)warp * lda;
+  double s = 0.0;
+  for (int i = lane; i < M; i += 32) s += fabs(a[i]);
+  s = warp_sum(s);
+  if (lane == 0) out[warp] = s;
+}
+
 // FP64 FMA throughput probe: 8 independent dependency chains per thread.
 __global__ void __launch_bounds__(256) k_fp64_fma(double* out, int iters, double b, double c) {
   double a[8];
@@ -467,10 +542,30 @@ void scale_matrix_launch(double* A, int64_t ld, int M, int N, double a, cudaStre
 void gje_invert(double* A, int64_t lda, int m, GjeState gs, cudaStream_t st) {
   if (m <= 0) return;
   count_launches(1);
-  k_gje_first<<<1, kGjeThreads, 0, st>>>(A, lda, m, gs);
-  const int blocks = (m + kGjeCols - 1) / kGjeCols;
-  count_launches(m);
-  for (int j = 0; j < m; ++j) k_gje_step<<<blocks, kGjeThreads, 0, st>>>(A, lda, m, j, gs);
+  k_gje_first<<<1, kGjeThreads, 0, st>>>(A, lda, m, 0, gs);
+  if (m <= kGjeBlockedMin || !gs.panel || !gs.bsave) {
+    const int blocks = (m + kGjeCols - 1) / kGjeCols;
+    count_launches(m);
+    for (int j = 0; j < m; ++j) k_gje_step<<<blocks, kGjeThreads, 0, st>>>(A, lda, m, j, gs);
+  } else {
+    // Blocked Gauss-Jordan: sweep a panel of kGjeNb columns with one small
+    // launch per pivot, then update every other column with one GEMM
+    //   A[:, R] <- [0 on the pivot rows; A[:, R]] + Panel * A_pivot_rows[:, R].
+    for (int k0 = 0; k0 < m; k0 += kGjeNb) {
+      const int nb = std::min(kGjeNb, m - k0);
+      if (k0 > 0) {
+        count_launches(1);
+        k_gje_first<<<1, kGjeThreads, 0, st>>>(A, lda, m, k0, gs);
+      }
+      count_launches(nb);
+      for (int j = k0; j < k0 + nb; ++j)
+        k_gje_panel_step<<<nb, kGjeThreads, 0, st>>>(A, lda, m, j, k0, nb, gs);
+      count_launches(1);
+      k_gje_prep<<<grid_for(m, 128), 128, 0, st>>>(A, lda, m, k0, nb, gs.ipiv, gs.bsave);
+      copy_matrix_launch(A + (int64_t)k0 * lda, lda, gs.panel, m, m, nb, st);
+      gemm_f64('N', 'N', m, m, nb, 1.0, gs.panel, m, gs.bsave, nb, 1.0, A, lda, st);
+    }
+  }
   count_launches(1);
   k_gje_colperm<<<grid_for(m, 128), 128, 0, st>>>(A, lda, m, gs.ipiv);
 }
@@ -505,6 +600,12 @@ void col_norms_launch(const double* A, int64_t lda, int M, int N, double* out, c
   if (N <= 0) return;
   count_launches(1);
   k_col_norms<<<N, 256, 0, st>>>(A, lda, M, out);
+}
+
+void col_abs_sums_launch(const double* A, int64_t lda, int M, int N, double* out, cudaStream_t st) {
+  if (N <= 0) return;
+  count_launches(1);
+  k_col_abs_sums<<<(N + 7) / 8, 256, 0, st>>>(A, lda, M, N, out);
 }
 
 double fp64_fma_probe(int sm_count, double* scratch, cudaStream_t st) {

@@ -49,11 +49,41 @@ __host__ __device__ void mm(const double* A, const double* B, double* C, int r) 
   for (int e = 0; e < r * r; ++e) C[e] = o[e];
 }
 
-// Rows i < mp of the new block column of H~.
+constexpr int kBRows = 128;   // rows per CTA of the bordering GEMV
+constexpr int kBCols = 256;   // columns of H~ per CTA
+
+// partial[(chunk*mp + i)*r + c] = sum_{l in chunk} H~[i, l] T_H[l, c]
+__global__ void __launch_bounds__(kBRows) k_border_gemv(const double* __restrict__ Ht, int64_t ldH,
+                                                       int mp, int r, const double* __restrict__ T,
+                                                       int64_t ldT, double* __restrict__ partial) {
+  __shared__ double th[kBCols * kMaxR];
+  const int l0 = blockIdx.y * kBCols;
+  const int l1 = min(mp, l0 + kBCols);
+  for (int e = threadIdx.x; e < (l1 - l0) * r; e += blockDim.x) {
+    const int l = e / r, c = e - l * r;
+    th[e] = T[l0 + l + (int64_t)(mp + c) * ldT];
+  }
+  __syncthreads();
+  const int i = blockIdx.x * kBRows + threadIdx.x;
+  if (i >= mp) return;
+  double v[kMaxR] = {0, 0, 0, 0};
+  const double* hrow = Ht + i + (int64_t)l0 * ldH;
+  for (int l = 0; l < l1 - l0; ++l) {
+    const double hv = hrow[(int64_t)l * ldH];
+#pragma unroll
+    for (int c = 0; c < kMaxR; ++c)
+      if (c < r) v[c] = fma(hv, th[l * r + c], v[c]);
+  }
+  for (int c = 0; c < r; ++c) partial[((int64_t)blockIdx.y * mp + i) * r + c] = v[c];
+}
+
+// Rows i < mp of the new block column of H~:
+// (-sum of GEMV partials + T_{d-1} H_col + T_H h_{d,d}) tau_d^{-1}.
 __global__ void k_border_col(double* __restrict__ Ht, int64_t ldH, int mp, int r,
                              const double* __restrict__ T, int64_t ldT,
                              const double* __restrict__ hslots, int first_block, int nslots,
-                             const double* __restrict__ h_dd) {
+                             const double* __restrict__ h_dd, const double* __restrict__ partial,
+                             int nchunk) {
   __shared__ double tinv[kMaxR * kMaxR];
   __shared__ double hdd[kMaxR * kMaxR];
   if (threadIdx.x == 0) upper_inv(T, ldT, mp, r, tinv);
@@ -62,12 +92,8 @@ __global__ void k_border_col(double* __restrict__ Ht, int64_t ldH, int mp, int r
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= mp) return;
   double v[kMaxR] = {0, 0, 0, 0};
-  // -H~_{d-1} T_H
-  for (int l = 0; l < mp; ++l) {
-    const double h = Ht[i + (int64_t)l * ldH];
-    for (int c = 0; c < r; ++c) v[c] -= h * T[l + (int64_t)(mp + c) * ldT];
-  }
-  // + T_{d-1} H_col (band of blocks first_block .. first_block+nslots-1)
+  for (int ch = 0; ch < nchunk; ++ch)
+    for (int c = 0; c < r; ++c) v[c] -= partial[((int64_t)ch * mp + i) * r + c];
   for (int q = 0; q < nslots; ++q) {
     const int b = first_block + q;  // 1-based block index
     for (int a = 0; a < r; ++a) {
@@ -76,7 +102,6 @@ __global__ void k_border_col(double* __restrict__ Ht, int64_t ldH, int mp, int r
       for (int c = 0; c < r; ++c) v[c] += t * hslots[(q * r + a) * r + c];
     }
   }
-  // + T_H h_{d,d}
   for (int a = 0; a < r; ++a) {
     const double t = T[i + (int64_t)(mp + a) * ldT];
     for (int c = 0; c < r; ++c) v[c] += t * hdd[a * r + c];
@@ -222,13 +247,19 @@ __global__ void k_fill_rhs(double* F, int64_t ldF, int r, const double* bU, cons
 
 }  // namespace
 
+int border_chunks(int mp) { return std::max(1, (mp + kBCols - 1) / kBCols); }
+
 void border_col_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, int64_t ldT,
                        const double* hslots, int first_block, int nslots, const double* h_dd,
-                       cudaStream_t st) {
+                       double* partial, cudaStream_t st) {
   if (mp <= 0) return;
+  const int nch = border_chunks(mp);
+  dim3 grid((mp + kBRows - 1) / kBRows, nch);
+  count_launches(1);
+  k_border_gemv<<<grid, kBRows, 0, st>>>(Ht, ldH, mp, r, T, ldT, partial);
   count_launches(1);
   k_border_col<<<(mp + 127) / 128, 128, 0, st>>>(Ht, ldH, mp, r, T, ldT, hslots, first_block,
-                                                 nslots, h_dd);
+                                                 nslots, h_dd, partial, nch);
 }
 
 void border_small_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, int64_t ldT,

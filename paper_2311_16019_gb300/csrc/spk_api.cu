@@ -226,10 +226,14 @@ int grid_rows(spk_handle* h, int64_t n) {
 
 // --------------------------------------------------------------------------
 // Small dense Sylvester solve H Y + Y G^T = F by the scaled Newton iteration
-// for the matrix sign function of [[H, -F], [0, -G^T]]:
+// for the matrix sign function of Z = [[H, -F], [0, -G^T]] (Roberts):
 //   H <- (c H + H^{-1}/c)/2,  G <- (c G + G^{-1}/c)/2,
 //   F <- (c F + H^{-1} F G^{-T} / c)/2,    Y = F_inf / 2,
-// c = |det H det G|^{-1/(2m)} while far from convergence, else 1.
+// with one scalar c for the whole of Z, the 1-norm scaling
+//   c = (||H^{-1}||_1 ||G^{-1}||_1 / (||H||_1 ||G||_1))^{1/4}
+// while the iterates still change by more than 1e-2, c = 1 afterwards.
+// Quadratic convergence: once an update changes H and G by less than 1e-8
+// (relative Frobenius), the next error is below 1e-16 and the loop stops.
 // Requires the spectra of H and G in the open right half plane (true for
 // the convection-diffusion operators here); a zero pivot is reported.
 // In: Hk, Gk, F (m x m, ld m, overwritten); out: F holds Y.
@@ -242,9 +246,12 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
   WS(cvec, double, "sg_cvec", 2 * (size_t)m);
   WS(scalH, double, "sg_scalH", 8);
   WS(scalG, double, "sg_scalG", 8);
+  WS(cs, double, "sg_colsums", 4 * (size_t)m);
+  WS(gpanel, double, "sg_panel", (size_t)m * 64);
+  WS(gbsave, double, "sg_bsave", (size_t)m * 64);
   const int sgrid = sign_combine_grid(m);
   WS(part, double, "sg_part", 4 * (size_t)sgrid);
-  std::vector<double> hpart(4 * (size_t)sgrid);
+  std::vector<double> hpart(4 * (size_t)sgrid), hcs(4 * (size_t)m);
   double delta_prev = 1e300;
   int it = 0;
   for (it = 0; it < max_newton; ++it) {
@@ -253,14 +260,20 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
     {
       const double mm2 = (double)m * m;
       ProfScope ps(h, F_GJE, st, 2 * (m + 2), 2 * 16.0 * mm2 * m, 2 * 2.0 * mm2 * m);
-      GjeState gh{ipiv, cvec, scalH, h->flags};
+      GjeState gh{ipiv, cvec, scalH, h->flags, gpanel, gbsave};
       gje_invert(Hinv, m, m, gh, st);
-      GjeState gg{ipiv, cvec, scalG, h->flags};
+      GjeState gg{ipiv, cvec, scalG, h->flags, gpanel, gbsave};
       gje_invert(Ginv, m, m, gg, st);
     }
-    double ld[2] = {0, 0};
-    CK(cudaMemcpyAsync(&ld[0], scalH, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&ld[1], scalG, sizeof(double), cudaMemcpyDeviceToHost, st));
+    double c = 1.0;
+    const bool scale = delta_prev > 1e-2;
+    if (scale) {
+      col_abs_sums_launch(Hk, m, m, m, cs, st);
+      col_abs_sums_launch(Hinv, m, m, m, cs + m, st);
+      col_abs_sums_launch(Gk, m, m, m, cs + 2 * m, st);
+      col_abs_sums_launch(Ginv, m, m, m, cs + 3 * m, st);
+      CK(cudaMemcpyAsync(hcs.data(), cs, sizeof(double) * 4 * m, cudaMemcpyDeviceToHost, st));
+    }
     TRY(wait_stream(h, st, h->host_wait_s));
     CK(cudaGetLastError());
     uint32_t f = 0;
@@ -269,9 +282,11 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
       *iters_out = it;
       return fail(h, SPK_ERR_SINGULAR_PROJECTED, "zero pivot in sign iteration %d (m=%d)", it, m);
     }
-    double c = 1.0;
-    if (delta_prev > 1e-2) {
-      c = std::exp(-(ld[0] + ld[1]) / (2.0 * m));
+    if (scale) {
+      double n1[4] = {0, 0, 0, 0};
+      for (int q = 0; q < 4; ++q)
+        for (int j = 0; j < m; ++j) n1[q] = std::max(n1[q], hcs[(size_t)q * m + j]);
+      c = std::pow((n1[1] * n1[3]) / (n1[0] * n1[2]), 0.25);
       if (!std::isfinite(c) || c <= 0.0) c = 1.0;
     }
     // F <- (c/2) F + (1/(2c)) (H^{-1} F) G^{-T}
@@ -301,7 +316,7 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
       *iters_out = it + 1;
       return fail(h, SPK_ERR_NONFINITE, "non-finite sign iteration (m=%d)", m);
     }
-    if (delta < 1e-11 || (delta < 1e-6 && delta > 0.5 * delta_prev)) {
+    if (delta < 1e-8) {
       ++it;
       break;
     }
@@ -562,7 +577,8 @@ struct Solver {
     const int groups = (k + 3) / 4;
     SWS(partial, double, "partial",
         (size_t)std::max(std::max(sd.grid, 2 * h->sm_count), 64) * 4 * r * r * std::max(groups, 1));
-    SWS(qpartial, double, "qpartial", (size_t)q_update_chunks((int)mmax) * s * r);
+    SWS(qpartial, double, "qpartial",
+        std::max((size_t)q_update_chunks((int)mmax) * s * r, (size_t)border_chunks((int)mmax) * mmax * r));
     SWS(sk_scratch, TC, "skscratch", std::max<int64_t>(1, sd.sk.npad * r));
 #undef SWS
     if (!sd.sk.identity) {
@@ -720,7 +736,7 @@ struct Solver {
     } else {
       const int nslots = d - i0;  // blocks i0 .. d-1
       border_col_launch(sd.Ht, sd.ldH, mp, r, sd.T, sd.ldT, sd.hslot(d, slot0), i0, nslots,
-                        sd.hslot(d, slot0 + nslots), st);
+                        sd.hslot(d, slot0 + nslots), sd.qpartial, st);
       border_small_launch(sd.Ht, sd.ldH, mp, r, sd.T, sd.ldT, sd.hslot(d - 1, sd.k),
                           sd.hslot(d, slot0 + nslots), st);
     }
@@ -894,17 +910,21 @@ struct Solver {
         break;
       }
       if (o.check_schedule == SPK_CHECK_ADAPTIVE && o.fixed_d <= 0) {
-        // geometric warm-up, then extrapolate log(rho) linearly in d
+        // Doubling warm-up (checks at p, 2p, 4p, ...) until log(rho) has
+        // decreased over two checks; then extrapolate log(rho) linearly in d
+        // from the last two checks and check next at the predicted
+        // convergence iteration plus 5% (rounded up to a multiple of p).
         int nxt = 2 * d;
         const size_t nh = hrel.size();
-        if (nh >= 2 && hrel[nh - 1] < hrel[nh - 2] && hrel[nh - 1] > 0) {
+        if (nh >= 3 && hrel[nh - 1] < hrel[nh - 2] && hrel[nh - 2] < hrel[nh - 3] &&
+            hrel[nh - 1] > 0) {
           const double slope = (std::log(hrel[nh - 1]) - std::log(hrel[nh - 2])) /
                                (double)(hd[nh - 1] - hd[nh - 2]);
           if (slope < 0) {
             const double need = (std::log(o.tol) - std::log(hrel[nh - 1])) / slope;
-            int pred = d + (int)std::ceil(need * 1.03) + 1;
+            int pred = d + (int)std::ceil(need * 1.05) + 1;
             pred = ((pred + o.p - 1) / o.p) * o.p;
-            nxt = std::min(nxt, std::max(pred, d + o.p));
+            nxt = std::max(pred, d + o.p);
           }
         }
         next_check = std::max(d + 1, std::min(nxt, dmax));

@@ -125,9 +125,11 @@ void t_write_launch(double* T, int64_t ldT, int m, int r, const double* t1, cons
                     const double* tau, cudaStream_t st);
 
 // ---------------------------------------------------------------- projected
+// partial: border_chunks(mp) * mp * r doubles of scratch
+int border_chunks(int mp);
 void border_col_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, int64_t ldT,
                        const double* hslots, int first_block, int nslots, const double* h_dd,
-                       cudaStream_t st);
+                       double* partial, cudaStream_t st);
 void border_small_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, int64_t ldT,
                          const double* h_sub, const double* h_dd, cudaStream_t st);
 void border_correct_launch(double* Ht, int64_t ldH, int m, int r, const double* T, int64_t ldT,
@@ -146,9 +148,11 @@ void copy_matrix_launch(const double* A, int64_t lda, double* B, int64_t ldb, in
 void set_zero_launch(double* A, int64_t count, cudaStream_t st);
 struct GjeState {
   int32_t* ipiv;   // m
-  double* cvec;    // m
-  double* scal;    // [0] logdet, [1] pivot, [2..] scratch
+  double* cvec;    // 2 m
+  double* scal;    // [0] log|det|, [2], [3] pivots (ping-pong)
   uint32_t* flags;
+  double* panel = nullptr;   // m x 64 scratch (blocked path)
+  double* bsave = nullptr;   // 64 x m scratch (blocked path)
 };
 void gje_invert(double* A, int64_t lda, int m, GjeState gs, cudaStream_t st);
 int sign_combine_grid(int m);
@@ -169,6 +173,8 @@ void select_sv_launch(const double* sigma, int N, double tol, int* idx, double* 
 // out[:, t] = A[:, idx[t]] * f[t]
 void gather_cols_launch(const double* A, int64_t lda, int M, const int* idx, const double* f,
                         int ncols, double* out, int64_t ldo, cudaStream_t st);
+// out[j] = column absolute sums of A (M x N, column-major)
+void col_abs_sums_launch(const double* A, int64_t lda, int M, int N, double* out, cudaStream_t st);
 // Measured FP64 FMA rate of the device in TFLOP/s (dependent-chain probe).
 double fp64_fma_probe(int sm_count, double* scratch, cudaStream_t st);
 double trace_product(const double* A, const double* B, int n, double* scratch, cudaStream_t st);
