@@ -26,6 +26,7 @@
 #ifndef SPK_H
 #define SPK_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -173,6 +174,26 @@ int spk_spmm(spk_handle* h, const spk_csr* A, const double* X_dev, int32_t r,
 int spk_sylvester_dense(spk_handle* h, int32_t m, const double* H_dev,
                         const double* G_dev, const double* F_dev, double* Y_dev,
                         int32_t* newton_iters_host, void* stream);
+
+/* ---- allocation-free variant ----------------------------------------------
+ * spk_sketch_apply_static: the same S X as spk_sketch_apply (same kernels,
+ * same output layout), without a handle and without allocating device
+ * memory, for callers that cannot let a library call cudaMalloc (a process
+ * that reserved the device heap for its own pool, a framework whose
+ * allocator must remain the only owner of device memory, a service with a
+ * fixed, pre-proven memory budget).  No counterpart in the paper: it is an
+ * interface variant of the sketch step.  Working memory is one file-scope
+ * device array of 10.1 MiB per device, held until the process exits.
+ * Limits: n <= 2^20, 1 <= r <= 4, n' r <= 2^20 (n' = 2^ceil(log2 n)),
+ * 1 <= s <= min(n', 32768); beyond them SPK_ERR_ARG and a message in err
+ * (errlen bytes, may be NULL).  The first call on a device (that device
+ * current) looks up the array's device address; make it before any stream
+ * capture.  All calls on a device share the array and leave their data in
+ * it; calls whose device work overlaps race and must be ordered by the
+ * caller.  Synchronises `stream` before returning.                       */
+int spk_sketch_apply_static(int64_t n, int32_t s, uint64_t seed, int32_t sketch_id,
+                            const double* X_dev, int32_t r, double* SX_dev, void* stream,
+                            char* err, size_t errlen);
 
 /* ---- measurement --------------------------------------------------------
  * spk_launch_count: number of CUDA kernel launches issued by the library

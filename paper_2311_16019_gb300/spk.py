@@ -94,6 +94,8 @@ def load() -> C.CDLL:
         "spk_profile_enable": (i32, [vp, C.c_int]),
         "spk_profile_read": (i32, [vp, C.c_int, P(C.c_char_p), P(dbl), P(i64), P(i64), P(dbl), P(dbl)]),
         "spk_fp64_peak": (i32, [vp, P(dbl), vp]),
+        "spk_sketch_apply_static": (i32, [i64, i32, u64, i32, vp, i32, vp, vp, C.c_char_p,
+                                          C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -386,3 +388,18 @@ def fp64_peak(device: int = 0) -> float:
     if rc != SPK_OK:
         raise SpkError(rc, h.error())
     return v.value
+
+
+def sketch_apply_static(X, s: int, seed: int, sketch_id: int):
+    """S X through the allocation-free entry point (no handle, static scratch)."""
+    torch = _torch()
+    lib = load()
+    x = _block(X)
+    n, r = x.shape
+    SX = torch.empty((r, s), dtype=torch.float64, device="cuda")
+    err = C.create_string_buffer(256)
+    rc = lib.spk_sketch_apply_static(n, s, seed, sketch_id, C.c_void_p(x.data_ptr()), r,
+                                     C.c_void_p(SX.data_ptr()), _stream_ptr(), err, 256)
+    if rc != SPK_OK:
+        raise SpkError(rc, err.value.decode())
+    return SX.t()
