@@ -31,6 +31,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -38,6 +40,13 @@ if ROOT not in sys.path:
 WORKLOAD = "cd2d_512_r4"
 SOLVER = dict(k=4, s=12000, maxit=1500, p=20, tol=1e-8, seed=0, check="adaptive",
               trunc_tol=1e-12)
+
+
+def solver_opts(args):
+    o = dict(SOLVER, s=args.s, maxit=args.maxit, p=args.p, k=args.k)
+    if args.fixed_d > 0:
+        o.update(fixed_d=args.fixed_d, tol=0.0)
+    return o
 
 
 def parse():
@@ -49,6 +58,10 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--maxit", type=int, default=SOLVER["maxit"])
     ap.add_argument("--s", type=int, default=SOLVER["s"])
+    ap.add_argument("--p", type=int, default=SOLVER["p"])
+    ap.add_argument("--k", type=int, default=SOLVER["k"])
+    ap.add_argument("--fixed-d", type=int, default=0,
+                    help="run exactly this many iterations (small profiling cases)")
     ap.add_argument("--forms", default="fp64,mixed_fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -56,6 +69,9 @@ def parse():
     ap.add_argument("--kernel-case", default=None, choices=["gje"],
                     help="run one small isolated case of a kernel family (for ncu captures)")
     ap.add_argument("--m", type=int, default=4200, help="size of the dense case")
+    ap.add_argument("--batched", action="store_true",
+                    help="time the batched form on the 64-instance workload instead")
+    ap.add_argument("--concurrency", type=int, default=8, help="batched-form workers")
     return ap.parse_args()
 
 
@@ -128,6 +144,17 @@ def measured_peaks():
     return 6800.0, 1900.0, "fallback"
 
 
+def fp64_alu_peak(sm_count: int):
+    """FP64 ALU peak in TFLOP/s from unit counts and clocks: each SM retires
+    2 FP64 FMAs per clock (4 flop), at the maximum SM clock."""
+    mhz = 2070.0
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return sm_count * 4 * mhz * 1e6 / 1e12, mhz
+
+
 def dist_setup(n_gpus):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -185,6 +212,21 @@ def pick_roofline(prof: dict, hbm_gbs: float, fp64_tflops: float):
     return roof, table
 
 
+# --------------------------------------------------------------------- accuracy of a result
+def _lowrank_fro(L, R):
+    """||L R^T||_F from the triangular factors of L and R (X is never formed)."""
+    _, Ra = np.linalg.qr(L, mode="reduced")
+    _, Rb = np.linalg.qr(R, mode="reduced")
+    return float(np.linalg.norm(Ra @ Rb.T))
+
+
+def true_residual(A, B, C1, C2, X1, X2):
+    """||A X + X B - C1 C2^T||_F / ||C1 C2^T||_F for X = X1 X2^T, in factored form."""
+    L = np.hstack([A @ X1, X1, -C1])
+    R = np.hstack([X2, B.T @ X2, C2])
+    return _lowrank_fro(L, R) / _lowrank_fro(C1, C2)
+
+
 # --------------------------------------------------------------------- CPU oracle sample
 def oracle_sample(P, opts, iters: int, hist_d, r: int):
     """Time the oracle (FP64 NumPy/SciPy, as it stands) on a bounded sample of
@@ -235,7 +277,7 @@ def run_reference(args, rank, world, pg):
         return
     from paper_2311_16019_gb300 import inputs as I
     P = I.workload(args.workload)
-    opts = dict(SOLVER, s=args.s, maxit=args.maxit)
+    opts = solver_opts(args)
     # schedule to extrapolate to: the oracle's own convergence is unknown at
     # this size, so use the checks of a geometric schedule up to the GPU's
     # typical stopping iteration for this workload (1100 for 512^2, r = 4).
@@ -271,7 +313,7 @@ def run_spk(args, rank, world, local, pg):
     barrier(pg)
     spk.load()
     P = I.workload(args.workload)
-    opts = dict(SOLVER, s=args.s, maxit=args.maxit)
+    opts = solver_opts(args)
     dA, dB = spk.DeviceCSR(P.A), spk.DeviceCSR(P.BT)
     c1 = torch.as_tensor(P.C1, device="cuda")
     c2 = torch.as_tensor(P.C2, device="cuda")
@@ -310,8 +352,7 @@ def run_spk(args, rank, world, local, pg):
         ms_max = max_over_ranks(pg, ms)
         g = results[-1]
         X1, X2 = g.X1.cpu().numpy(), g.X2.cpu().numpy()
-        from oracle import measure as M
-        tres = M.true_residual(P.A, P.B, P.C1, P.C2, X1, X2)
+        tres = true_residual(P.A, P.B, P.C1, P.C2, X1, X2)
         per_form[form] = dict(ms_per_step=ms_max / args.steps,
                               solves_per_s=world * args.steps / (ms_max * 1e-3),
                               iters=g.iters, rank=g.rank, converged=g.converged,
@@ -323,10 +364,11 @@ def run_spk(args, rank, world, local, pg):
             first = form
     base = per_form[first]
     # error of the mixed form against the FP64 GPU form
-    from oracle import measure as M
     for f, v in per_form.items():
         if f != first:
-            v["rel_err_vs_fp64"] = M.rel_error(v["X"][0], v["X"][1], base["X"][0], base["X"][1])
+            v["rel_err_vs_fp64"] = (_lowrank_fro(np.hstack([v["X"][0], -base["X"][0]]),
+                                                 np.hstack([v["X"][1], base["X"][1]]))
+                                    / _lowrank_fro(*base["X"]))
     # end-to-end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -357,9 +399,13 @@ def run_spk(args, rank, world, local, pg):
         secs = max_over_ranks(pg, time.perf_counter() - t0)
         e2e = {"value": world * args.steps / secs, "unit": "solves/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
-    roof, table = pick_roofline(base["prof"] or {}, hbm, fp64)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp64_peak, mhz = fp64_alu_peak(sms)
+    roof, table = pick_roofline(base["prof"] or {}, hbm, fp64_peak)
     if roof is not None:
-        roof["peak_source"] = f"{peak_src} (HBM GB/s from MEASURED_PEAKS.json); FP64 TFLOP/s measured live"
+        roof["peak_source"] = (f"HBM: {peak_src} copy GB/s (MEASURED_PEAKS.json); FP64 ALU: derived, "
+                               f"{sms} SMs x 2 FMA/clk x 2 flop x {mhz:.0f} MHz = {fp64_peak:.4f} "
+                               f"TFLOP/s (live FMA probe {fp64:.4f})")
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         s = oracle_sample(P, opts, args.cpu_sample_iters, base["checks"], P.r)
@@ -411,10 +457,68 @@ def run_kernel_case(args):
                       "seconds": time.perf_counter() - t0}), flush=True)
 
 
+def batched_opts(P, form, maxit=2000):
+    """Per-instance options of the batched workload: k = 4, tol 1e-8, p = 20,
+    s = min(n', 2 r maxit) and maxit clamped so that s >= (maxit + 1) r."""
+    npad = 1 << (P.n1 - 1).bit_length()
+    s = min(npad, 2 * P.r * maxit)
+    return dict(k=4, s=s, maxit=min(maxit, s // P.r - 1), p=20, tol=1e-8, seed=4,
+                check="adaptive", trunc_tol=1e-12, precision=form)
+
+
+def run_batched(args):
+    """The batched form on 64 uneven conv-diff instances (N uniform in
+    [64, 384], theta in [1, 50], r in {1, 2, 4}), solved by concurrent
+    workers; one step = the whole batch."""
+    import torch
+    from paper_2311_16019_gb300 import build, inputs as I, spk
+    build.build()
+    spk.load()
+    form = args.forms.split(",")[0]
+    probs = I.batched_instances(count=64, seed=4)
+    opts = [batched_opts(P, form) for P in probs]
+    dev = [(spk.DeviceCSR(P.A), spk.DeviceCSR(P.BT)) for P in probs]
+
+    class Inst:
+        pass
+    insts = []
+    for P, (dA, dB) in zip(probs, dev):
+        o = Inst()
+        o.A, o.BT = dA, dB
+        o.C1 = torch.as_tensor(P.C1, device="cuda")
+        o.C2 = torch.as_tensor(P.C2, device="cuda")
+        insts.append(o)
+    for _ in range(args.warmup):
+        spk.solve_batched(insts, concurrency=args.concurrency, opts_list=opts, raise_on_error=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    outs = None
+    for _ in range(args.steps):
+        rc, outs = spk.solve_batched(insts, concurrency=args.concurrency, opts_list=opts,
+                                     raise_on_error=False)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    conv = sum(1 for g in outs if g is not None and g.converged)
+    failed = sum(1 for g in outs if g is None)
+    line = {"metric": "solves/s, batched form (64 uneven instances)",
+            "value": len(insts) * args.steps / secs, "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f32+f64" if form != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": "batch64: N~U{64..384}, theta~U[1,50], r~U{1,2,4}, k=4, "
+                                   "tol=1e-8, p=20 adaptive", "form": form,
+                       "concurrency": args.concurrency},
+            "seconds_per_batch": secs / args.steps, "converged": conv, "failed": failed,
+            "iters": [g.iters if g is not None else None for g in outs]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.kernel_case:
         run_kernel_case(args)
+        return
+    if args.batched:
+        run_batched(args)
         return
     rank, world, local, pg = dist_setup(args.gpus)
     if args.impl == "reference":

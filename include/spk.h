@@ -53,6 +53,11 @@ enum {
 enum { SPK_SKETCH_SRHT = 0, SPK_SKETCH_IDENTITY = 1 };
 enum { SPK_PREC_FP64 = 0, SPK_PREC_MIXED_FP32 = 1, SPK_PREC_MIXED_BF16 = 2 };
 enum { SPK_CHECK_EVERY_P = 0, SPK_CHECK_ADAPTIVE = 1 };
+/* SPK_METHOD_SKETCHED: Algorithm 1 (s-PKSM, whitened by the sketch).
+ * SPK_METHOD_TRUNCATED: Algorithm 2 (t-PKSM): the same truncated Arnoldi
+ * without sketch or whitening; projected equation with the banded H_d, G_d
+ * and the residual bound of Proposition 3.1 (Eq. (3.3)); s is ignored.    */
+enum { SPK_METHOD_SKETCHED = 0, SPK_METHOD_TRUNCATED = 1 };
 /* host-side fault injection bits for spk_opts.inject (tests only) */
 enum {
     SPK_INJECT_NAN_C1 = 1u << 0,      /* treat C1 as containing a NaN          */
@@ -92,7 +97,8 @@ typedef struct spk_opts {
     double tol;              /* stop when rho / ||beta1 beta2^T||_F < tol      */
     double trunc_tol;        /* keep singular values of Y above trunc_tol*s_1  */
     uint64_t seed;           /* sketch draws (SplitMix64 streams)              */
-    int32_t reserved[8];
+    int32_t method;          /* SPK_METHOD_*                                   */
+    int32_t reserved[7];
 } spk_opts;
 
 /* Result of a solve.  X1/X2 and the history arrays are library-owned and
@@ -153,6 +159,33 @@ int spk_adjoint_gradients(spk_handle* h, const spk_result* X, const spk_result* 
                           void* stream);
 
 void spk_result_free(spk_result* res);
+
+/* ---- batched form -------------------------------------------------------
+ * One instance of Eq. (1.1) for spk_solve_batched: device CSR operators and
+ * factors (caller-owned, as for spk_solve), its own r and options.        */
+typedef struct spk_problem {
+    spk_csr A;               /* left operator, n1 x n1                         */
+    spk_csr BT;              /* B^T, n2 x n2                                   */
+    const double* C1_dev;    /* n1 x r row-major                               */
+    const double* C2_dev;    /* n2 x r row-major                               */
+    int32_t r;
+    int32_t reserved0;
+    spk_opts opts;
+} spk_problem;
+
+/* spk_solve_batched: Algorithm 1 for `count` independent instances of
+ * uneven sizes.  Up to `concurrency` workers (1..64), each with its own
+ * stream and workspace kept in the handle between calls, take the
+ * instances in index order, so that small instances share the SMs.  All
+ * workers start after the work already queued on `stream`, and `stream`
+ * waits for all of them.  outs[i] is filled as by spk_solve (free each with
+ * spk_result_free) and outs[i].status is that instance's status.  Returns
+ * SPK_OK when every instance ended with SPK_OK or SPK_ERR_NOT_CONVERGED,
+ * else the status of the lowest-index instance that did not (its message
+ * in spk_last_error(h)).  A worker's results are bitwise those of spk_solve
+ * on the same instance.                                                   */
+int spk_solve_batched(spk_handle* h, int32_t count, const spk_problem* probs,
+                      int32_t concurrency, void* stream, spk_result* outs);
 
 /* ---- single steps, for parity tests ----------------------------------- */
 /* Sketch draws (Section 2.2; SplitMix64 streams as documented in the

@@ -29,26 +29,6 @@ __device__ __forceinline__ void load_row(const TB* p, TC (&v)[R]) {
   for (int a = 0; a < R; ++a) v[a] = (TC)Store<TB>::ld(p + a);
 }
 
-// Block-wide sum of NV per-thread values; thread e < NV of warp 0..: result to out[e].
-template <int NV>
-__device__ void block_reduce_store(double (&acc)[NV], double* out) {
-  __shared__ double red[32][NV > 0 ? NV : 1];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-#pragma unroll
-  for (int e = 0; e < NV; ++e) {
-    double v = warp_sum(acc[e]);
-    if (lane == 0) red[wid][e] = v;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < NV; e += blockDim.x) {
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += red[w][e];
-    out[e] = s;
-  }
-  __syncthreads();
-}
-
 template <typename TB, typename TC, typename TV, int R, bool DOTS>
 __global__ void __launch_bounds__(256) k_spmm_dots(const int32_t* __restrict__ rowptr,
                                                    const int32_t* __restrict__ col,
@@ -91,7 +71,7 @@ __global__ void __launch_bounds__(256) k_spmm_dots(const int32_t* __restrict__ r
       }
     }
   }
-  if constexpr (DOTS) block_reduce_store<kFuse * R * R>(acc, partial + (int64_t)blockIdx.x * kFuse * R * R);
+  if constexpr (DOTS) block_sum_store<kFuse * R * R>(acc, partial + (int64_t)blockIdx.x * kFuse * R * R);
 }
 
 // Dots of an already computed U~ against up to four more window blocks.
@@ -119,7 +99,7 @@ __global__ void __launch_bounds__(256) k_dots(const TC* __restrict__ W, int64_t 
       }
     }
   }
-  block_reduce_store<kFuse * R * R>(acc, partial + (int64_t)blockIdx.x * kFuse * R * R);
+  block_sum_store<kFuse * R * R>(acc, partial + (int64_t)blockIdx.x * kFuse * R * R);
 }
 
 __global__ void k_reduce_partials(const double* __restrict__ partial, int nparts, int stride,
@@ -167,7 +147,7 @@ __global__ void __launch_bounds__(256) k_update_gram(TC* __restrict__ W, int64_t
         for (int b = 0; b < R; ++b) acc[a * R + b] = fma((double)w[a], (double)w[b], acc[a * R + b]);
     }
   }
-  if (want_gram) block_reduce_store<R * R>(acc, partial + (int64_t)blockIdx.x * R * R);
+  if (want_gram) block_sum_store<R * R>(acc, partial + (int64_t)blockIdx.x * R * R);
 }
 
 // G = sum of partial Grams; R upper with R^T R = G; Rinv = R^{-1}.
@@ -252,7 +232,7 @@ __global__ void __launch_bounds__(256) k_scale_gram(TC* __restrict__ W, int64_t 
 #pragma unroll
       for (int b = 0; b < R; ++b) acc[a * R + b] = fma((double)o[a], (double)o[b], acc[a * R + b]);
   }
-  block_reduce_store<R * R>(acc, partial + (int64_t)blockIdx.x * R * R);
+  block_sum_store<R * R>(acc, partial + (int64_t)blockIdx.x * R * R);
 }
 
 template <typename TB, typename TC, int R>

@@ -459,12 +459,13 @@ __global__ void k_gather_cols(const double* __restrict__ A, int64_t lda, int M,
 }
 
 // scratch[0] = sum_{i,j} A[i + j n] B[j + i n]  = trace(A B), n x n column-major
-__global__ void k_trace_product(const double* __restrict__ A, const double* __restrict__ B, int n,
-                                double* out) {
+// out[0] = trace(A B) = sum_{i<p, j<q} A[i + j*p] B[j + i*q]  (A p x q, B q x p)
+__global__ void k_trace_product(const double* __restrict__ A, const double* __restrict__ B, int p,
+                                int q, double* out) {
   double s = 0.0;
-  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
-    const int64_t j = e / n, i = e - j * n;
-    s = fma(A[i + j * n], B[j + i * n], s);
+  for (int64_t e = threadIdx.x; e < (int64_t)p * q; e += blockDim.x) {
+    const int64_t j = e / p, i = e - j * p;
+    s = fma(A[i + j * p], B[j + i * q], s);
   }
   __shared__ double r[32];
   s = warp_sum(s);
@@ -474,6 +475,33 @@ __global__ void k_trace_product(const double* __restrict__ A, const double* __re
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += r[w];
     out[0] = t;
+  }
+}
+
+// out2 = {trace(A), trace(B)} for m x m A, B (one block, fixed order).
+__global__ void k_diag_sums(const double* __restrict__ A, int64_t lda, const double* __restrict__ B,
+                            int64_t ldb, int m, double* __restrict__ out2) {
+  __shared__ double red[2][32];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    a += A[i + (int64_t)i * lda];
+    b += B[i + (int64_t)i * ldb];
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sa += red[0][w];
+      sb += red[1][w];
+    }
+    out2[0] = sa;
+    out2[1] = sb;
   }
 }
 
@@ -602,6 +630,12 @@ void col_norms_launch(const double* A, int64_t lda, int M, int N, double* out, c
   k_col_norms<<<N, 256, 0, st>>>(A, lda, M, out);
 }
 
+void diag_sums_launch(const double* A, int64_t lda, const double* B, int64_t ldb, int m,
+                      double* out2, cudaStream_t st) {
+  count_launches(1);
+  k_diag_sums<<<1, 256, 0, st>>>(A, lda, B, ldb, m, out2);
+}
+
 void col_abs_sums_launch(const double* A, int64_t lda, int M, int N, double* out, cudaStream_t st) {
   if (N <= 0) return;
   count_launches(1);
@@ -641,13 +675,10 @@ void gather_cols_launch(const double* A, int64_t lda, int M, const int* idx, con
   k_gather_cols<<<grid_for((int64_t)M * ncols, 256), 256, 0, st>>>(A, lda, M, idx, f, ncols, out, ldo);
 }
 
-double trace_product(const double* A, const double* B, int n, double* scratch, cudaStream_t st) {
+void trace_product_launch(const double* A, const double* B, int p, int q, double* out,
+                          cudaStream_t st) {
   count_launches(1);
-  k_trace_product<<<1, 256, 0, st>>>(A, B, n, scratch);
-  double h = 0.0;
-  cudaMemcpyAsync(&h, scratch, sizeof(double), cudaMemcpyDeviceToHost, st);
-  cudaStreamSynchronize(st);
-  return h;
+  k_trace_product<<<1, 256, 0, st>>>(A, B, p, q, out);
 }
 
 }  // namespace spk

@@ -180,24 +180,39 @@ __global__ void k_border_correct(double* __restrict__ Ht, int64_t ldH, int m, in
 }
 
 // out3 = {rho, rho/||beta_U beta_V^T||_F, ||beta_U beta_V^T||_F}
+// Residual estimate at a check (Y m x m column-major, ld ldY).
+// Sketched method (TU, TV given), Eq. (3.5) with the whitened subdiagonal
+// blocks hhat = tau_{d+1} h_{d+1,d} tau_d^{-1} (and ghat likewise):
+//   rho = sqrt(||hhat E_d^T Y||_F^2 + ||Y E_d ghat^T||_F^2).
+// Truncated method (TU == nullptr), the bound of Proposition 3.1 (Eq. (3.3)):
+//   rho = sqrt(m) (||h E_d^T Y||_F + ||Y E_d g^T||_F),  h = h_{d+1,d}.
+// out3 = {rho, rho / ||beta1 beta2^T||_F, ||beta1 beta2^T||_F}.
 __global__ void k_rho(const double* __restrict__ Y, int64_t ldY, int m, int r,
                       const double* __restrict__ TU, int64_t ldTU, const double* __restrict__ TV,
                       int64_t ldTV, const double* __restrict__ hU, const double* __restrict__ hV,
                       const double* __restrict__ bU, const double* __restrict__ bV,
                       double* __restrict__ out3) {
   __shared__ double hh[kMaxR * kMaxR], gh[kMaxR * kMaxR];
-  __shared__ double red[32];
+  __shared__ double red[2][32];
   __shared__ double nb;
+  const bool sketched = TU != nullptr;
   if (threadIdx.x == 0) {
-    double tau[kMaxR * kMaxR], tinv[kMaxR * kMaxR], X[kMaxR * kMaxR];
-    tblock(TU, ldTU, m, r, tau);
-    upper_inv(TU, ldTU, m - r, r, tinv);
-    mm(tau, hU, X, r);
-    mm(X, tinv, hh, r);
-    tblock(TV, ldTV, m, r, tau);
-    upper_inv(TV, ldTV, m - r, r, tinv);
-    mm(tau, hV, X, r);
-    mm(X, tinv, gh, r);
+    if (sketched) {
+      double tau[kMaxR * kMaxR], tinv[kMaxR * kMaxR], X[kMaxR * kMaxR];
+      tblock(TU, ldTU, m, r, tau);
+      upper_inv(TU, ldTU, m - r, r, tinv);
+      mm(tau, hU, X, r);
+      mm(X, tinv, hh, r);
+      tblock(TV, ldTV, m, r, tau);
+      upper_inv(TV, ldTV, m - r, r, tinv);
+      mm(tau, hV, X, r);
+      mm(X, tinv, gh, r);
+    } else {
+      for (int e = 0; e < r * r; ++e) {
+        hh[e] = hU[e];
+        gh[e] = hV[e];
+      }
+    }
     double s = 0.0;
     for (int a = 0; a < r; ++a)
       for (int b = 0; b < r; ++b) {
@@ -208,41 +223,69 @@ __global__ void k_rho(const double* __restrict__ Y, int64_t ldY, int m, int r,
     nb = sqrt(s);
   }
   __syncthreads();
-  double acc = 0.0;
+  double accH = 0.0, accG = 0.0;
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     // row block: (hhat Y[m-r:m, j])_a
     for (int a = 0; a < r; ++a) {
       double s = 0.0;
       for (int b = 0; b < r; ++b) s += hh[a * r + b] * Y[m - r + b + (int64_t)j * ldY];
-      acc += s * s;
+      accH += s * s;
     }
     // column block: (Y[j, m-r:m] ghat^T)_a
     for (int a = 0; a < r; ++a) {
       double s = 0.0;
       for (int b = 0; b < r; ++b) s += Y[j + (int64_t)(m - r + b) * ldY] * gh[a * r + b];
-      acc += s * s;
+      accG += s * s;
     }
   }
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  accH = warp_sum(accH);
+  accG = warp_sum(accG);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = accH;
+    red[1][threadIdx.x >> 5] = accG;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    const double rho = sqrt(s);
+    double sH = 0.0, sG = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sH += red[0][w];
+      sG += red[1][w];
+    }
+    const double rho = sketched ? sqrt(sH + sG) : sqrt((double)m) * (sqrt(sH) + sqrt(sG));
     out3[0] = rho;
     out3[1] = rho / nb;
     out3[2] = nb;
   }
 }
 
-__global__ void k_fill_rhs(double* F, int64_t ldF, int r, const double* bU, const double* bV) {
+// Dense H_d (m x m column-major, zeroed beforehand) from the stored Arnoldi
+// coefficients: block column j (1..d) holds h_{i,j} for the window rows
+// i = j-k+1 .. j and h_{j+1,j} (slot q <-> i = j-k+1+q), rows i in [1, d].
+__global__ void k_band_to_dense(const double* __restrict__ hband, int k, int r, int d,
+                                double* __restrict__ H, int64_t ldH) {
+  const int64_t per_col = (int64_t)(k + 1) * r * r;
+  const int64_t total = (int64_t)d * per_col;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / per_col) + 1;
+    const int64_t rem = e - (int64_t)(j - 1) * per_col;
+    const int q = (int)(rem / (r * r));
+    const int ac = (int)(rem - (int64_t)q * r * r);
+    const int a = ac / r, c = ac - a * r;
+    const int i = j - k + 1 + q;
+    if (i < 1 || i > d) continue;
+    H[(int64_t)(i - 1) * r + a + ((int64_t)(j - 1) * r + c) * ldH] =
+        hband[(int64_t)j * per_col + (int64_t)q * r * r + a * r + c];
+  }
+}
+
+// L[a + l*ldL] = beta[a*r + l]: the r x r row-major beta into the top of a
+// column-major factor.
+__global__ void k_fill_factor(double* L, int64_t ldL, int r, const double* beta) {
   const int e = threadIdx.x;
   if (e >= r * r) return;
-  const int a = e / r, b = e - a * r;
-  double s = 0.0;
-  for (int l = 0; l < r; ++l) s += bU[a * r + l] * bV[b * r + l];
-  F[a + (int64_t)b * ldF] = s;
+  const int a = e / r, l = e - a * r;
+  L[a + (int64_t)l * ldL] = beta[a * r + l];
 }
 
 }  // namespace
@@ -281,11 +324,17 @@ void rho_launch(const double* Y, int64_t ldY, int m, int r, const double* TU, in
   k_rho<<<1, 256, 0, st>>>(Y, ldY, m, r, TU, ldTU, TV, ldTV, hU, hV, betaU, betaV, out3);
 }
 
-void fill_rhs_launch(double* F, int64_t ldF, int m, int r, const double* betaU,
-                     const double* betaV, cudaStream_t st) {
-  (void)m;
+void band_to_dense_launch(const double* hband, int k, int r, int d, double* H, int64_t ldH,
+                          cudaStream_t st) {
+  const int64_t total = (int64_t)d * (k + 1) * r * r;
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 4));
   count_launches(1);
-  k_fill_rhs<<<1, 32, 0, st>>>(F, ldF, r, betaU, betaV);
+  k_band_to_dense<<<g, 256, 0, st>>>(hband, k, r, d, H, ldH);
+}
+
+void fill_factor_launch(double* L, int64_t ldL, int r, const double* beta, cudaStream_t st) {
+  count_launches(1);
+  k_fill_factor<<<1, 32, 0, st>>>(L, ldL, r, beta);
 }
 
 }  // namespace spk

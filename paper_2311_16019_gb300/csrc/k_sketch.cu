@@ -21,6 +21,8 @@
 //         rho_hi; one warp per row, fixed summation order (deterministic).
 #include "spk_internal.cuh"
 
+#include <atomic>
+
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -274,11 +276,15 @@ void sketch_apply_launch(const SketchDev& sk, const TB* X, int r, double* SX, TC
     return;
   }
   const size_t smem = (size_t)sk.n2 * r * sizeof(TC);
-  static bool attr_set = false;
-  if (!attr_set) {
+  // the shared-memory opt-in is per device: one bit per device, set once
+  static std::atomic<uint64_t> attr_set{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t bit = 1ull << (dev & 63);
+  if (!(attr_set.load(std::memory_order_acquire) & bit)) {
     cudaFuncSetAttribute(k_fwht_chunks<TB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          128 * 1024 * 2 / 2 + 1024);
-    attr_set = true;
+    attr_set.fetch_or(bit, std::memory_order_acq_rel);
   }
   int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(32, (int64_t)sk.n2 * r / 2));
   count_launches(1);

@@ -15,19 +15,28 @@ namespace spk {
 
 namespace {
 
-// t[j*r + c] = sum_i Q[i + j*ldq] * w[i + c*s]; one warp per column j.
+// Partial dot products of the columns of Q with w over one chunk of rows:
+//   tpart[(ch*m + j)*R + c] = sum_{i in chunk ch} Q[i + j*ldq] * w[i + c*s],
+// one warp per (column j, row chunk ch).  Splitting the rows gives enough
+// equal work items to keep every SM's FP64 pipe busy to the end (one warp
+// per column alone leaves a partial last wave on 152 SMs).
 template <int R>
 __global__ void __launch_bounds__(256) k_qt_dot(const double* __restrict__ Q, int64_t ldq, int64_t s,
-                                                int m, const double* __restrict__ w,
-                                                double* __restrict__ t) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                                                int m, int64_t rows_per_chunk, int nchunk,
+                                                const double* __restrict__ w,
+                                                double* __restrict__ tpart) {
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (warp >= m) return;
-  const double* q = Q + (int64_t)warp * ldq;
+  if (item >= (int64_t)m * nchunk) return;
+  const int j = (int)(item % m);
+  const int ch = (int)(item / m);
+  const int64_t i0 = (int64_t)ch * rows_per_chunk;
+  const int64_t i1 = min(s, i0 + rows_per_chunk);
+  const double* q = Q + (int64_t)j * ldq;
   double acc[R];
 #pragma unroll
   for (int c = 0; c < R; ++c) acc[c] = 0.0;
-  for (int64_t i = lane; i < s; i += 32) {
+  for (int64_t i = i0 + lane; i < i1; i += 32) {
     const double qi = q[i];
 #pragma unroll
     for (int c = 0; c < R; ++c) acc[c] = fma(qi, w[i + c * s], acc[c]);
@@ -35,12 +44,24 @@ __global__ void __launch_bounds__(256) k_qt_dot(const double* __restrict__ Q, in
 #pragma unroll
   for (int c = 0; c < R; ++c) {
     const double v = warp_sum(acc[c]);
-    if (lane == 0) t[(int64_t)warp * R + c] = v;
+    if (lane == 0) tpart[((int64_t)ch * m + j) * R + c] = v;
   }
 }
 
-constexpr int kRowTile = 256;
+// t[e] = sum_ch tpart[ch*m*R + e], chunks in ascending order.
+__global__ void k_qt_finish(const double* __restrict__ tpart, int64_t count, int nchunk,
+                            double* __restrict__ t) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) acc += tpart[(int64_t)ch * count + e];
+    t[e] = acc;
+  }
+}
+
+constexpr int kRowTile = 128;
 constexpr int kColChunk = 256;
+constexpr int kQtMaxChunks = 16;
 
 // partial[(chunk*s + i)*r + c] = sum_{j in chunk} Q[i + j*ldq] * t[j*r + c]
 template <int R>
@@ -84,24 +105,6 @@ __global__ void k_q_update_finish(const double* __restrict__ w_in, double* __res
   }
 }
 
-template <int NV>
-__device__ void block_reduce_store(double (&acc)[NV], double* out) {
-  __shared__ double red[32][NV];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-#pragma unroll
-  for (int e = 0; e < NV; ++e) {
-    double v = warp_sum(acc[e]);
-    if (lane == 0) red[wid][e] = v;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < NV; e += blockDim.x) {
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += red[w][e];
-    out[e] = s;
-  }
-}
-
 template <int R>
 __global__ void __launch_bounds__(256) k_ts_gram(const double* __restrict__ w, int64_t s,
                                                  double* __restrict__ partial) {
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(256) k_ts_gram(const double* __restrict__ w, i
 #pragma unroll
       for (int b = 0; b < R; ++b) acc[a * R + b] = fma(v[a], v[b], acc[a * R + b]);
   }
-  block_reduce_store<R * R>(acc, partial + (int64_t)blockIdx.x * R * R);
+  block_sum_store<R * R>(acc, partial + (int64_t)blockIdx.x * R * R);
 }
 
 // out[i + c*ldo] = sum_{a<=c} w[i + a*s] Rinv[a][c]   (w may alias out when ldo == s)
@@ -169,17 +172,35 @@ int grid_for(int64_t work, int block) {
 
 }  // namespace
 
+int qt_dot_chunks(int64_t s, int m) {
+  // about four waves of 8-warp blocks over 152 SMs, at least 256 rows per chunk
+  const int64_t target = 4LL * 152 * 64;
+  int64_t nc = (target + m - 1) / std::max(1, m);
+  nc = std::min<int64_t>(nc, std::max<int64_t>(1, s / 256));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(nc, kQtMaxChunks));
+}
+
 void qt_dot_launch(const double* Q, int64_t ldq, int64_t s, int m, const double* w, int r,
-                   double* t, cudaStream_t st) {
+                   double* t, double* tpart, cudaStream_t st) {
   if (m <= 0) return;
-  const int blocks = (m + 7) / 8;
+  const int nc = qt_dot_chunks(s, m);
+  const int64_t rows = ((s + nc - 1) / nc + 31) / 32 * 32;
+  double* out = nc == 1 ? t : tpart;
+  const unsigned blocks = (unsigned)(((int64_t)m * nc + 7) / 8);
+  count_launches(1);
   switch (r) {
-    case 1: count_launches(1); k_qt_dot<1><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
-    case 2: count_launches(1); k_qt_dot<2><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
-    case 3: count_launches(1); k_qt_dot<3><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
-    default: count_launches(1); k_qt_dot<4><<<blocks, 256, 0, st>>>(Q, ldq, s, m, w, t); break;
+    case 1: k_qt_dot<1><<<blocks, 256, 0, st>>>(Q, ldq, s, m, rows, nc, w, out); break;
+    case 2: k_qt_dot<2><<<blocks, 256, 0, st>>>(Q, ldq, s, m, rows, nc, w, out); break;
+    case 3: k_qt_dot<3><<<blocks, 256, 0, st>>>(Q, ldq, s, m, rows, nc, w, out); break;
+    default: k_qt_dot<4><<<blocks, 256, 0, st>>>(Q, ldq, s, m, rows, nc, w, out); break;
+  }
+  if (nc > 1) {
+    count_launches(1);
+    k_qt_finish<<<grid_for((int64_t)m * r, 256), 256, 0, st>>>(tpart, (int64_t)m * r, nc, t);
   }
 }
+
+int qt_dot_partial_doubles(int mmax, int r) { return kQtMaxChunks * mmax * r; }
 
 void q_update_launch(const double* Q, int64_t ldq, int64_t s, int m, const double* t, int r,
                      const double* w_in, double* w_out, double* partial, int nchunk,

@@ -14,6 +14,7 @@
 #include "spk_internal.cuh"
 
 #include <algorithm>
+#include <thread>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -46,7 +47,7 @@ enum ProfFam {
 };
 static const char* kFamNames[F_COUNT] = {
   "spmm_dots", "gs_update", "cholqr_scale", "sketch_srht", "whiten_qt_dot", "whiten_q_update",
-  "whiten_cholqr", "border_update", "gje_step", "gemm_f64", "sign_combine", "rho", "truncate_svd",
+  "whiten_cholqr", "border_update", "gje_invert", "gemm_f64", "sign_combine", "rho", "truncate_svd",
   "trsm", "x_accumulate"};
 
 struct ProfAcc {
@@ -100,19 +101,33 @@ struct spk_handle {
   uint32_t* flags = nullptr;
   double host_wait_s = 600.0;
   Profiler prof;
+  // second stream and fork/join events: the two inversions of a sign step
+  // run concurrently (each one's latency-bound panel sweeps overlap the
+  // other's GEMM updates)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // batched form: worker handles, each with its own stream and workspace
+  struct Worker {
+    spk_handle* h = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+  };
+  std::vector<Worker> workers;
 };
 
 namespace {
-// RAII timing of one group of launches of one family.
+// RAII timing of one group of launches of one family.  `bytes` and `flops`
+// are the group's algorithmic traffic and work; the launch count is taken
+// from the library's launch counter over the scope.
 struct ProfScope {
   spk_handle* h;
   int f;
   cudaStream_t st;
-  int64_t launches;
+  int64_t l0;
   double bytes, flops;
   cudaEvent_t a = nullptr;
-  ProfScope(spk_handle* h_, int f_, cudaStream_t st_, int64_t l, double by, double fl)
-      : h(h_), f(f_), st(st_), launches(l), bytes(by), flops(fl) {
+  ProfScope(spk_handle* h_, int f_, cudaStream_t st_, double by, double fl)
+      : h(h_), f(f_), st(st_), l0(launch_count()), bytes(by), flops(fl) {
     if (h->prof.on) {
       a = h->prof.get();
       cudaEventRecord(a, st);
@@ -122,7 +137,7 @@ struct ProfScope {
     if (!a) return;
     cudaEvent_t b = h->prof.get();
     cudaEventRecord(b, st);
-    h->prof.pend.push_back({f, a, b, launches, bytes, flops});
+    h->prof.pend.push_back({f, a, b, launch_count() - l0, bytes, flops});
     if (h->prof.pend.size() > 8192) h->prof.resolve();
   }
 };
@@ -237,33 +252,53 @@ int grid_rows(spk_handle* h, int64_t n) {
 // Requires the spectra of H and G in the open right half plane (true for
 // the convection-diffusion operators here); a zero pivot is reported.
 // In: Hk, Gk, F (m x m, ld m, overwritten); out: F holds Y.
+//
+// Low-rank right-hand side (Lf != nullptr): F_0 = L_0 R_0^T with q0 columns
+// (the projected equation's right-hand side E_1 beta_1 beta_2^T E_1^T has
+// rank r), and the input F is not read.  The F update then keeps factors,
+//   L <- [sqrt(c/2) L, H^{-1} L / sqrt(2c)],  R <- [sqrt(c/2) R, G^{-1} R / sqrt(2c)],
+// which doubles the column count per step at 4 m^2 q flops instead of the
+// 8 m^3 of the two dense products; once 2q would pass qcap (the factors'
+// capacity) the product is formed and the iteration continues densely.
 int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_newton,
-               cudaStream_t st, int* iters_out) {
+               cudaStream_t st, int* iters_out, double* Lf = nullptr, double* Rf = nullptr,
+               int q0 = 0, int qcap = 0) {
+  bool fact = Lf != nullptr && Rf != nullptr && q0 > 0;
+  int q = q0;
   WS(Hinv, double, "sg_Hinv", (size_t)m * m);
   WS(Ginv, double, "sg_Ginv", (size_t)m * m);
   WS(P, double, "sg_P", (size_t)m * m);
   WS(ipiv, int32_t, "sg_ipiv", m);
   WS(cvec, double, "sg_cvec", 2 * (size_t)m);
+  WS(ipivG, int32_t, "sg_ipivG", m);
+  WS(cvecG, double, "sg_cvecG", 2 * (size_t)m);
   WS(scalH, double, "sg_scalH", 8);
   WS(scalG, double, "sg_scalG", 8);
   WS(cs, double, "sg_colsums", 4 * (size_t)m);
   WS(gpanel, double, "sg_panel", (size_t)m * 64);
   WS(gbsave, double, "sg_bsave", (size_t)m * 64);
+  WS(gpanelG, double, "sg_panelG", (size_t)m * 64);
+  WS(gbsaveG, double, "sg_bsaveG", (size_t)m * 64);
   const int sgrid = sign_combine_grid(m);
   WS(part, double, "sg_part", 4 * (size_t)sgrid);
   std::vector<double> hpart(4 * (size_t)sgrid), hcs(4 * (size_t)m);
   double delta_prev = 1e300;
+  bool converged = false;
   int it = 0;
   for (it = 0; it < max_newton; ++it) {
     CK(cudaMemcpyAsync(Hinv, Hk, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(Ginv, Gk, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
     {
       const double mm2 = (double)m * m;
-      ProfScope ps(h, F_GJE, st, 2 * (m + 2), 2 * 16.0 * mm2 * m, 2 * 2.0 * mm2 * m);
+      ProfScope ps(h, F_GJE, st, 2 * 16.0 * mm2, 2 * 2.0 * mm2 * m);
       GjeState gh{ipiv, cvec, scalH, h->flags, gpanel, gbsave};
+      GjeState gg{ipivG, cvecG, scalG, h->flags, gpanelG, gbsaveG};
+      CK(cudaEventRecord(h->ev_fork, st));
+      CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
       gje_invert(Hinv, m, m, gh, st);
-      GjeState gg{ipiv, cvec, scalG, h->flags, gpanel, gbsave};
-      gje_invert(Ginv, m, m, gg, st);
+      gje_invert(Ginv, m, m, gg, h->aux);
+      CK(cudaEventRecord(h->ev_join, h->aux));
+      CK(cudaStreamWaitEvent(st, h->ev_join, 0));
     }
     double c = 1.0;
     const bool scale = delta_prev > 1e-2;
@@ -289,16 +324,32 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
       c = std::pow((n1[1] * n1[3]) / (n1[0] * n1[2]), 0.25);
       if (!std::isfinite(c) || c <= 0.0) c = 1.0;
     }
-    // F <- (c/2) F + (1/(2c)) (H^{-1} F) G^{-T}
-    {
+    if (fact && 2 * q > qcap) {
+      // the factors would outgrow their capacity: F = L R^T from here on
       const double mm2 = (double)m * m;
-      ProfScope ps(h, F_GEMM, st, 2, 7 * 8.0 * mm2, 4.0 * mm2 * m);
+      ProfScope ps(h, F_GEMM, st, 8.0 * (mm2 + 2.0 * m * q), 2.0 * mm2 * q);
+      gemm_f64('N', 'T', m, m, q, 1.0, Lf, m, Rf, m, 0.0, F, m, st);
+      fact = false;
+    }
+    if (fact) {
+      const double mm2 = (double)m * m;
+      ProfScope ps(h, F_GEMM, st, 2 * 8.0 * (mm2 + 3.0 * m * q), 2 * 2.0 * mm2 * q);
+      const double a_new = 1.0 / std::sqrt(2.0 * c), a_old = std::sqrt(0.5 * c);
+      gemm_f64('N', 'N', m, q, m, a_new, Hinv, m, Lf, m, 0.0, Lf + (size_t)q * m, m, st);
+      gemm_f64('N', 'N', m, q, m, a_new, Ginv, m, Rf, m, 0.0, Rf + (size_t)q * m, m, st);
+      scale_matrix_launch(Lf, m, m, q, a_old, st);
+      scale_matrix_launch(Rf, m, m, q, a_old, st);
+      q *= 2;
+    } else {
+      // F <- (c/2) F + (1/(2c)) (H^{-1} F) G^{-T}
+      const double mm2 = (double)m * m;
+      ProfScope ps(h, F_GEMM, st, 7 * 8.0 * mm2, 4.0 * mm2 * m);
       gemm_f64('N', 'N', m, m, m, 1.0, Hinv, m, F, m, 0.0, P, m, st);
       gemm_f64('N', 'T', m, m, m, 0.5 / c, P, m, Ginv, m, 0.5 * c, F, m, st);
     }
     {
       const double mm2 = (double)m * m;
-      ProfScope ps(h, F_SIGNCOMB, st, 2, 2 * 3 * 8.0 * mm2, 2 * 3.0 * mm2);
+      ProfScope ps(h, F_SIGNCOMB, st, 2 * 3 * 8.0 * mm2, 2 * 3.0 * mm2);
       sign_combine_launch(Hk, Hinv, m, m, c, part, sgrid, st);
       sign_combine_launch(Gk, Ginv, m, m, c, part + 2 * sgrid, sgrid, st);
     }
@@ -318,12 +369,38 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
     }
     if (delta < 1e-8) {
       ++it;
+      converged = true;
       break;
     }
     delta_prev = delta;
   }
   *iters_out = it;
-  scale_matrix_launch(F, m, m, m, 0.5, st);
+  if (!converged)
+    return fail(h, SPK_ERR_SINGULAR_PROJECTED,
+                "sign iteration did not converge in %d steps (m=%d)", max_newton, m);
+  // The iterates converge to sign(H) and sign(G), which are the identity
+  // only if every eigenvalue lies in the open right half plane; otherwise
+  // the limit of F is not 2Y.  trace(sign(H)) = m - 2 (#eigenvalues with
+  // negative real part).
+  {
+    double tr[2] = {0.0, 0.0};
+    diag_sums_launch(Hk, m, Gk, m, m, part, st);
+    CK(cudaMemcpyAsync(tr, part, sizeof tr, cudaMemcpyDeviceToHost, st));
+    TRY(wait_stream(h, st, h->host_wait_s));
+    const int negH = (int)std::lround((m - tr[0]) / 2.0), negG = (int)std::lround((m - tr[1]) / 2.0);
+    if (negH != 0 || negG != 0)
+      return fail(h, SPK_ERR_SINGULAR_PROJECTED,
+                  "projected matrices have %d and %d eigenvalues off the open right half plane "
+                  "(m=%d): the sign iteration does not apply; a larger sketch s helps",
+                  negH, negG, m);
+  }
+  if (fact) {
+    const double mm2 = (double)m * m;
+    ProfScope ps(h, F_GEMM, st, 8.0 * (mm2 + 2.0 * m * q), 2.0 * mm2 * q);
+    gemm_f64('N', 'T', m, m, q, 0.5, Lf, m, Rf, m, 0.0, F, m, st);
+  } else {
+    scale_matrix_launch(F, m, m, m, 0.5, st);
+  }
   return SPK_OK;
 }
 
@@ -559,15 +636,22 @@ struct Solver {
     SWS(hband, double, "hband", (size_t)(o.maxit + 2) * (k + 1) * r * r);
     SWS(r1inv, double, "r1inv", (size_t)(o.maxit + 2) * r * r);
     SWS(r2inv, double, "r2inv", (size_t)(o.maxit + 2) * r * r);
-    SWS(T, double, "T", (size_t)sd.ldT * sd.ldT);
-    SWS(Ht, double, "Ht", (size_t)sd.ldH * sd.ldH);
-    sketch_geometry(sd.sk, sd.n, s_rows, o.sketch_kind == SPK_SKETCH_IDENTITY, (int)sizeof(TC), r);
-    const int64_t s = sd.sk.s;
-    SWS(Q, double, "Q", (size_t)s * sd.ldT);
-    SWS(w, double, "w", (size_t)s * r);
-    SWS(w1, double, "w1", (size_t)s * r);
-    SWS(t1, double, "t1", (size_t)mmax * r);
-    SWS(t2, double, "t2", (size_t)mmax * r);
+    const bool sketched = o.method == SPK_METHOD_SKETCHED;
+    if (sketched) {
+      SWS(T, double, "T", (size_t)sd.ldT * sd.ldT);
+      SWS(Ht, double, "Ht", (size_t)sd.ldH * sd.ldH);
+      sketch_geometry(sd.sk, sd.n, s_rows, o.sketch_kind == SPK_SKETCH_IDENTITY, (int)sizeof(TC), r);
+    } else {
+      sketch_geometry(sd.sk, sd.n, 1, 1, (int)sizeof(TC), r);
+    }
+    const int64_t s = sketched ? sd.sk.s : 1;
+    if (sketched) {
+      SWS(Q, double, "Q", (size_t)s * sd.ldT);
+      SWS(w, double, "w", (size_t)s * r);
+      SWS(w1, double, "w1", (size_t)s * r);
+      SWS(t1, double, "t1", (size_t)mmax * r);
+      SWS(t2, double, "t2", (size_t)mmax * r);
+    }
     SWS(ell, double, "ell", r * r);
     SWS(beta, double, "beta", r * r);
     SWS(R1, double, "R1", r * r);
@@ -577,11 +661,14 @@ struct Solver {
     const int groups = (k + 3) / 4;
     SWS(partial, double, "partial",
         (size_t)std::max(std::max(sd.grid, 2 * h->sm_count), 64) * 4 * r * r * std::max(groups, 1));
-    SWS(qpartial, double, "qpartial",
-        std::max((size_t)q_update_chunks((int)mmax) * s * r, (size_t)border_chunks((int)mmax) * mmax * r));
-    SWS(sk_scratch, TC, "skscratch", std::max<int64_t>(1, sd.sk.npad * r));
+    if (sketched) {
+      SWS(qpartial, double, "qpartial",
+          std::max({(size_t)q_update_chunks((int)mmax) * s * r, (size_t)border_chunks((int)mmax) * mmax * r,
+                    (size_t)qt_dot_partial_doubles((int)mmax, r)}));
+      SWS(sk_scratch, TC, "skscratch", std::max<int64_t>(1, sd.sk.npad * r));
+    }
 #undef SWS
-    if (!sd.sk.identity) {
+    if (sketched && !sd.sk.identity) {
       int32_t* rows = static_cast<int32_t*>(ws_get(h, p + "rows", sizeof(int32_t) * s));
       int8_t* signs = static_cast<int8_t*>(ws_get(h, p + "signs", (size_t)sd.n));
       const size_t sb = sketch_draws_scratch_bytes(sd.n, s);
@@ -593,8 +680,10 @@ struct Solver {
       sd.sk.rows = rows;
       sd.sk.signs = signs;
     }
-    CK(cudaMemsetAsync(sd.T, 0, sizeof(double) * sd.ldT * sd.ldT, st));
-    CK(cudaMemsetAsync(sd.Ht, 0, sizeof(double) * sd.ldH * sd.ldH, st));
+    if (sketched) {
+      CK(cudaMemsetAsync(sd.T, 0, sizeof(double) * sd.ldT * sd.ldT, st));
+      CK(cudaMemsetAsync(sd.Ht, 0, sizeof(double) * sd.ldH * sd.ldH, st));
+    }
     CK(cudaMemsetAsync(sd.hband, 0, sizeof(double) * (o.maxit + 2) * (k + 1) * r * r, st));
     return SPK_OK;
   }
@@ -623,6 +712,11 @@ struct Solver {
     chol_small_launch(sd.partial, sd.grid, r, sd.R2, sd.R2inv(0), h->flags, 1e-28, st);
     combine_small_launch(sd.R2, sd.R1, sd.ell, r, 0, st);
     scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(0), sd.block(1), st);
+    if (o.method == SPK_METHOD_TRUNCATED) {
+      // Algorithm 2: C = U_1 beta with beta = ell
+      CK(cudaMemcpyAsync(sd.beta, sd.ell, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+      return SPK_OK;
+    }
     // T_1 = R factor of S U_1 (reading of Algorithm 1's first step), beta = T_1 ell
     sketch_apply_launch<TB, TC>(sd.sk, sd.block(1), r, sd.w, sd.sk_scratch, st);
     sketch_qr(sd, 0);
@@ -651,7 +745,7 @@ struct Solver {
     const double csr_bytes = (double)op->nnz * (bV + 4) + (double)(sd.n + 1) * 4;
     if (!replay) {
       {
-        ProfScope ps(h, F_SPMM, st, 1 + (win.nwin - 1) / 4 + (win.nwin + 3) / 4,
+        ProfScope ps(h, F_SPMM, st,
                      csr_bytes + nr * (bB + bC) + win.nwin * nr * bB,
                      2.0 * op->nnz * r + 2.0 * win.nwin * nr * r);
         spmm_dots_launch<TB, TC, TV>(op->rowptr_dev, op->col_dev, sd.vals, sd.n, r, sd.block(d), sd.W,
@@ -663,12 +757,12 @@ struct Solver {
         }
       }
       {
-        ProfScope ps(h, F_UPDATE, st, 2, 2 * nr * bC + win.nwin * nr * bB,
+        ProfScope ps(h, F_UPDATE, st, 2 * nr * bC + win.nwin * nr * bB,
                      2.0 * win.nwin * nr * r + 2.0 * nr * r);
         update_gram_launch<TB, TC>(sd.W, sd.n, r, win, hs, sd.partial, sd.grid, 1, st);
         chol_small_launch(sd.partial, sd.grid, r, sd.R1, sd.R1inv(d), h->flags, kBreakdownFloor, st);
       }
-      ProfScope ps(h, F_SCALE, st, 4, 3 * nr * bC + nr * bB, 4.0 * nr * r);
+      ProfScope ps(h, F_SCALE, st, 3 * nr * bC + nr * bB, 4.0 * nr * r);
       scale_gram_launch<TC>(sd.W, sd.n, r, sd.R1inv(d), sd.partial, sd.grid, st);
       chol_small_launch(sd.partial, sd.grid, r, sd.R2, sd.R2inv(d), h->flags, 1e-28, st);
       combine_small_launch(sd.R2, sd.R1, sd.hslot(d, sd.k), r, 0, st);
@@ -677,15 +771,15 @@ struct Solver {
       WindowPtrs none{};
       none.nwin = 0;
       {
-        ProfScope ps(h, F_SPMM, st, 1, csr_bytes + nr * (bB + bC), 2.0 * op->nnz * r);
+        ProfScope ps(h, F_SPMM, st, csr_bytes + nr * (bB + bC), 2.0 * op->nnz * r);
         spmm_dots_launch<TB, TC, TV>(op->rowptr_dev, op->col_dev, sd.vals, sd.n, r, sd.block(d),
                                      sd.W, none, sd.partial, sd.grid, st);
       }
       {
-        ProfScope ps(h, F_UPDATE, st, 1, 2 * nr * bC + win.nwin * nr * bB, 2.0 * win.nwin * nr * r);
+        ProfScope ps(h, F_UPDATE, st, 2 * nr * bC + win.nwin * nr * bB, 2.0 * win.nwin * nr * r);
         update_gram_launch<TB, TC>(sd.W, sd.n, r, win, hs, sd.partial, sd.grid, 0, st);
       }
-      ProfScope ps(h, F_SCALE, st, 2, 3 * nr * bC + nr * bB, 2.0 * nr * r);
+      ProfScope ps(h, F_SCALE, st, 3 * nr * bC + nr * bB, 2.0 * nr * r);
       scale_gram_launch<TC>(sd.W, sd.n, r, sd.R1inv(d), sd.partial, sd.grid, st);
       scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(d), sd.block(d + 1), st);
     }
@@ -697,34 +791,34 @@ struct Solver {
     const int64_t s = sd.sk.s;
     const double sr8 = 8.0 * s * r, sm8 = 8.0 * s * m;
     {
-      ProfScope ps(h, F_SKETCH, st, sd.sk.identity ? 1 : 2,
+      ProfScope ps(h, F_SKETCH, st,
                    (double)sd.n * r * sizeof(TB) + (double)sd.n + sr8,
                    sd.sk.identity ? 0.0 : (double)sd.sk.npad * r * sd.sk.log2n2 + (double)s * sd.sk.n1 * r);
       sketch_apply_launch<TB, TC>(sd.sk, sd.block(d + 1), r, sd.w, sd.sk_scratch, st);
     }
     const int nch = q_update_chunks(m);
     {
-      ProfScope ps(h, F_QTDOT, st, 1, sm8 + sr8 + 8.0 * m * r, 2.0 * s * m * r);
-      qt_dot_launch(sd.Q, s, s, m, sd.w, r, sd.t1, st);
+      ProfScope ps(h, F_QTDOT, st, sm8 + sr8 + 8.0 * m * r, 2.0 * s * m * r);
+      qt_dot_launch(sd.Q, s, s, m, sd.w, r, sd.t1, sd.qpartial, st);
     }
     {
-      ProfScope ps(h, F_QUPDATE, st, 2, sm8 + 2 * sr8 + 8.0 * m * r, 2.0 * s * m * r);
+      ProfScope ps(h, F_QUPDATE, st, sm8 + 2 * sr8 + 8.0 * m * r, 2.0 * s * m * r);
       q_update_launch(sd.Q, s, s, m, sd.t1, r, sd.w, sd.w1, sd.qpartial, nch, st);
     }
     {
-      ProfScope ps(h, F_QTDOT, st, 1, sm8 + sr8 + 8.0 * m * r, 2.0 * s * m * r);
-      qt_dot_launch(sd.Q, s, s, m, sd.w1, r, sd.t2, st);
+      ProfScope ps(h, F_QTDOT, st, sm8 + sr8 + 8.0 * m * r, 2.0 * s * m * r);
+      qt_dot_launch(sd.Q, s, s, m, sd.w1, r, sd.t2, sd.qpartial, st);
     }
     {
-      ProfScope ps(h, F_QUPDATE, st, 2, sm8 + 2 * sr8 + 8.0 * m * r, 2.0 * s * m * r);
+      ProfScope ps(h, F_QUPDATE, st, sm8 + 2 * sr8 + 8.0 * m * r, 2.0 * s * m * r);
       q_update_launch(sd.Q, s, s, m, sd.t2, r, sd.w1, sd.w, sd.qpartial, nch, st);
     }
     {
-      ProfScope ps(h, F_TSQR, st, 8, 6 * sr8, 6.0 * s * r * r);
+      ProfScope ps(h, F_TSQR, st, 6 * sr8, 6.0 * s * r * r);
       sketch_qr(sd, m);
       t_write_launch(sd.T, sd.ldT, m, r, sd.t1, sd.t2, sd.tau, st);
     }
-    ProfScope psb(h, F_BORDER, st, d == 1 ? 2 : 3, 8.0 * (double)(m - r) * (m - r) + 16.0 * m * r,
+    ProfScope psb(h, F_BORDER, st, 8.0 * (double)(m - r) * (m - r) + 16.0 * m * r,
                   2.0 * (double)(m - r) * (m - r) * r);
     // bordering (Section 5): Hhat_d from H~_{d-1}, then the correction -> H~_d
     const int mp = m - r;
@@ -749,17 +843,34 @@ struct Solver {
     WS(Gk, double, "pj_Gk", (size_t)m * m);
     WS(F, double, "pj_F", (size_t)m * m);
     WS(out3, double, "pj_out3", 4);
-    copy_matrix_launch(S[0].Ht, S[0].ldH, Hk, m, m, m, st);
-    copy_matrix_launch(S[1].Ht, S[1].ldH, Gk, m, m, m, st);
-    set_zero_launch(F, (int64_t)m * m, st);
-    fill_rhs_launch(F, m, m, r, S[0].beta, S[1].beta, st);
+    const bool sketched = o.method == SPK_METHOD_SKETCHED;
+    if (sketched) {
+      copy_matrix_launch(S[0].Ht, S[0].ldH, Hk, m, m, m, st);
+      copy_matrix_launch(S[1].Ht, S[1].ldH, Gk, m, m, m, st);
+    } else {
+      // Algorithm 2: the projected matrices are the banded H_d, G_d themselves
+      set_zero_launch(Hk, (int64_t)m * m, st);
+      set_zero_launch(Gk, (int64_t)m * m, st);
+      band_to_dense_launch(S[0].hband, S[0].k, r, d, Hk, m, st);
+      band_to_dense_launch(S[1].hband, S[1].k, r, d, Gk, m, st);
+    }
+    // right-hand side E_1 beta_1 beta_2^T E_1^T in factored form, L_0 = E_1 beta_1,
+    // R_0 = E_1 beta_2 (the sign iteration forms F once the factors pass m/2 columns)
+    const int qcap = std::max(r, m / 2);
+    WS(Lf, double, "pj_L", (size_t)m * qcap);
+    WS(Rf, double, "pj_R", (size_t)m * qcap);
+    set_zero_launch(Lf, (int64_t)m * r, st);
+    set_zero_launch(Rf, (int64_t)m * r, st);
+    fill_factor_launch(Lf, m, r, S[0].beta, st);
+    fill_factor_launch(Rf, m, r, S[1].beta, st);
     if (o.inject & SPK_INJECT_SINGULAR)
       return fail(h, SPK_ERR_SINGULAR_PROJECTED, "injected: singular projected equation");
-    TRY(sign_solve(h, m, Hk, Gk, F, o.max_newton, st, newton_iters));
+    TRY(sign_solve(h, m, Hk, Gk, F, o.max_newton, st, newton_iters, Lf, Rf, r, qcap));
     {
-      ProfScope ps(h, F_RHO, st, 1, 16.0 * m * r, 8.0 * m * r * r);
-      rho_launch(F, m, m, r, S[0].T, S[0].ldT, S[1].T, S[1].ldT, S[0].hslot(d, S[0].k),
-                 S[1].hslot(d, S[1].k), S[0].beta, S[1].beta, out3, st);
+      ProfScope ps(h, F_RHO, st, 16.0 * m * r, 8.0 * m * r * r);
+      rho_launch(F, m, m, r, sketched ? S[0].T : nullptr, S[0].ldT, sketched ? S[1].T : nullptr,
+                 S[1].ldT, S[0].hslot(d, S[0].k), S[1].hslot(d, S[1].k), S[0].beta, S[1].beta,
+                 out3, st);
     }
     CK(cudaMemcpyAsync(rho3, out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     TRY(wait_stream(h, st, (o.inject & SPK_INJECT_TIMEOUT) ? 0.0 : h->host_wait_s));
@@ -772,7 +883,7 @@ struct Solver {
     double *Y1 = nullptr, *Y2 = nullptr;
     int ell = 0;
     {
-      ProfScope ps(h, F_TRUNC, st, 0, 8.0 * m * m, 0.0);
+      ProfScope ps(h, F_TRUNC, st, 8.0 * m * m, 0.0);
       TRY(truncate_Y(h, Y, m, o.trunc_tol, o.seed, st, &Y1, &Y2, &ell));
     }
     out->rank = ell;
@@ -780,9 +891,11 @@ struct Solver {
     if (ell == 0) return SPK_OK;
     // W_i = T_i^{-1} Y_i  (T_U, T_V leading m x m)
     {
-      ProfScope ps(h, F_TRSM, st, 2, 2 * 8.0 * ((double)m * m / 2 + 2.0 * m * ell), 2.0 * m * m * ell);
-      trsm_upper_left_launch(S[0].T, S[0].ldT, m, Y1, m, ell, st);
-      trsm_upper_left_launch(S[1].T, S[1].ldT, m, Y2, m, ell, st);
+      ProfScope ps(h, F_TRSM, st, 2 * 8.0 * ((double)m * m / 2 + 2.0 * m * ell), 2.0 * m * m * ell);
+      if (o.method == SPK_METHOD_SKETCHED) {
+        trsm_upper_left_launch(S[0].T, S[0].ldT, m, Y1, m, ell, st);
+        trsm_upper_left_launch(S[1].T, S[1].ldT, m, Y2, m, ell, st);
+      }
     }
     double* Wf[2] = {Y1, Y2};
     for (int side = 0; side < 2; ++side) {
@@ -801,7 +914,7 @@ struct Solver {
           WindowPtrs blocks{};
           blocks.nwin = j - last;
           for (int q = 0; q < blocks.nwin; ++q) blocks.blk[q] = sd.block(last + 1 + q);
-          ProfScope ps(h, F_XACC, st, 1,
+          ProfScope ps(h, F_XACC, st,
                        (double)sd.n * (2.0 * 8 * ell + blocks.nwin * r * sizeof(TB)),
                        2.0 * sd.n * ell * r * blocks.nwin);
           x_accumulate_launch<TB>(X, sd.n, ell, r, blocks, Wf[side] + (size_t)last * r, m, st);
@@ -883,7 +996,7 @@ struct Solver {
     for (d = 1; d <= dmax; ++d) {
       for (int side = 0; side < 2; ++side) {
         arnoldi_basis(S[side], d, false);
-        whiten_and_border(S[side], d);
+        if (o.method == SPK_METHOD_SKETCHED) whiten_and_border(S[side], d);
       }
       const bool last = d == dmax;
       bool do_check = last;
@@ -986,7 +1099,11 @@ int validate(spk_handle* h, const spk_csr* A, const spk_csr* BT, const double* C
   if (o->same_sketch && A->nrows != BT->nrows)
     return fail(h, SPK_ERR_ARG, "same_sketch needs n1 == n2");
   const int64_t mmax = (int64_t)(o->maxit + 1) * r;
-  if (o->sketch_kind == SPK_SKETCH_IDENTITY) {
+  if (o->method != SPK_METHOD_SKETCHED && o->method != SPK_METHOD_TRUNCATED)
+    return fail(h, SPK_ERR_ARG, "unknown method");
+  if (o->method == SPK_METHOD_TRUNCATED) {
+    // no sketch
+  } else if (o->sketch_kind == SPK_SKETCH_IDENTITY) {
     if (A->nrows < mmax || BT->nrows < mmax)
       return fail(h, SPK_ERR_ARG, "identity sketch needs n >= (maxit+1) r");
   } else if (o->sketch_kind == SPK_SKETCH_SRHT) {
@@ -1056,6 +1173,13 @@ int spk_create(spk_handle** out, int device) {
     delete h;
     return SPK_ERR_ALLOC;
   }
+  if (cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    spk_destroy(h);
+    return SPK_ERR_CUDA;
+  }
   *out = h;
   return SPK_OK;
 }
@@ -1063,9 +1187,18 @@ int spk_create(spk_handle** out, int device) {
 void spk_destroy(spk_handle* h) {
   if (!h) return;
   cudaSetDevice(h->device);
+  for (auto& w : h->workers) {
+    if (w.st) cudaStreamDestroy(w.st);
+    if (w.done) cudaEventDestroy(w.done);
+    spk_destroy(w.h);
+  }
+  h->workers.clear();
   for (auto& kv : h->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
   if (h->flags) cudaFree(h->flags);
+  if (h->aux) cudaStreamDestroy(h->aux);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
 }
 
@@ -1120,6 +1253,58 @@ int spk_solve(spk_handle* h, const spk_csr* A, const spk_csr* BT, const double* 
   return rc;
 }
 
+int spk_solve_batched(spk_handle* h, int32_t count, const spk_problem* probs,
+                      int32_t concurrency, void* stream, spk_result* outs) {
+  if (!h || count < 0 || (count > 0 && (!probs || !outs)) || concurrency < 1 || concurrency > 64)
+    return SPK_ERR_ARG;
+  if (count == 0) return SPK_OK;
+  if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, SPK_ERR_CUDA, "cudaSetDevice failed");
+  const int nw = std::min<int>(concurrency, count);
+  while ((int)h->workers.size() < nw) {
+    spk_handle::Worker w;
+    int rc = spk_create(&w.h, h->device);
+    if (rc != SPK_OK) return fail(h, rc, "cannot create batched worker");
+    if (cudaStreamCreateWithFlags(&w.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (w.st) cudaStreamDestroy(w.st);
+      spk_destroy(w.h);
+      return fail(h, SPK_ERR_CUDA, "cannot create batched worker stream");
+    }
+    w.h->host_wait_s = h->host_wait_s;
+    h->workers.push_back(w);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaEventRecord(h->ev_fork, st));
+  for (int t = 0; t < nw; ++t) CK(cudaStreamWaitEvent(h->workers[t].st, h->ev_fork, 0));
+  std::atomic<int> next{0};
+  std::vector<int> status(count, SPK_OK);
+  std::vector<std::string> msgs(count);
+  std::vector<std::thread> threads;
+  threads.reserve(nw);
+  for (int t = 0; t < nw; ++t) {
+    threads.emplace_back([&, t]() {
+      spk_handle::Worker& w = h->workers[t];
+      cudaSetDevice(h->device);
+      for (;;) {
+        const int i = next.fetch_add(1);
+        if (i >= count) break;
+        const spk_problem& pb = probs[i];
+        status[i] = spk_solve(w.h, &pb.A, &pb.BT, pb.C1_dev, pb.C2_dev, pb.r, &pb.opts, w.st,
+                              &outs[i]);
+        if (status[i] != SPK_OK && status[i] != SPK_ERR_NOT_CONVERGED) msgs[i] = w.h->err;
+      }
+      cudaEventRecord(w.done, w.st);
+    });
+  }
+  for (auto& th : threads) th.join();
+  for (int t = 0; t < nw; ++t) CK(cudaStreamWaitEvent(st, h->workers[t].done, 0));
+  for (int i = 0; i < count; ++i)
+    if (status[i] != SPK_OK && status[i] != SPK_ERR_NOT_CONVERGED)
+      return fail(h, status[i], "instance %d: %s", i, msgs[i].c_str());
+  return SPK_OK;
+}
+
 int spk_solve_adjoint(spk_handle* h, const spk_csr* AT, const spk_csr* B, const double* G1,
                       const double* G2, int q, const spk_opts* opts, void* stream,
                       spk_result* out) {
@@ -1152,44 +1337,34 @@ int spk_adjoint_gradients(spk_handle* h, const spk_result* X, const spk_result* 
   gemm_f64('N', 'T', ll, r, n1, 1.0, L->X1_dev, ll, C1, r, 0.0, t1, ll, st);
   gemm_f64('T', 'N', r, n2, ll, 1.0, t1, ll, L->X2_dev, ll, 0.0, dC2, r, st);
   if (dtheta) {
-    double val = 0.0;
-    const int mx = std::max(lx, ll);
-    WS(M1, double, "ag_M1", (size_t)mx * mx);
-    WS(M2, double, "ag_M2", (size_t)mx * mx);
-    WS(sc, double, "ag_sc", 4);
+    // dtheta = -<L, A_theta X + X B_theta>_F
+    //        = -trace((L1^T A_theta X1)(X2^T L2)) - trace((L1^T X1)(X2^T B_theta L2))
+    WS(M1, double, "ag_M1", (size_t)ll * lx);
+    WS(M2, double, "ag_M2", (size_t)lx * ll);
+    WS(sc, double, "ag_sc", 2);
+    CK(cudaMemsetAsync(sc, 0, 2 * sizeof(double), st));
     if (A_theta) {
       WS(AX, double, "ag_AX", (size_t)n1 * lx);
-      spmm_wide_launch(A_theta->rowptr_dev, A_theta->col_dev, A_theta->val_dev, n1, lx, X->X1_dev, AX, st);
-      // M1 = L1^T (A_theta X1)  (ll x lx);  M2 = X2^T L2 (lx x ll)
+      spmm_wide_launch(A_theta->rowptr_dev, A_theta->col_dev, A_theta->val_dev, n1, lx, X->X1_dev,
+                       AX, st);
+      // M1 = L1^T (A_theta X1)  (ll x lx);  M2 = X2^T L2  (lx x ll)
       gemm_f64('N', 'T', ll, lx, n1, 1.0, L->X1_dev, ll, AX, lx, 0.0, M1, ll, st);
       gemm_f64('N', 'T', lx, ll, n2, 1.0, X->X2_dev, lx, L->X2_dev, ll, 0.0, M2, lx, st);
-      if (ll == lx) val += trace_product(M1, M2, ll, sc, st);
-      else {
-        // general: trace(M1 M2) with M1 ll x lx, M2 lx x ll -> sum_ij M1[i,j] M2[j,i]
-        WS(P, double, "ag_P", (size_t)ll * ll);
-        gemm_f64('N', 'N', ll, ll, lx, 1.0, M1, ll, M2, lx, 0.0, P, ll, st);
-        WS(I, double, "ag_I", (size_t)ll * ll);
-        std::vector<double> eye((size_t)ll * ll, 0.0);
-        for (int i = 0; i < ll; ++i) eye[(size_t)i * ll + i] = 1.0;
-        CK(cudaMemcpyAsync(I, eye.data(), sizeof(double) * eye.size(), cudaMemcpyHostToDevice, st));
-        val += trace_product(P, I, ll, sc, st);
-      }
+      trace_product_launch(M1, M2, ll, lx, sc, st);
     }
     if (B_theta) {
       WS(BL, double, "ag_BL", (size_t)n2 * ll);
-      spmm_wide_launch(B_theta->rowptr_dev, B_theta->col_dev, B_theta->val_dev, n2, ll, L->X2_dev, BL, st);
-      // M1 = L1^T X1 (ll x lx); M2 = X2^T (B_theta L2) (lx x ll)
+      spmm_wide_launch(B_theta->rowptr_dev, B_theta->col_dev, B_theta->val_dev, n2, ll,
+                       L->X2_dev, BL, st);
+      // M1 = L1^T X1  (ll x lx);  M2 = X2^T (B_theta L2)  (lx x ll)
       gemm_f64('N', 'T', ll, lx, n1, 1.0, L->X1_dev, ll, X->X1_dev, lx, 0.0, M1, ll, st);
       gemm_f64('N', 'T', lx, ll, n2, 1.0, X->X2_dev, lx, BL, ll, 0.0, M2, lx, st);
-      WS(P2, double, "ag_P2", (size_t)ll * ll);
-      gemm_f64('N', 'N', ll, ll, lx, 1.0, M1, ll, M2, lx, 0.0, P2, ll, st);
-      WS(I2, double, "ag_I2", (size_t)ll * ll);
-      std::vector<double> eye((size_t)ll * ll, 0.0);
-      for (int i = 0; i < ll; ++i) eye[(size_t)i * ll + i] = 1.0;
-      CK(cudaMemcpyAsync(I2, eye.data(), sizeof(double) * eye.size(), cudaMemcpyHostToDevice, st));
-      val += trace_product(P2, I2, ll, sc, st);
+      trace_product_launch(M1, M2, ll, lx, sc + 1, st);
     }
-    *dtheta = -val;
+    double hv[2] = {0.0, 0.0};
+    CK(cudaMemcpyAsync(hv, sc, sizeof hv, cudaMemcpyDeviceToHost, st));
+    TRY(wait_stream(h, st, h->host_wait_s));
+    *dtheta = -(hv[0] + hv[1]);
   }
   TRY(wait_stream(h, st, h->host_wait_s));
   CK(cudaGetLastError());

@@ -51,6 +51,62 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Block-wide sums of NV per-thread values: out[e] = sum over the block's
+// threads of acc[e], for e < NV (fixed order, so deterministic).  Within a
+// warp, NV > 8 values are reduce-scattered: at each of the five shuffle
+// levels a lane keeps one half of its values and adds its partner's copy of
+// that half, ending with NV/32 complete warp sums for about NV additions
+// (5 NV with one shuffle tree per value).  acc may be clobbered.  Ends
+// with a barrier, so the caller may reuse shared memory afterwards.
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&acc)[NV], double* out) {
+  constexpr int NVP = NV <= 8 ? NV : ((NV + 31) / 32) * 32;
+  __shared__ double red[32][NVP];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  if constexpr (NV <= 8) {
+#pragma unroll
+    for (int e = 0; e < NV; ++e) {
+      const double v = warp_sum(acc[e]);
+      if (lane == 0) red[wid][e] = v;
+    }
+  } else {
+    // in place when NV is a multiple of 32 (acc is clobbered), else padded
+    double pad[NV == NVP ? 1 : NVP];
+    double* v;
+    if constexpr (NV == NVP) {
+      v = acc;
+    } else {
+#pragma unroll
+      for (int e = 0; e < NVP; ++e) pad[e] = e < NV ? acc[e] : 0.0;
+      v = pad;
+    }
+#pragma unroll
+    for (int lv = 0; lv < 5; ++lv) {
+      const int o = 16 >> lv;
+      const int half = NVP >> (lv + 1);
+      const bool upper = (lane & o) != 0;
+#pragma unroll
+      for (int e = 0; e < half; ++e) {
+        const double give = upper ? v[e] : v[e + half];
+        const double keep = upper ? v[e + half] : v[e];
+        v[e] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+      }
+    }
+    // lane holds the sums of entries lane*PER .. lane*PER + PER - 1
+    constexpr int PER = NVP / 32;
+#pragma unroll
+    for (int e = 0; e < PER; ++e) red[wid][lane * PER + e] = v[e];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NV; e += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w][e];
+    out[e] = t;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- sketch
 struct SketchDev {
   int64_t n = 0;        // rows of the sketched blocks
@@ -112,8 +168,11 @@ void combine_small_launch(const double* A, const double* B, double* C, int r, in
                           cudaStream_t st);
 
 // ---------------------------------------------------------------- whitening
+// t (m x r, row-major) = Q^T w for Q s x m (ld ldq) and w s x r (column-major);
+// tpart: qt_dot_partial_doubles(mmax, r) doubles of scratch.
 void qt_dot_launch(const double* Q, int64_t ldq, int64_t s, int m, const double* w, int r,
-                   double* t, cudaStream_t st);
+                   double* t, double* tpart, cudaStream_t st);
+int qt_dot_partial_doubles(int mmax, int r);
 void q_update_launch(const double* Q, int64_t ldq, int64_t s, int m, const double* t, int r,
                      const double* w_in, double* w_out, double* partial, int nchunk,
                      cudaStream_t st);
@@ -137,8 +196,12 @@ void border_correct_launch(double* Ht, int64_t ldH, int m, int r, const double* 
 void rho_launch(const double* Y, int64_t ldY, int m, int r, const double* TU, int64_t ldTU,
                 const double* TV, int64_t ldTV, const double* hU, const double* hV,
                 const double* betaU, const double* betaV, double* out3, cudaStream_t st);
-void fill_rhs_launch(double* F, int64_t ldF, int m, int r, const double* betaU,
-                     const double* betaV, cudaStream_t st);
+// Dense block Hessenberg H_d (m = d r, column-major, zeroed beforehand) from
+// the stored coefficients hband ((k+1) r x r row-major slots per column).
+void band_to_dense_launch(const double* hband, int k, int r, int d, double* H, int64_t ldH,
+                          cudaStream_t st);
+// Top r x r block of a column-major m x q factor from a row-major r x r beta.
+void fill_factor_launch(double* L, int64_t ldL, int r, const double* beta, cudaStream_t st);
 
 // ---------------------------------------------------------------- dense FP64
 void gemm_f64(char ta, char tb, int M, int N, int K, double alpha, const double* A, int64_t lda,
@@ -175,8 +238,13 @@ void gather_cols_launch(const double* A, int64_t lda, int M, const int* idx, con
                         int ncols, double* out, int64_t ldo, cudaStream_t st);
 // out[j] = column absolute sums of A (M x N, column-major)
 void col_abs_sums_launch(const double* A, int64_t lda, int M, int N, double* out, cudaStream_t st);
+// out2_dev = {trace(A), trace(B)}, A and B m x m column-major.
+void diag_sums_launch(const double* A, int64_t lda, const double* B, int64_t ldb, int m,
+                      double* out2_dev, cudaStream_t st);
 // Measured FP64 FMA rate of the device in TFLOP/s (dependent-chain probe).
 double fp64_fma_probe(int sm_count, double* scratch, cudaStream_t st);
-double trace_product(const double* A, const double* B, int n, double* scratch, cudaStream_t st);
+// out_dev[0] = trace(A B), A p x q and B q x p column-major (ld p and q).
+void trace_product_launch(const double* A, const double* B, int p, int q, double* out_dev,
+                          cudaStream_t st);
 
 }  // namespace spk

@@ -30,6 +30,7 @@ SPK_ERR_UNSUPPORTED = -9
 
 SKETCH = {"srht": 0, "identity": 1}
 PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_bf16": 2}
+METHOD = {"sketched": 0, "truncated": 1}
 CHECK = {"every_p": 0, "adaptive": 1}
 INJECT_NAN_C1, INJECT_RANK_DEFICIENT, INJECT_TIMEOUT, INJECT_SINGULAR = 1, 2, 4, 8
 
@@ -45,7 +46,7 @@ class Opts(C.Structure):
                 ("precision", C.c_int32), ("check_schedule", C.c_int32),
                 ("same_sketch", C.c_int32), ("fixed_d", C.c_int32), ("max_newton", C.c_int32),
                 ("inject", C.c_uint32), ("tol", C.c_double), ("trunc_tol", C.c_double),
-                ("seed", C.c_uint64), ("reserved", C.c_int32 * 8)]
+                ("seed", C.c_uint64), ("method", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class Result(C.Structure):
@@ -58,6 +59,11 @@ class Result(C.Structure):
                 ("mem_basis_vectors", C.c_int64), ("mem_solution_vectors", C.c_int64),
                 ("ms_arnoldi", C.c_double), ("ms_project", C.c_double), ("ms_recover", C.c_double),
                 ("reserved", C.c_int32 * 8)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("A", Csr), ("BT", Csr), ("C1_dev", C.c_void_p), ("C2_dev", C.c_void_p),
+                ("r", C.c_int32), ("reserved0", C.c_int32), ("opts", Opts)]
 
 
 _lib = None
@@ -94,6 +100,7 @@ def load() -> C.CDLL:
         "spk_profile_enable": (i32, [vp, C.c_int]),
         "spk_profile_read": (i32, [vp, C.c_int, P(C.c_char_p), P(dbl), P(i64), P(i64), P(dbl), P(dbl)]),
         "spk_fp64_peak": (i32, [vp, P(dbl), vp]),
+        "spk_solve_batched": (i32, [vp, i32, P(Problem), i32, vp, P(Result)]),
         "spk_sketch_apply_static": (i32, [i64, i32, u64, i32, vp, i32, vp, vp, C.c_char_p,
                                           C.c_size_t]),
     }
@@ -201,7 +208,7 @@ class SolveResult:
 
 def make_opts(*, k=2, k_right=None, s=600, maxit=300, p=1, tol=1e-8, trunc_tol=1e-12, seed=0,
               sketch="srht", precision="fp64", check="every_p", same_sketch=False, fixed_d=0,
-              max_newton=100, inject=0) -> Opts:
+              max_newton=100, inject=0, method="sketched") -> Opts:
     o = Opts()
     load().spk_opts_default(C.byref(o))
     o.k_left = k
@@ -219,6 +226,7 @@ def make_opts(*, k=2, k_right=None, s=600, maxit=300, p=1, tol=1e-8, trunc_tol=1
     o.fixed_d = fixed_d
     o.max_newton = max_newton
     o.inject = inject
+    o.method = METHOD[method]
     return o
 
 
@@ -252,6 +260,43 @@ def solve(A, BT, C1, C2, *, device: int = 0, stream=None, raise_on_error: bool =
     Result struct is returned as well (the caller then frees it with
     free_raw); used by the adjoint gradients.
     """
+    return _solve_entry("spk_solve", A, BT, C1, C2, device, stream, raise_on_error, keep_raw,
+                        opts)
+
+
+def solve_adjoint(AT, B, G1, G2, *, device: int = 0, stream=None, raise_on_error: bool = True,
+                  keep_raw: bool = False, **opts):
+    """The transposed equation A^T L + L B^T = G1 G2^T by the same solver:
+    pass AT = A^T and B itself (the right Krylov space is K(B, G2))."""
+    return _solve_entry("spk_solve_adjoint", AT, B, G1, G2, device, stream, raise_on_error,
+                        keep_raw, opts)
+
+
+def adjoint_gradients(xraw: Result, lraw: Result, C1, C2, A_theta=None, B_theta=None,
+                      device: int = 0):
+    """dC1 = L C2, dC2 = L^T C1 (device tensors) and dtheta =
+    -<L, A_theta X + X B_theta>_F (None without derivative operators), from the
+    raw results of a solve (X) and of its adjoint solve (L)."""
+    torch = _torch()
+    h = handle(device)
+    c1, c2 = _block(C1), _block(C2)
+    dC1 = torch.empty_like(c1)
+    dC2 = torch.empty_like(c2)
+    dA = None if A_theta is None else (A_theta if isinstance(A_theta, DeviceCSR) else DeviceCSR(A_theta))
+    dB = None if B_theta is None else (B_theta if isinstance(B_theta, DeviceCSR) else DeviceCSR(B_theta))
+    dth = C.c_double(0.0)
+    want = dA is not None or dB is not None
+    rc = h.lib.spk_adjoint_gradients(
+        h.h, C.byref(xraw), C.byref(lraw), C.c_void_p(c1.data_ptr()), C.c_void_p(c2.data_ptr()),
+        c1.shape[1], C.byref(dA.c) if dA is not None else None,
+        C.byref(dB.c) if dB is not None else None, C.c_void_p(dC1.data_ptr()),
+        C.c_void_p(dC2.data_ptr()), C.byref(dth) if want else None, _stream_ptr())
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+    return dC1, dC2, (dth.value if want else None)
+
+
+def _solve_entry(fn, A, BT, C1, C2, device, stream, raise_on_error, keep_raw, opts):
     torch = _torch()
     h = handle(device)
     dA = A if isinstance(A, DeviceCSR) else DeviceCSR(A)
@@ -261,9 +306,9 @@ def solve(A, BT, C1, C2, *, device: int = 0, stream=None, raise_on_error: bool =
     o = make_opts(**opts)
     res = Result()
     torch.cuda.synchronize()
-    rc = h.lib.spk_solve(h.h, C.byref(dA.c), C.byref(dB.c), C.c_void_p(c1.data_ptr()),
-                         C.c_void_p(c2.data_ptr()), c1.shape[1], C.byref(o), _stream_ptr(stream),
-                         C.byref(res))
+    rc = getattr(h.lib, fn)(h.h, C.byref(dA.c), C.byref(dB.c), C.c_void_p(c1.data_ptr()),
+                            C.c_void_p(c2.data_ptr()), c1.shape[1], C.byref(o),
+                            _stream_ptr(stream), C.byref(res))
     if rc not in (SPK_OK, SPK_ERR_NOT_CONVERGED):
         msg = h.error()
         h.lib.spk_result_free(C.byref(res))
@@ -276,6 +321,52 @@ def solve(A, BT, C1, C2, *, device: int = 0, stream=None, raise_on_error: bool =
         return out, res
     h.lib.spk_result_free(C.byref(res))
     return out
+
+
+def solve_batched(problems, *, concurrency: int = 8, device: int = 0, stream=None,
+                  raise_on_error: bool = True, opts_list=None, **opts):
+    """The batched form: solve independent instances (objects with A, BT, C1,
+    C2 as scipy CSR / arrays) by concurrent workers on the device.
+
+    Options are common (**opts) unless opts_list gives one dict per
+    instance.  Returns (status, [SolveResult or None per instance])."""
+    torch = _torch()
+    h = handle(device)
+    keep = []
+    arr = (Problem * max(1, len(problems)))()
+    for i, P in enumerate(problems):
+        dA = P.A if isinstance(P.A, DeviceCSR) else DeviceCSR(P.A)
+        dB = P.BT if isinstance(P.BT, DeviceCSR) else DeviceCSR(P.BT)
+        c1, c2 = _block(P.C1), _block(P.C2)
+        keep += [dA, dB, c1, c2]
+        o = make_opts(**(opts_list[i] if opts_list is not None else opts))
+        arr[i] = Problem(dA.c, dB.c, c1.data_ptr(), c2.data_ptr(), c1.shape[1], 0, o)
+    outs = (Result * max(1, len(problems)))()
+    torch.cuda.synchronize()
+    rc = h.lib.spk_solve_batched(h.h, len(problems), arr, concurrency, _stream_ptr(stream), outs)
+    torch.cuda.synchronize()
+    results = []
+    for i in range(len(problems)):
+        if outs[i].status in (SPK_OK, SPK_ERR_NOT_CONVERGED):
+            results.append(_result_to_py(h.lib, outs[i]))
+        else:
+            results.append(None)
+        h.lib.spk_result_free(C.byref(outs[i]))
+    if rc != SPK_OK and raise_on_error:
+        raise SpkError(rc, h.error())
+    return rc, results
+
+
+def result_view(sol: "SolveResult") -> Result:
+    """A Result struct whose factor pointers view sol.X1, sol.X2 (tensors the
+    caller keeps alive), for spk_adjoint_gradients."""
+    res = Result()
+    res.status, res.iters, res.rank = sol.status, sol.iters, sol.rank
+    res.n1 = sol.X1.shape[0] if sol.X1 is not None else 0
+    res.n2 = sol.X2.shape[0] if sol.X2 is not None else 0
+    res.X1_dev = sol.X1.data_ptr() if sol.X1 is not None else None
+    res.X2_dev = sol.X2.data_ptr() if sol.X2 is not None else None
+    return res
 
 
 def free_raw(res: Result, device: int = 0):

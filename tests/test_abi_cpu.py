@@ -39,8 +39,9 @@ def test_struct_layout_matches_binding(lib):
 #include <stddef.h>
 #include "spk.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(spk_csr), sizeof(spk_opts), sizeof(spk_result),
-         offsetof(spk_opts, tol), offsetof(spk_result, X1_dev), offsetof(spk_result, ms_recover));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(spk_csr), sizeof(spk_opts), sizeof(spk_result),
+         offsetof(spk_opts, tol), offsetof(spk_result, X1_dev), offsetof(spk_result, ms_recover),
+         sizeof(spk_problem), offsetof(spk_problem, opts));
   return 0;
 }
 '''
@@ -51,7 +52,8 @@ int main(void) {
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         got = [int(x) for x in subprocess.check_output([exe]).split()]
     want = [ctypes.sizeof(spk.Csr), ctypes.sizeof(spk.Opts), ctypes.sizeof(spk.Result),
-            spk.Opts.tol.offset, spk.Result.X1_dev.offset, spk.Result.ms_recover.offset]
+            spk.Opts.tol.offset, spk.Result.X1_dev.offset, spk.Result.ms_recover.offset,
+            ctypes.sizeof(spk.Problem), spk.Problem.opts.offset]
     assert got == want
 
 

@@ -1,0 +1,109 @@
+"""Adjoint and gradients (differentiating Eq. (1.1)) on the GPU: the
+transposed equation by the same sketched solver, the gradients of
+L = u^T X v with respect to C1, C2 and the convection coefficient theta,
+against the dense FP64 oracle gradient at n = 32^2 and against central
+finite differences of the GPU solve, and through torch.autograd."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2311_16019_gb300 import inputs as I  # noqa: E402
+from oracle import adjoint as ADJ, measure as M  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2311_16019_gb300 import build, spk
+    build.build()
+    return spk.load()
+
+
+OPTS = dict(k=4, s=1000, maxit=400, p=5, tol=1e-12, seed=3, trunc_tol=1e-14)
+
+
+def _uv(n1, n2, seed=21):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(n1), rng.standard_normal(n2)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def test_adjoint_solve_matches_dense_transposed_equation():
+    from paper_2311_16019_gb300 import spk
+    P = I.workload("cd2d_32_r2")
+    u, v = _uv(P.n1, P.n2)
+    lam = spk.solve_adjoint(P.AT, P.B, u[:, None], v[:, None], **OPTS)
+    assert lam.converged
+    ref = ADJ.dense_gradient(P.A, P.B, P.A_theta, P.B_theta, P.C1, P.C2, u, v)["Lam"]
+    got = host(lam.X1) @ host(lam.X2).T
+    assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_gradients_against_dense_oracle_gradient():
+    from paper_2311_16019_gb300 import spk
+    P = I.workload("cd2d_32_r2")
+    u, v = _uv(P.n1, P.n2)
+    x = spk.solve(P.A, P.BT, P.C1, P.C2, **OPTS)
+    lam = spk.solve_adjoint(P.AT, P.B, u[:, None], v[:, None], **OPTS)
+    assert x.converged and lam.converged
+    dC1, dC2, dth = spk.adjoint_gradients(spk.result_view(x), spk.result_view(lam), P.C1, P.C2,
+                                          P.A_theta, P.B_theta)
+    ref = ADJ.dense_gradient(P.A, P.B, P.A_theta, P.B_theta, P.C1, P.C2, u, v)
+    for got, want in ((host(dC1), ref["dC1"]), (host(dC2), ref["dC2"])):
+        assert np.linalg.norm(got - want) <= 1e-6 * np.linalg.norm(want)
+    assert dth == pytest.approx(ref["dtheta"], rel=1e-6)
+
+
+def test_theta_gradient_against_central_differences():
+    """Central differences, h = 1e-6, of the GPU solve at tol 1e-12 with the
+    sketch seed fixed and d frozen at the base run; the agreement is bounded
+    by about tol / h plus O(h^2)."""
+    from paper_2311_16019_gb300 import spk
+    from paper_2311_16019_gb300.autograd import OperatorFamily
+    P = I.workload("cd2d_32_r2")
+    fam = OperatorFamily.from_problem(P)
+    u, v = _uv(P.n1, P.n2, seed=5)
+    x = spk.solve(P.A, P.BT, P.C1, P.C2, **OPTS)
+    lam = spk.solve_adjoint(P.AT, P.B, u[:, None], v[:, None], **OPTS)
+    _, _, dth = spk.adjoint_gradients(spk.result_view(x), spk.result_view(lam), P.C1, P.C2,
+                                      P.A_theta, P.B_theta)
+    h = 1e-6
+    vals = []
+    for th in (P.theta + h, P.theta - h):
+        A, B = fam.at(th)
+        g = spk.solve(A, sp.csr_matrix(B.T), P.C1, P.C2,
+                      **dict(OPTS, fixed_d=x.iters, maxit=x.iters))
+        vals.append(float((u @ host(g.X1)) @ (host(g.X2).T @ v)))
+    fd = (vals[0] - vals[1]) / (2 * h)
+    assert fd == pytest.approx(dth, rel=1e-5)
+
+
+def test_autograd_function_backward():
+    from paper_2311_16019_gb300 import spk
+    from paper_2311_16019_gb300.autograd import OperatorFamily, bilinear_loss
+    P = I.workload("cd2d_32_r2")
+    fam = OperatorFamily.from_problem(P)
+    u, v = _uv(P.n1, P.n2)
+    dev = "cuda"
+    C1 = torch.tensor(P.C1, device=dev, requires_grad=True)
+    C2 = torch.tensor(P.C2, device=dev, requires_grad=True)
+    th = torch.tensor(P.theta, dtype=torch.float64, device=dev, requires_grad=True)
+    ut = torch.tensor(u, device=dev, requires_grad=True)
+    vt = torch.tensor(v, device=dev, requires_grad=True)
+    L = bilinear_loss(C1, C2, th, ut, vt, fam, **OPTS)
+    (2.0 * L).backward()
+    ref = ADJ.dense_gradient(P.A, P.B, P.A_theta, P.B_theta, P.C1, P.C2, u, v)
+    assert float(L) == pytest.approx(ref["L"], rel=1e-8)
+    assert np.linalg.norm(host(C1.grad) - 2 * ref["dC1"]) <= 1e-6 * np.linalg.norm(2 * ref["dC1"])
+    assert np.linalg.norm(host(C2.grad) - 2 * ref["dC2"]) <= 1e-6 * np.linalg.norm(2 * ref["dC2"])
+    assert float(th.grad) == pytest.approx(2 * ref["dtheta"], rel=1e-6)
+    assert np.linalg.norm(host(ut.grad) - 2 * ref["du"]) <= 1e-8 * np.linalg.norm(ref["du"])
+    assert np.linalg.norm(host(vt.grad) - 2 * ref["dv"]) <= 1e-8 * np.linalg.norm(ref["dv"])

@@ -1,0 +1,82 @@
+"""The batched form: independent instances of uneven size and rank solved by
+concurrent workers must give, instance by instance, bitwise the result of a
+single solve (the same kernels and fixed-order reductions run), and an
+invalid instance must fail alone."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2311_16019_gb300 import inputs as I  # noqa: E402
+from oracle import spkms as SP, measure as M  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2311_16019_gb300 import build, spk
+    build.build()
+    return spk.load()
+
+
+def _opts(P, maxit=120):
+    npad = 1 << (P.n1 - 1).bit_length()
+    s = min(npad, 2 * P.r * maxit)
+    return dict(k=4, s=s, maxit=min(maxit, s // P.r - 1), p=10, tol=1e-8, seed=11,
+                precision="fp64")
+
+
+def test_batched_equals_single_solves_bitwise():
+    from paper_2311_16019_gb300 import spk
+    probs = I.batched_instances(count=7, seed=9, nmin=12, nmax=40)
+    opts = [_opts(P) for P in probs]
+    rc, outs = spk.solve_batched(probs, concurrency=3, opts_list=opts, raise_on_error=False)
+    assert rc == 0
+    for P, o, g in zip(probs, opts, outs):
+        single = spk.solve(P.A, P.BT, P.C1, P.C2, raise_on_error=False, **o)
+        assert g is not None and g.iters == single.iters and g.rank == single.rank
+        assert torch.equal(g.X1, single.X1) and torch.equal(g.X2, single.X2)
+
+
+def test_batched_against_oracle_fixed_d():
+    """s = 6 (d+1) r keeps the projected spectra in the right half plane for
+    these instances (s = 2 d r does not for one of them: see the next test)."""
+    from paper_2311_16019_gb300 import spk
+    probs = I.batched_instances(count=4, seed=10, nmin=12, nmax=24)
+    opts = []
+    for P in probs:
+        npad = 1 << (P.n1 - 1).bit_length()
+        opts.append(dict(_opts(P, maxit=12), s=min(npad, 6 * P.r * 13), fixed_d=12, tol=0.0))
+    rc, outs = spk.solve_batched(probs, concurrency=4, opts_list=opts)
+    assert rc == 0
+    for P, o, g in zip(probs, opts, outs):
+        ref = SP.spkms(P.A, P.BT, P.C1, P.C2, k=4, s=o["s"], tol=0.0, maxit=12, p=12, seed=11)
+        err = M.rel_error(g.X1.cpu().numpy(), g.X2.cpu().numpy(), ref["X1"], ref["X2"])
+        assert err < 1e-10, (P.name, err)
+
+
+def test_batched_invalid_instance_fails_alone():
+    from paper_2311_16019_gb300 import spk
+    probs = I.batched_instances(count=3, seed=9, nmin=12, nmax=20)
+    opts = [_opts(P) for P in probs]
+    opts[1] = dict(opts[1], s=4)          # s < (maxit + 1) r: invalid
+    rc, outs = spk.solve_batched(probs, concurrency=2, opts_list=opts, raise_on_error=False)
+    assert rc == spk.SPK_ERR_ARG
+    assert outs[1] is None and outs[0] is not None and outs[2] is not None
+
+
+def test_projected_spectrum_off_right_half_plane_is_reported():
+    """With s = 2 d r this instance's sketched projection has an eigenvalue
+    with negative real part (the oracle's H~ has min Re = -41.6), where the
+    sign-function solve does not apply: the solver must say so, not return
+    a wrong X."""
+    from paper_2311_16019_gb300 import spk
+    P = I.batched_instances(count=4, seed=10, nmin=12, nmax=24)[2]
+    with pytest.raises(spk.SpkError) as e:
+        spk.solve(P.A, P.BT, P.C1, P.C2, k=4, s=48, maxit=12, p=12, tol=0.0, seed=11,
+                  fixed_d=12)
+    assert e.value.code == spk.SPK_ERR_SINGULAR_PROJECTED
+    assert "right half plane" in str(e.value)

@@ -208,3 +208,68 @@ def test_converged_conv_diff_r4_randomized_truncation():
     assert err < 1e-8, err
     assert abs(g.rank - o["rank"]) <= 2
     assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 2e-8
+
+
+@pytest.mark.parametrize("form,bound", [("mixed_fp32", 1e-6), ("mixed_bf16", 1e-2)])
+def test_mixed_forms_against_fp64_oracle_fixed_d(form, bound):
+    """Mixed forms (not in the paper): FP32 basis and SpMM, or BF16 basis
+    storage with FP32 accumulation; the sketch side stays FP64.  Parity with
+    the FP64 oracle is unpinned for these forms: the test bounds the measured
+    relative error at a fixed d (printed)."""
+    P = I.workload("cd2d_24_r2")
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=3, s=300, maxit=25, p=1, tol=0.0, seed=7,
+                    fixed_d=25, precision=form)
+    o = SP.spkms(P.A, P.BT, P.C1, P.C2, k=3, s=300, tol=0.0, maxit=25, p=25, seed=7)
+    err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
+    print(f"{form}: relative error vs FP64 oracle at d=25: {err:.3e}")
+    assert err < bound, err
+
+
+def test_mixed_fp32_true_residual_converged():
+    """The FP32-basis form run to tol 1e-8 on the 64 x 64 conv-diff problem
+    (r = 4): converges, true relative residual below 1e-6 (printed)."""
+    P = I.workload("cd2d_64_r4")
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=4, s=3200, maxit=400, p=20, tol=1e-8, seed=0,
+                    precision="mixed_fp32")
+    res = M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2))
+    print(f"mixed_fp32: d={g.iters} converged={g.converged} true residual {res:.3e}")
+    assert g.converged and res < 1e-6, res
+
+
+def test_mixed_bf16_stagnation_is_reported():
+    """The BF16-basis form cannot reach tol 1e-8 (its basis carries ~3e-3
+    relative error); run that far, the corrupted projection leaves the right
+    half plane and the solver reports it (or stops at maxit), never
+    returning factors that claim convergence."""
+    from paper_2311_16019_gb300.spk import SPK_ERR_NOT_CONVERGED, SPK_ERR_SINGULAR_PROJECTED
+    P = I.workload("cd2d_64_r4")
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=4, s=3200, maxit=400, p=20, tol=1e-8, seed=0,
+                    precision="mixed_bf16", raise_on_error=False)
+    print(f"mixed_bf16: status {g.status} d={g.iters}")
+    assert g.status in (SPK_ERR_NOT_CONVERGED, SPK_ERR_SINGULAR_PROJECTED)
+    assert not g.converged
+
+
+@pytest.mark.parametrize("name,k,d", [("lap16_r1", 2, 15), ("cd2d_24_r2", 3, 20),
+                                      ("cd2d_20_r4", 4, 12), ("cd2d_20_r3", 1, 10)])
+def test_truncated_method_fixed_d_parity(name, k, d):
+    """Algorithm 2 (t-PKSM) through the same kernels: X and the residual
+    bound of Proposition 3.1 against the oracle's Algorithm 2."""
+    from oracle import tpkms as TP
+    P = I.workload(name)
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=k, maxit=d, p=1, tol=0.0, fixed_d=d,
+                    method="truncated", trunc_tol=1e-14)
+    o = TP.tpkms(P.A, P.BT, P.C1, P.C2, kA=k, kB=k, tol=0.0, maxit=d, p=d)
+    assert g.iters == d
+    err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
+    assert err < TOL_X, err
+    assert g.rho == pytest.approx(o["hist"][-1][1], rel=1e-8)
+
+
+def test_truncated_method_converged_same_d():
+    from oracle import tpkms as TP
+    P = I.workload("lap32_r1")
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=2, maxit=300, p=1, tol=1e-8, method="truncated")
+    o = TP.tpkms(P.A, P.BT, P.C1, P.C2, kA=2, kB=2, tol=1e-8, maxit=300, p=1)
+    assert g.converged and abs(g.iters - o["d"]) <= 1
+    assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 1e-7
