@@ -326,7 +326,8 @@ def run_spk(args, rank, world, local, pg):
     for form in forms:
         last = None
         for _ in range(args.warmup):
-            last = spk.solve(dA, dB, c1, c2, precision=form, device=local, **opts)
+            last = spk.solve(dA, dB, c1, c2, precision=form, device=local,
+                             raise_on_error=form == forms[0], **opts)
         torch.cuda.synchronize()
         barrier(pg)
         spk.profile_enable(form == forms[0], local)
@@ -340,7 +341,8 @@ def run_spk(args, rank, world, local, pg):
         ev0.record()
         results = []
         for _ in range(args.steps):
-            results.append(spk.solve(dA, dB, c1, c2, precision=form, device=local, **opts))
+            results.append(spk.solve(dA, dB, c1, c2, precision=form, device=local,
+                                     raise_on_error=form == forms[0], **opts))
         ev1.record()
         torch.cuda.synchronize()
         barrier(pg)
@@ -351,6 +353,10 @@ def run_spk(args, rank, world, local, pg):
         spk.profile_enable(False, local)
         ms_max = max_over_ranks(pg, ms)
         g = results[-1]
+        if g.X1 is None:
+            # a later form that stopped with an error (reported, not timed as a solve)
+            per_form[form] = dict(status=g.status, ms_per_step=ms_max / args.steps)
+            continue
         X1, X2 = g.X1.cpu().numpy(), g.X2.cpu().numpy()
         tres = true_residual(P.A, P.B, P.C1, P.C2, X1, X2)
         per_form[form] = dict(ms_per_step=ms_max / args.steps,
@@ -359,13 +365,14 @@ def run_spk(args, rank, world, local, pg):
                               rel_rho=g.rel_rho, true_rel_residual=tres, checks=g.hist_d,
                               ms_phases=dict(arnoldi=g.ms_arnoldi, project=g.ms_project,
                                              recover=g.ms_recover),
-                              gpu_launches=launches, clocks=clocks, prof=prof, X=(X1, X2))
+                              gpu_launches=launches, clocks=clocks, prof=prof, X=(X1, X2),
+                              status=g.status)
         if first is None:
             first = form
     base = per_form[first]
     # error of the mixed form against the FP64 GPU form
     for f, v in per_form.items():
-        if f != first:
+        if f != first and "X" in v:
             v["rel_err_vs_fp64"] = (_lowrank_fro(np.hstack([v["X"][0], -base["X"][0]]),
                                                  np.hstack([v["X"][1], base["X"][1]]))
                                     / _lowrank_fro(*base["X"]))
@@ -450,11 +457,20 @@ def run_kernel_case(args):
     H, G = rhp(), rhp()
     F = np.zeros((m, m))
     F[:4, :4] = rng.standard_normal((4, 4))
+    spk.sylvester_dense(H, G, F)        # warm-up (workspace, first launches)
+    torch.cuda.synchronize()
+    spk.profile_enable(True)
     t0 = time.perf_counter()
     Y, it = spk.sylvester_dense(H, G, F)
     torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    prof = spk.profile_read()
+    spk.profile_enable(False)
+    fams = {k: {"ms": round(v["ms"], 2), "launches": v["launches"],
+                "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4)}
+            for k, v in prof.items() if v["ms"] > 0}
     print(json.dumps({"kernel_case": args.kernel_case, "m": m, "newton_iters": it,
-                      "seconds": time.perf_counter() - t0}), flush=True)
+                      "seconds": secs, "families": fams}), flush=True)
 
 
 def batched_opts(P, form, maxit=2000):
@@ -498,8 +514,11 @@ def run_batched(args):
                                      raise_on_error=False)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
-    conv = sum(1 for g in outs if g is not None and g.converged)
-    failed = sum(1 for g in outs if g is None)
+    conv = sum(1 for g in outs if g.converged)
+    failed = {}
+    for g in outs:
+        if g.X1 is None:
+            failed[str(g.status)] = failed.get(str(g.status), 0) + 1
     line = {"metric": "solves/s, batched form (64 uneven instances)",
             "value": len(insts) * args.steps / secs, "unit": "solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
@@ -508,7 +527,8 @@ def run_batched(args):
                                    "tol=1e-8, p=20 adaptive", "form": form,
                        "concurrency": args.concurrency},
             "seconds_per_batch": secs / args.steps, "converged": conv, "failed": failed,
-            "iters": [g.iters if g is not None else None for g in outs]}
+            "iters": [g.iters if g.X1 is not None else g.status for g in outs],
+            "first_error": spk.handle().error() if failed else ""}
     print(json.dumps(line), flush=True)
 
 

@@ -35,10 +35,12 @@ __global__ void __launch_bounds__(256) k_spmm_dots(const int32_t* __restrict__ r
                                                    const TV* __restrict__ val, int64_t n,
                                                    const TB* __restrict__ U, TC* __restrict__ W,
                                                    WindowPtrs win, double* __restrict__ partial) {
-  double acc[DOTS ? kFuse * R * R : 1];
+  // per-thread partial sums in the compute type (FP32 in the mixed forms,
+  // over a few rows only), cross-thread sums in FP64
+  TC acc[DOTS ? kFuse * R * R : 1];
   if constexpr (DOTS) {
 #pragma unroll
-    for (int e = 0; e < kFuse * R * R; ++e) acc[e] = 0.0;
+    for (int e = 0; e < kFuse * R * R; ++e) acc[e] = TC(0);
   }
   const int nwin = DOTS ? win.nwin : 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -66,21 +68,26 @@ __global__ void __launch_bounds__(256) k_spmm_dots(const int32_t* __restrict__ r
           for (int a = 0; a < R; ++a)
 #pragma unroll
             for (int b = 0; b < R; ++b)
-              acc[(q * R + a) * R + b] = fma((double)u[a], (double)w[b], acc[(q * R + a) * R + b]);
+              acc[(q * R + a) * R + b] = fma(u[a], w[b], acc[(q * R + a) * R + b]);
         }
       }
     }
   }
-  if constexpr (DOTS) block_sum_store<kFuse * R * R>(acc, partial + (int64_t)blockIdx.x * kFuse * R * R);
+  if constexpr (DOTS) {
+    double accd[kFuse * R * R];
+#pragma unroll
+    for (int e = 0; e < kFuse * R * R; ++e) accd[e] = (double)acc[e];
+    block_sum_store<kFuse * R * R>(accd, partial + (int64_t)blockIdx.x * kFuse * R * R);
+  }
 }
 
 // Dots of an already computed U~ against up to four more window blocks.
 template <typename TB, typename TC, int R>
 __global__ void __launch_bounds__(256) k_dots(const TC* __restrict__ W, int64_t n, WindowPtrs win,
                                               double* __restrict__ partial) {
-  double acc[kFuse * R * R];
+  TC acc[kFuse * R * R];
 #pragma unroll
-  for (int e = 0; e < kFuse * R * R; ++e) acc[e] = 0.0;
+  for (int e = 0; e < kFuse * R * R; ++e) acc[e] = TC(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     TC w[R];
@@ -95,20 +102,35 @@ __global__ void __launch_bounds__(256) k_dots(const TC* __restrict__ W, int64_t 
         for (int a = 0; a < R; ++a)
 #pragma unroll
           for (int b = 0; b < R; ++b)
-            acc[(q * R + a) * R + b] = fma((double)u[a], (double)w[b], acc[(q * R + a) * R + b]);
+            acc[(q * R + a) * R + b] = fma(u[a], w[b], acc[(q * R + a) * R + b]);
       }
     }
   }
-  block_sum_store<kFuse * R * R>(acc, partial + (int64_t)blockIdx.x * kFuse * R * R);
+  double accd[kFuse * R * R];
+#pragma unroll
+  for (int e = 0; e < kFuse * R * R; ++e) accd[e] = (double)acc[e];
+  block_sum_store<kFuse * R * R>(accd, partial + (int64_t)blockIdx.x * kFuse * R * R);
 }
 
-__global__ void k_reduce_partials(const double* __restrict__ partial, int nparts, int stride,
-                                  int count, double* __restrict__ out) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+// out[e] = sum_p partial[p*stride + e] for e < count: warp w of the block
+// takes e = w, w + 8, ...; its lanes load the partials p = lane, lane + 32,
+// ... (independent loads in flight) and finish with a shuffle sum, so the
+// order of the additions is fixed.
+__device__ __forceinline__ void sum_partials(const double* __restrict__ partial, int nparts,
+                                             int stride, int count, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = wid; e < count; e += nw) {
     double s = 0.0;
-    for (int p = 0; p < nparts; ++p) s += partial[(int64_t)p * stride + e];
-    out[e] = s;
+    for (int p = lane; p < nparts; p += 32) s += partial[(int64_t)p * stride + e];
+    s = warp_sum(s);
+    if (lane == 0) out[e] = s;
   }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_partials(const double* __restrict__ partial,
+                                                         int nparts, int stride, int count,
+                                                         double* __restrict__ out) {
+  sum_partials(partial, nparts, stride, count, out);
 }
 
 template <typename TB, typename TC, int R>
@@ -118,9 +140,9 @@ __global__ void __launch_bounds__(256) k_update_gram(TC* __restrict__ W, int64_t
   __shared__ TC hs[kMaxWin * R * R];
   for (int e = threadIdx.x; e < win.nwin * R * R; e += blockDim.x) hs[e] = (TC)h[e];
   __syncthreads();
-  double acc[R * R];
+  TC acc[R * R];
 #pragma unroll
-  for (int e = 0; e < R * R; ++e) acc[e] = 0.0;
+  for (int e = 0; e < R * R; ++e) acc[e] = TC(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     TC w[R];
@@ -144,10 +166,15 @@ __global__ void __launch_bounds__(256) k_update_gram(TC* __restrict__ W, int64_t
 #pragma unroll
       for (int a = 0; a < R; ++a)
 #pragma unroll
-        for (int b = 0; b < R; ++b) acc[a * R + b] = fma((double)w[a], (double)w[b], acc[a * R + b]);
+        for (int b = 0; b < R; ++b) acc[a * R + b] = fma(w[a], w[b], acc[a * R + b]);
     }
   }
-  if (want_gram) block_sum_store<R * R>(acc, partial + (int64_t)blockIdx.x * R * R);
+  if (want_gram) {
+    double accd[R * R];
+#pragma unroll
+    for (int e = 0; e < R * R; ++e) accd[e] = (double)acc[e];
+    block_sum_store<R * R>(accd, partial + (int64_t)blockIdx.x * R * R);
+  }
 }
 
 // G = sum of partial Grams; R upper with R^T R = G; Rinv = R^{-1}.
@@ -156,11 +183,7 @@ __global__ void k_chol_small(const double* __restrict__ partial, int nparts, int
                              uint32_t* flags, double rel_floor) {
   __shared__ double G[kMaxR * kMaxR];
   const int rr = r * r;
-  for (int e = threadIdx.x; e < rr; e += blockDim.x) {
-    double s = 0.0;
-    for (int p = 0; p < nparts; ++p) s += partial[(int64_t)p * rr + e];
-    G[e] = s;
-  }
+  sum_partials(partial, nparts, rr, rr, G);
   __syncthreads();
   if (threadIdx.x != 0) return;
   double R[kMaxR][kMaxR] = {};
@@ -210,9 +233,9 @@ __global__ void __launch_bounds__(256) k_scale_gram(TC* __restrict__ W, int64_t 
   __shared__ TC ri[R * R];
   if (threadIdx.x < R * R) ri[threadIdx.x] = (TC)Rinv[threadIdx.x];
   __syncthreads();
-  double acc[R * R];
+  TC acc[R * R];
 #pragma unroll
-  for (int e = 0; e < R * R; ++e) acc[e] = 0.0;
+  for (int e = 0; e < R * R; ++e) acc[e] = TC(0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     TC w[R], o[R];
@@ -230,9 +253,12 @@ __global__ void __launch_bounds__(256) k_scale_gram(TC* __restrict__ W, int64_t 
 #pragma unroll
     for (int a = 0; a < R; ++a)
 #pragma unroll
-      for (int b = 0; b < R; ++b) acc[a * R + b] = fma((double)o[a], (double)o[b], acc[a * R + b]);
+      for (int b = 0; b < R; ++b) acc[a * R + b] = fma(o[a], o[b], acc[a * R + b]);
   }
-  block_sum_store<R * R>(acc, partial + (int64_t)blockIdx.x * R * R);
+  double accd[R * R];
+#pragma unroll
+  for (int e = 0; e < R * R; ++e) accd[e] = (double)acc[e];
+  block_sum_store<R * R>(accd, partial + (int64_t)blockIdx.x * R * R);
 }
 
 template <typename TB, typename TC, int R>
@@ -373,7 +399,7 @@ void spmm_dots_launch(const int32_t* rowptr, const int32_t* col, const TV* val, 
 void reduce_partials_launch(const double* partial, int nparts, int stride, int count,
                             double* out, cudaStream_t st) {
   count_launches(1);
-  k_reduce_partials<<<(count + 127) / 128, 128, 0, st>>>(partial, nparts, stride, count, out);
+  k_reduce_partials<<<1, 256, 0, st>>>(partial, nparts, stride, count, out);
 }
 
 template <typename TB, typename TC>
@@ -390,7 +416,7 @@ void update_gram_launch(TC* W, int64_t n, int r, WindowPtrs win, const double* h
 void chol_small_launch(const double* partial, int nparts, int r, double* R, double* Rinv,
                        uint32_t* flags, double rel_floor, cudaStream_t st) {
   count_launches(1);
-  k_chol_small<<<1, 32, 0, st>>>(partial, nparts, r, R, Rinv, flags, rel_floor);
+  k_chol_small<<<1, 256, 0, st>>>(partial, nparts, r, R, Rinv, flags, rel_floor);
 }
 
 template <typename TC>

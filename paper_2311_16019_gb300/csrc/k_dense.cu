@@ -13,6 +13,8 @@
 // so these are CUDA-core FP64 kernels.
 #include "spk_internal.cuh"
 
+#include <atomic>
+
 #include <algorithm>
 #include <cmath>
 
@@ -109,20 +111,18 @@ __global__ void k_scale_matrix(double* A, int64_t ld, int M, int N, double a) {
 // ---- Gauss-Jordan inversion
 constexpr int kGjeCols = 8;     // columns per CTA (unblocked path)
 constexpr int kGjeThreads = 256;
+constexpr int kGjePanelThreads = 128;
+constexpr int kGjeBatch = 8;     // rows per thread per load batch
+constexpr size_t kGemmReserve = 42 * 1024;
 constexpr int kGjeNb = 64;      // panel width of the blocked path
 constexpr int kGjeBlockedMin = 256;
 
-// Block argmax of |A[i + col*ld]| over i in [j, m), ties to the smaller index.
-__device__ void block_argmax(const double* A, int64_t ld, int m, int j, int col, int* p_out,
-                             double* v_out) {
+// Block-wide argmax of per-thread (best |value|, index) pairs, ties to the
+// smaller index; the result goes to *p_out, *v_out (all threads see it after
+// the final barrier).
+__device__ void block_argmax_reduce(double best, int bidx, int* p_out, double* v_out) {
   __shared__ double bv[32];
   __shared__ int bi[32];
-  double best = -1.0;
-  int bidx = m;
-  for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
-    const double v = fabs(A[i + (int64_t)col * ld]);
-    if (v > best || (v == best && i < bidx)) { best = v; bidx = i; }
-  }
   for (int o = 16; o > 0; o >>= 1) {
     const double ov = __shfl_down_sync(0xffffffffu, best, o);
     const int oi = __shfl_down_sync(0xffffffffu, bidx, o);
@@ -132,7 +132,7 @@ __device__ void block_argmax(const double* A, int64_t ld, int m, int j, int col,
   __syncthreads();
   if (threadIdx.x == 0) {
     double b = -1.0;
-    int ix = m;
+    int ix = 0x7fffffff;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
       if (bv[w] > b || (bv[w] == b && bi[w] < ix)) { b = bv[w]; ix = bi[w]; }
     *p_out = ix;
@@ -141,25 +141,44 @@ __device__ void block_argmax(const double* A, int64_t ld, int m, int j, int col,
   __syncthreads();
 }
 
-// Pivot bookkeeping for column j (called by one CTA, after column j is current).
+// Block argmax of |A[i + col*ld]| over i in [j, m), ties to the smaller index.
+__device__ void block_argmax(const double* A, int64_t ld, int m, int j, int col, int* p_out,
+                             double* v_out) {
+  double best = -1.0;
+  int bidx = m;
+  for (int i = j + threadIdx.x; i < m; i += blockDim.x) {
+    const double v = fabs(A[i + (int64_t)col * ld]);
+    if (v > best || (v == best && i < bidx)) { best = v; bidx = i; }
+  }
+  block_argmax_reduce(best, bidx, p_out, v_out);
+}
+
+// Pivot record of column j (one thread): row p, the pivot value, log|det|,
+// and the zero-pivot flag.
+__device__ void gje_record_pivot(GjeState gs, int j, int p, double piv) {
+  gs.ipiv[j] = p;
+  gs.scal[2 + (j & 1)] = piv;
+  if (!(fabs(piv) > 1e-300) || !isfinite(piv)) atomicOr(gs.flags, kFlagZeroPivot);
+  gs.scal[0] += log(fabs(piv));
+}
+
+// Entry i of pivot column j after the exchange of rows j and p, from the raw
+// column c (before the exchange); cj = c[p], cp = c[j].
+__device__ __forceinline__ double gje_ceff(const double* c, int i, int j, int p, double cj,
+                                           double cp) {
+  return i == j ? cj : (i == p ? cp : c[i]);
+}
+
+// Pivot bookkeeping for column j (called by one CTA, after column j is
+// current): the pivot row p over rows j..m-1 and the raw column j in cvec.
 __device__ void gje_prepare_pivot(double* A, int64_t ld, int m, int j, GjeState gs) {
   __shared__ int sp;
   __shared__ double sv;
   block_argmax(A, ld, m, j, j, &sp, &sv);
   const int p = sp;
   double* c = gs.cvec + (int64_t)(j & 1) * m;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    int src = i;
-    if (i == j) src = p; else if (i == p) src = j;
-    c[i] = A[src + (int64_t)j * ld];
-  }
-  if (threadIdx.x == 0) {
-    const double piv = A[p + (int64_t)j * ld];
-    gs.ipiv[j] = p;
-    gs.scal[2 + (j & 1)] = piv;
-    if (!(fabs(piv) > 1e-300) || !isfinite(piv)) atomicOr(gs.flags, kFlagZeroPivot);
-    gs.scal[0] += log(fabs(piv));
-  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) c[i] = A[i + (int64_t)j * ld];
+  if (threadIdx.x == 0) gje_record_pivot(gs, j, p, A[p + (int64_t)j * ld]);
   __syncthreads();
 }
 
@@ -171,35 +190,73 @@ __global__ void __launch_bounds__(kGjeThreads) k_gje_first(double* A, int64_t ld
 }
 
 // Blocked variant, one pivot step j restricted to the panel columns
-// [k0, k0 + nb): CTA b sweeps column k0 + b (row exchange j <-> p included);
-// the CTA of column j+1 prepares the next pivot when j+1 is in the panel.
-__global__ void __launch_bounds__(kGjeThreads) k_gje_panel_step(double* A, int64_t ld, int m, int j,
-                                                                int k0, int nb, GjeState gs) {
+// [k0, k0 + nb): CTA b sweeps column k0 + b (row exchange j <-> p included).
+// The CTA of column j+1 (when in the panel) also finds the next pivot and
+// stores its raw column during the same sweep.  128 threads per CTA, so that
+// the pivot sweeps fit beside the update GEMMs of the other matrix.
+__global__ void __launch_bounds__(kGjePanelThreads) k_gje_panel_step(double* A, int64_t ld, int m,
+                                                                     int j, int k0, int nb,
+                                                                     GjeState gs) {
   const int p = gs.ipiv[j];
   const double piv = gs.scal[2 + (j & 1)];
   const double rpiv = 1.0 / piv;
-  const double* c = gs.cvec + (int64_t)(j & 1) * m;
+  const double* __restrict__ c = gs.cvec + (int64_t)(j & 1) * m;
+  const double cj = c[p], cp = c[j];
   const int l = k0 + blockIdx.x;
-  double* col = A + (int64_t)l * ld;
+  double* __restrict__ col = A + (int64_t)l * ld;
   const double aj = col[p];
   const double ap = col[j];
   __syncthreads();
+  // rows in batches of kGjeBatch per thread: all loads of a batch are issued
+  // before its stores, so a sweep costs a few memory round trips
+  const int stride = blockDim.x;
   if (l == j) {
-    for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] = (i == j) ? rpiv : -c[i] * rpiv;
-  } else {
-    const double f = aj * rpiv;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      double v;
-      if (i == j) v = f;
-      else {
-        const double base = (i == p) ? ap : col[i];
-        v = fma(-c[i], f, base);
+    for (int b0 = threadIdx.x; b0 < m; b0 += kGjeBatch * stride) {
+      double cv[kGjeBatch];
+#pragma unroll
+      for (int u = 0; u < kGjeBatch; ++u) {
+        const int i = b0 + u * stride;
+        cv[u] = i < m ? c[i] : 0.0;
       }
+#pragma unroll
+      for (int u = 0; u < kGjeBatch; ++u) {
+        const int i = b0 + u * stride;
+        if (i < m) col[i] = (i == j) ? rpiv : -(i == p ? cp : cv[u]) * rpiv;
+      }
+    }
+    return;
+  }
+  const bool next = (l == j + 1) && (j + 1 < k0 + nb);
+  double* __restrict__ cn = gs.cvec + (int64_t)((j + 1) & 1) * m;
+  const double f = aj * rpiv;
+  double best = -1.0;
+  int bidx = m;
+  for (int b0 = threadIdx.x; b0 < m; b0 += kGjeBatch * stride) {
+    double cv[kGjeBatch], av[kGjeBatch];
+#pragma unroll
+    for (int u = 0; u < kGjeBatch; ++u) {
+      const int i = b0 + u * stride;
+      cv[u] = i < m ? c[i] : 0.0;
+      av[u] = i < m ? col[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kGjeBatch; ++u) {
+      const int i = b0 + u * stride;
+      if (i >= m) continue;
+      const double ce = (i == j) ? cj : (i == p ? cp : cv[u]);
+      const double v = (i == j) ? f : fma(-ce, f, (i == p) ? ap : av[u]);
       col[i] = v;
+      if (next) {
+        cn[i] = v;
+        if (i > j && (fabs(v) > best || (fabs(v) == best && i < bidx))) { best = fabs(v); bidx = i; }
+      }
     }
   }
-  __syncthreads();
-  if (l == j + 1 && j + 1 < k0 + nb) gje_prepare_pivot(A, ld, m, j + 1, gs);
+  if (!next) return;
+  __shared__ int sp;
+  __shared__ double sv;
+  block_argmax_reduce(best, bidx, &sp, &sv);
+  if (threadIdx.x == 0) gje_record_pivot(gs, j + 1, sp, col[sp]);
 }
 
 // After a panel: for every column outside it, apply the panel's row
@@ -234,6 +291,7 @@ __global__ void __launch_bounds__(kGjeThreads) k_gje_step(double* A, int64_t ld,
   const double piv = gs.scal[2 + (j & 1)];
   const double rpiv = 1.0 / piv;
   const double* c = gs.cvec + (int64_t)(j & 1) * m;
+  const double cj = c[p], cp = c[j];
   const int l0 = blockIdx.x * kGjeCols;
   const int l1 = min(m, l0 + kGjeCols);
   for (int l = l0; l < l1; ++l) {
@@ -242,16 +300,14 @@ __global__ void __launch_bounds__(kGjeThreads) k_gje_step(double* A, int64_t ld,
     const double ap = col[j];   // row p after the swap
     __syncthreads();
     if (l == j) {
-      for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] = (i == j) ? rpiv : -c[i] * rpiv;
+      for (int i = threadIdx.x; i < m; i += blockDim.x)
+        col[i] = (i == j) ? rpiv : -gje_ceff(c, i, j, p, cj, cp) * rpiv;
     } else {
       const double f = aj * rpiv;
       for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double v;
         if (i == j) v = f;
-        else {
-          const double base = (i == p) ? ap : col[i];
-          v = fma(-c[i], f, base);
-        }
+        else v = fma(-gje_ceff(c, i, j, p, cj, cp), f, (i == p) ? ap : col[i]);
         col[i] = v;
       }
     }
@@ -541,11 +597,25 @@ int grid_for(int64_t work, int block) {
 }  // namespace
 
 void gemm_f64(char ta, char tb, int M, int N, int K, double alpha, const double* A, int64_t lda,
-              const double* B, int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st) {
+              const double* B, int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st,
+              size_t reserve_smem) {
   if (M <= 0 || N <= 0) return;
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  if (reserve_smem > 0) {
+    // static + reserved shared memory passes the default 48 KB per CTA:
+    // opt in once per device
+    static std::atomic<uint64_t> attr_set{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(attr_set.load(std::memory_order_acquire) & bit)) {
+      cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+      attr_set.fetch_or(bit, std::memory_order_acq_rel);
+    }
+  }
   count_launches(1);
-  k_gemm<<<grid, 256, 0, st>>>(ta == 'T', tb == 'T', M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  k_gemm<<<grid, 256, reserve_smem, st>>>(ta == 'T', tb == 'T', M, N, K, alpha, A, lda, B, ldb,
+                                           beta, C, ldc);
 }
 
 void copy_matrix_launch(const double* A, int64_t lda, double* B, int64_t ldb, int M, int N,
@@ -567,35 +637,54 @@ void scale_matrix_launch(double* A, int64_t ld, int M, int N, double a, cudaStre
   k_scale_matrix<<<grid_for((int64_t)M * N, 256), 256, 0, st>>>(A, ld, M, N, a);
 }
 
+bool gje_blocked(int m, const GjeState& gs) {
+  return m > kGjeBlockedMin && gs.panel && gs.bsave;
+}
+
+int gje_panel_width() { return kGjeNb; }
+
+void gje_panel_launch(double* A, int64_t lda, int m, int k0, int nb, GjeState gs, cudaStream_t st) {
+  count_launches(1);
+  k_gje_first<<<1, kGjeThreads, 0, st>>>(A, lda, m, k0, gs);
+  count_launches(nb);
+  for (int j = k0; j < k0 + nb; ++j)
+    k_gje_panel_step<<<nb, kGjePanelThreads, 0, st>>>(A, lda, m, j, k0, nb, gs);
+}
+
+void gje_update_launch(double* A, int64_t lda, int m, int k0, int nb, GjeState gs, cudaStream_t st) {
+  // every column outside the panel: the panel's row exchanges, its pivot rows
+  // saved to Bsave and zeroed; then A[:, R] += Panel * Bsave[:, R]
+  count_launches(1);
+  k_gje_prep<<<grid_for(m, 128), 128, 0, st>>>(A, lda, m, k0, nb, gs.ipiv, gs.bsave);
+  copy_matrix_launch(A + (int64_t)k0 * lda, lda, gs.panel, m, m, nb, st);
+  // unused dynamic shared memory caps the GEMM at three CTAs per SM, which
+  // leaves registers for the other matrix's pivot sweeps running alongside
+  gemm_f64('N', 'N', m, m, nb, 1.0, gs.panel, m, gs.bsave, nb, 1.0, A, lda, st, kGemmReserve);
+}
+
+void gje_finish_launch(double* A, int64_t lda, int m, GjeState gs, cudaStream_t st) {
+  count_launches(1);
+  k_gje_colperm<<<grid_for(m, 128), 128, 0, st>>>(A, lda, m, gs.ipiv);
+}
+
 void gje_invert(double* A, int64_t lda, int m, GjeState gs, cudaStream_t st) {
   if (m <= 0) return;
-  count_launches(1);
-  k_gje_first<<<1, kGjeThreads, 0, st>>>(A, lda, m, 0, gs);
-  if (m <= kGjeBlockedMin || !gs.panel || !gs.bsave) {
+  if (!gje_blocked(m, gs)) {
+    count_launches(1);
+    k_gje_first<<<1, kGjeThreads, 0, st>>>(A, lda, m, 0, gs);
     const int blocks = (m + kGjeCols - 1) / kGjeCols;
     count_launches(m);
     for (int j = 0; j < m; ++j) k_gje_step<<<blocks, kGjeThreads, 0, st>>>(A, lda, m, j, gs);
   } else {
     // Blocked Gauss-Jordan: sweep a panel of kGjeNb columns with one small
-    // launch per pivot, then update every other column with one GEMM
-    //   A[:, R] <- [0 on the pivot rows; A[:, R]] + Panel * A_pivot_rows[:, R].
+    // launch per pivot, then update every other column with one GEMM.
     for (int k0 = 0; k0 < m; k0 += kGjeNb) {
       const int nb = std::min(kGjeNb, m - k0);
-      if (k0 > 0) {
-        count_launches(1);
-        k_gje_first<<<1, kGjeThreads, 0, st>>>(A, lda, m, k0, gs);
-      }
-      count_launches(nb);
-      for (int j = k0; j < k0 + nb; ++j)
-        k_gje_panel_step<<<nb, kGjeThreads, 0, st>>>(A, lda, m, j, k0, nb, gs);
-      count_launches(1);
-      k_gje_prep<<<grid_for(m, 128), 128, 0, st>>>(A, lda, m, k0, nb, gs.ipiv, gs.bsave);
-      copy_matrix_launch(A + (int64_t)k0 * lda, lda, gs.panel, m, m, nb, st);
-      gemm_f64('N', 'N', m, m, nb, 1.0, gs.panel, m, gs.bsave, nb, 1.0, A, lda, st);
+      gje_panel_launch(A, lda, m, k0, nb, gs, st);
+      gje_update_launch(A, lda, m, k0, nb, gs, st);
     }
   }
-  count_launches(1);
-  k_gje_colperm<<<grid_for(m, 128), 128, 0, st>>>(A, lda, m, gs.ipiv);
+  gje_finish_launch(A, lda, m, gs, st);
 }
 
 int sign_combine_grid(int m) { return grid_for((int64_t)m * m, 256) > 304 ? 304 : grid_for((int64_t)m * m, 256); }

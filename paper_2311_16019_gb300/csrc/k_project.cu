@@ -50,7 +50,7 @@ __host__ __device__ void mm(const double* A, const double* B, double* C, int r) 
 }
 
 constexpr int kBRows = 128;   // rows per CTA of the bordering GEMV
-constexpr int kBCols = 256;   // columns of H~ per CTA
+constexpr int kBCols = 64;    // columns of H~ per CTA (enough CTAs to fill the FP64 pipes)
 
 // partial[(chunk*mp + i)*r + c] = sum_{l in chunk} H~[i, l] T_H[l, c]
 __global__ void __launch_bounds__(kBRows) k_border_gemv(const double* __restrict__ Ht, int64_t ldH,

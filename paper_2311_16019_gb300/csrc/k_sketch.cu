@@ -87,41 +87,70 @@ __global__ void k_place_rows(const int32_t* cnt_p, const int32_t* cidx, const in
   }
 }
 
+// First level of the transform: for chunk q (blockIdx.x) and column c
+// (blockIdx.y), the length-n2 Walsh-Hadamard transform of the signed rows
+// q*n2 .. q*n2+n2-1 of column c, written to Y[(t*n1 + q)*r + c].  The stages
+// (butterflies a+b, a-b at distance h = 1, 2, 4, ...) are taken three at a
+// time on eight values held in registers, one shared-memory round trip per
+// three stages; the operations and their order are those of the radix-2
+// sweep.
+template <typename TC>
+__device__ __forceinline__ void bfly(TC& a, TC& b) {
+  const TC x = a, y = b;
+  a = x + y;
+  b = x - y;
+}
+
 template <typename TB, typename TC>
-__global__ void k_fwht_chunks(const TB* __restrict__ X, int64_t n, int r, const int8_t* __restrict__ signs,
-                              int n2, int log2n2, int64_t n1, TC* __restrict__ Y) {
+__global__ void __launch_bounds__(512) k_fwht_chunks(const TB* __restrict__ X, int64_t n, int r,
+                                                     const int8_t* __restrict__ signs, int n2,
+                                                     int log2n2, int64_t n1, TC* __restrict__ Y) {
   extern __shared__ unsigned char smem_raw[];
   TC* buf = reinterpret_cast<TC*>(smem_raw);
   const int64_t chunk = blockIdx.x;
-  const int total = n2 * r;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int t = e / r, c = e - t * r;
+  const int c = blockIdx.y;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
     const int64_t row = chunk * n2 + t;
     TC v = TC(0);
     if (row < n) {
       v = TC(Store<TB>::ld(X + row * r + c));
       if (signs[row] < 0) v = -v;
     }
-    buf[c * n2 + t] = v;
+    buf[t] = v;
   }
   __syncthreads();
-  const int half = n2 >> 1;
-  for (int h = 1; h < n2; h <<= 1) {
-    for (int e = threadIdx.x; e < half * r; e += blockDim.x) {
-      const int c = e / half, b = e - c * half;
-      const int i = ((b / h) * (2 * h)) + (b % h);
-      TC* col = buf + c * n2;
-      const TC a = col[i], bb = col[i + h];
-      col[i] = a + bb;
-      col[i + h] = a - bb;
+  int lg = 0;
+  for (; lg + 3 <= log2n2; lg += 3) {
+    const int h = 1 << lg;
+    for (int b = threadIdx.x; b < (n2 >> 3); b += blockDim.x) {
+      const int base = ((b >> lg) << (lg + 3)) + (b & (h - 1));
+      TC v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = buf[base + k * h];
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) bfly(v[k], v[k + 1]);       // distance h
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (!(k & 2)) bfly(v[k], v[k + 2]);                       // distance 2h
+#pragma unroll
+      for (int k = 0; k < 4; ++k) bfly(v[k], v[k + 4]);           // distance 4h
+#pragma unroll
+      for (int k = 0; k < 8; ++k) buf[base + k * h] = v[k];
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int t = e / r, c = e - t * r;
-    Y[((int64_t)t * n1 + chunk) * r + c] = buf[c * n2 + t];
+  for (; lg < log2n2; ++lg) {
+    const int h = 1 << lg;
+    for (int b = threadIdx.x; b < (n2 >> 1); b += blockDim.x) {
+      const int i = ((b >> lg) << (lg + 1)) + (b & (h - 1));
+      TC a = buf[i], bb = buf[i + h];
+      bfly(a, bb);
+      buf[i] = a;
+      buf[i + h] = bb;
+    }
+    __syncthreads();
   }
-  (void)log2n2;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) Y[((int64_t)t * n1 + chunk) * r + c] = buf[t];
 }
 
 template <typename TC>
@@ -275,21 +304,11 @@ void sketch_apply_launch(const SketchDev& sk, const TB* X, int r, double* SX, TC
     k_identity_sketch<TB><<<grid_for(sk.n * r, 256), 256, 0, st>>>(X, sk.n, r, sk.scale, SX);
     return;
   }
-  const size_t smem = (size_t)sk.n2 * r * sizeof(TC);
-  // the shared-memory opt-in is per device: one bit per device, set once
-  static std::atomic<uint64_t> attr_set{0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const uint64_t bit = 1ull << (dev & 63);
-  if (!(attr_set.load(std::memory_order_acquire) & bit)) {
-    cudaFuncSetAttribute(k_fwht_chunks<TB, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         128 * 1024 * 2 / 2 + 1024);
-    attr_set.fetch_or(bit, std::memory_order_acq_rel);
-  }
-  int threads = (int)std::min<int64_t>(1024, std::max<int64_t>(32, (int64_t)sk.n2 * r / 2));
+  const size_t smem = (size_t)sk.n2 * sizeof(TC);
+  const int threads = (int)std::min<int64_t>(512, std::max<int64_t>(32, (int64_t)sk.n2 >> 3));
   count_launches(1);
-  k_fwht_chunks<TB, TC><<<(unsigned)sk.n1, threads, smem, st>>>(X, sk.n, r, sk.signs, sk.n2,
-                                                                 sk.log2n2, sk.n1, scratch);
+  k_fwht_chunks<TB, TC><<<dim3((unsigned)sk.n1, (unsigned)r), threads, smem, st>>>(
+      X, sk.n, r, sk.signs, sk.n2, sk.log2n2, sk.n1, scratch);
   const int warps_per_block = 8;
   const int blocks = (sk.s + warps_per_block - 1) / warps_per_block;
   count_launches(1);

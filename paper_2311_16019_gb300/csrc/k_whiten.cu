@@ -25,26 +25,31 @@ __global__ void __launch_bounds__(256) k_qt_dot(const double* __restrict__ Q, in
                                                 int m, int64_t rows_per_chunk, int nchunk,
                                                 const double* __restrict__ w,
                                                 double* __restrict__ tpart) {
-  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // warps stride over the items (a grid of a few CTAs per SM): every SM gets
+  // the same share of FP64 work and no partial last wave is left
   const int lane = threadIdx.x & 31;
-  if (item >= (int64_t)m * nchunk) return;
-  const int j = (int)(item % m);
-  const int ch = (int)(item / m);
-  const int64_t i0 = (int64_t)ch * rows_per_chunk;
-  const int64_t i1 = min(s, i0 + rows_per_chunk);
-  const double* q = Q + (int64_t)j * ldq;
-  double acc[R];
+  const int64_t nitems = (int64_t)m * nchunk;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < nitems;
+       item += nwarps) {
+    const int j = (int)(item % m);
+    const int ch = (int)(item / m);
+    const int64_t i0 = (int64_t)ch * rows_per_chunk;
+    const int64_t i1 = min(s, i0 + rows_per_chunk);
+    const double* q = Q + (int64_t)j * ldq;
+    double acc[R];
 #pragma unroll
-  for (int c = 0; c < R; ++c) acc[c] = 0.0;
-  for (int64_t i = i0 + lane; i < i1; i += 32) {
-    const double qi = q[i];
+    for (int c = 0; c < R; ++c) acc[c] = 0.0;
+    for (int64_t i = i0 + lane; i < i1; i += 32) {
+      const double qi = q[i];
 #pragma unroll
-    for (int c = 0; c < R; ++c) acc[c] = fma(qi, w[i + c * s], acc[c]);
-  }
+      for (int c = 0; c < R; ++c) acc[c] = fma(qi, w[i + c * s], acc[c]);
+    }
 #pragma unroll
-  for (int c = 0; c < R; ++c) {
-    const double v = warp_sum(acc[c]);
-    if (lane == 0) tpart[((int64_t)ch * m + j) * R + c] = v;
+    for (int c = 0; c < R; ++c) {
+      const double v = warp_sum(acc[c]);
+      if (lane == 0) tpart[((int64_t)ch * m + j) * R + c] = v;
+    }
   }
 }
 
@@ -61,7 +66,7 @@ __global__ void k_qt_finish(const double* __restrict__ tpart, int64_t count, int
 
 constexpr int kRowTile = 128;
 constexpr int kColChunk = 256;
-constexpr int kQtMaxChunks = 16;
+constexpr int kQtMaxChunks = 32;
 
 // partial[(chunk*s + i)*r + c] = sum_{j in chunk} Q[i + j*ldq] * t[j*r + c]
 template <int R>
@@ -186,7 +191,7 @@ void qt_dot_launch(const double* Q, int64_t ldq, int64_t s, int m, const double*
   const int nc = qt_dot_chunks(s, m);
   const int64_t rows = ((s + nc - 1) / nc + 31) / 32 * 32;
   double* out = nc == 1 ? t : tpart;
-  const unsigned blocks = (unsigned)(((int64_t)m * nc + 7) / 8);
+  const unsigned blocks = (unsigned)std::min<int64_t>(((int64_t)m * nc + 7) / 8, 152 * 8);
   count_launches(1);
   switch (r) {
     case 1: k_qt_dot<1><<<blocks, 256, 0, st>>>(Q, ldq, s, m, rows, nc, w, out); break;

@@ -43,12 +43,12 @@ struct Buf {
 // the launching stream around each group of launches).
 enum ProfFam {
   F_SPMM, F_UPDATE, F_SCALE, F_SKETCH, F_QTDOT, F_QUPDATE, F_TSQR, F_BORDER,
-  F_GJE, F_GEMM, F_SIGNCOMB, F_RHO, F_TRUNC, F_TRSM, F_XACC, F_COUNT
+  F_GJE, F_GEMM, F_SIGNCOMB, F_RHO, F_TRUNC, F_TRSM, F_XACC, F_GJE_PANEL, F_GJE_UPDATE, F_COUNT
 };
 static const char* kFamNames[F_COUNT] = {
   "spmm_dots", "gs_update", "cholqr_scale", "sketch_srht", "whiten_qt_dot", "whiten_q_update",
   "whiten_cholqr", "border_update", "gje_invert", "gemm_f64", "sign_combine", "rho", "truncate_svd",
-  "trsm", "x_accumulate"};
+  "trsm", "x_accumulate", "gje_panel_H", "gje_update_H"};
 
 struct ProfAcc {
   double ms = 0, bytes = 0, flops = 0;
@@ -106,6 +106,9 @@ struct spk_handle {
   // other's GEMM updates)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // set by the sign iteration when it fails because of the spectrum (an
+  // eigenvalue off the open right half plane, or no convergence)
+  bool spectrum_bad = false;
   // batched form: worker handles, each with its own stream and workspace
   struct Worker {
     spk_handle* h = nullptr;
@@ -295,8 +298,30 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
       GjeState gg{ipivG, cvecG, scalG, h->flags, gpanelG, gbsaveG};
       CK(cudaEventRecord(h->ev_fork, st));
       CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
-      gje_invert(Hinv, m, m, gh, st);
-      gje_invert(Ginv, m, m, gg, h->aux);
+      if (gje_blocked(m, gh)) {
+        // the two blocked inversions interleaved panel by panel; the
+        // sub-families time the H inversion's own stream
+        const int nbw = gje_panel_width();
+        for (int k0 = 0; k0 < m; k0 += nbw) {
+          const int nb = std::min(nbw, m - k0);
+          {
+            ProfScope pp(h, F_GJE_PANEL, st, 16.0 * m * nb, 2.0 * m * nb * nb);
+            gje_panel_launch(Hinv, m, m, k0, nb, gh, st);
+          }
+          gje_panel_launch(Ginv, m, m, k0, nb, gg, h->aux);
+          {
+            ProfScope pu(h, F_GJE_UPDATE, st, 8.0 * (2.0 * m * m + 2.0 * m * nb),
+                         2.0 * m * m * nb);
+            gje_update_launch(Hinv, m, m, k0, nb, gh, st);
+          }
+          gje_update_launch(Ginv, m, m, k0, nb, gg, h->aux);
+        }
+        gje_finish_launch(Hinv, m, m, gh, st);
+        gje_finish_launch(Ginv, m, m, gg, h->aux);
+      } else {
+        gje_invert(Hinv, m, m, gh, st);
+        gje_invert(Ginv, m, m, gg, h->aux);
+      }
       CK(cudaEventRecord(h->ev_join, h->aux));
       CK(cudaStreamWaitEvent(st, h->ev_join, 0));
     }
@@ -375,9 +400,11 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
     delta_prev = delta;
   }
   *iters_out = it;
-  if (!converged)
+  if (!converged) {
+    h->spectrum_bad = true;
     return fail(h, SPK_ERR_SINGULAR_PROJECTED,
                 "sign iteration did not converge in %d steps (m=%d)", max_newton, m);
+  }
   // The iterates converge to sign(H) and sign(G), which are the identity
   // only if every eigenvalue lies in the open right half plane; otherwise
   // the limit of F is not 2Y.  trace(sign(H)) = m - 2 (#eigenvalues with
@@ -388,11 +415,13 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
     CK(cudaMemcpyAsync(tr, part, sizeof tr, cudaMemcpyDeviceToHost, st));
     TRY(wait_stream(h, st, h->host_wait_s));
     const int negH = (int)std::lround((m - tr[0]) / 2.0), negG = (int)std::lround((m - tr[1]) / 2.0);
-    if (negH != 0 || negG != 0)
+    if (negH != 0 || negG != 0) {
+      h->spectrum_bad = true;
       return fail(h, SPK_ERR_SINGULAR_PROJECTED,
                   "projected matrices have %d and %d eigenvalues off the open right half plane "
-                  "(m=%d): the sign iteration does not apply; a larger sketch s helps",
+                  "(m=%d): the sign iteration does not apply",
                   negH, negG, m);
+    }
   }
   if (fact) {
     const double mm2 = (double)m * m;
@@ -990,6 +1019,7 @@ struct Solver {
     int newton = 0;
     int d = 0;
     bool converged = false;
+    int last_good = 0;
     double ms_proj = 0.0;
     int next_check = o.fixed_d > 0 ? o.fixed_d : (o.check_schedule == SPK_CHECK_ADAPTIVE ? o.p : o.p);
     const int dmax = o.fixed_d > 0 ? std::min(o.fixed_d, o.maxit) : o.maxit;
@@ -1009,7 +1039,52 @@ struct Solver {
       CK(cudaGetLastError());
       TRY(flags_to_status(h, f));
       cudaEventRecord(ec0, st);
-      TRY(check(d, rho3, &newton));
+      h->spectrum_bad = false;
+      int crc = check(d, rho3, &newton);
+      if (crc == SPK_ERR_SINGULAR_PROJECTED && h->spectrum_bad && o.fixed_d <= 0) {
+        // Eigenvalues of H~ or G~ off the open right half plane.  Past
+        // convergence the truncated basis degrades and such eigenvalues
+        // appear; the leading block of H~_d is H~_d' for every d' < d, so
+        // bisect between the last good check and d for a check that solves.
+        int lo = last_good, hi = d, found = -1;
+        while (hi - lo > 1) {
+          const int mid = lo + (hi - lo) / 2;
+          double r3[3] = {0, 0, 0};
+          h->spectrum_bad = false;
+          const int rc2 = check(mid, r3, &newton);
+          if (rc2 == SPK_OK) {
+            hd.push_back(mid);
+            hrel.push_back(r3[1]);
+            if (!std::isfinite(r3[1])) return fail(h, SPK_ERR_NONFINITE, "non-finite residual estimate at d=%d", mid);
+            if (r3[1] < o.tol) {
+              found = mid;
+              for (int e = 0; e < 3; ++e) rho3[e] = r3[e];
+              break;
+            }
+            lo = mid;
+          } else if (rc2 == SPK_ERR_SINGULAR_PROJECTED && h->spectrum_bad) {
+            hi = mid;
+          } else {
+            return rc2;
+          }
+        }
+        if (found < 0 && lo == 0) return crc;  // no solvable check at all (message kept)
+        if (found < 0) {
+          // not converged: the factors of the last solvable check
+          TRY(check(lo, rho3, &newton));
+          d = lo;
+        } else {
+          d = found;
+          converged = true;
+        }
+        cudaEventRecord(ec1, st);
+        TRY(wait_stream(h, st, h->host_wait_s));
+        float msb = 0.f;
+        cudaEventElapsedTime(&msb, ec0, ec1);
+        ms_proj += msb;
+        break;
+      }
+      TRY(crc);
       cudaEventRecord(ec1, st);
       TRY(wait_stream(h, st, h->host_wait_s));
       float ms = 0.f;
@@ -1022,6 +1097,7 @@ struct Solver {
         converged = true;
         break;
       }
+      last_good = d;
       if (o.check_schedule == SPK_CHECK_ADAPTIVE && o.fixed_d <= 0) {
         // Doubling warm-up (checks at p, 2p, 4p, ...) until log(rho) has
         // decreased over two checks; then extrapolate log(rho) linearly in d

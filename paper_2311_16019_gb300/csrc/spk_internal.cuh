@@ -205,7 +205,8 @@ void fill_factor_launch(double* L, int64_t ldL, int r, const double* beta, cudaS
 
 // ---------------------------------------------------------------- dense FP64
 void gemm_f64(char ta, char tb, int M, int N, int K, double alpha, const double* A, int64_t lda,
-              const double* B, int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st);
+              const double* B, int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t st,
+              size_t reserve_smem = 0);
 void copy_matrix_launch(const double* A, int64_t lda, double* B, int64_t ldb, int M, int N,
                         cudaStream_t st);
 void set_zero_launch(double* A, int64_t count, cudaStream_t st);
@@ -218,6 +219,15 @@ struct GjeState {
   double* bsave = nullptr;   // 64 x m scratch (blocked path)
 };
 void gje_invert(double* A, int64_t lda, int m, GjeState gs, cudaStream_t st);
+// The blocked inversion's pieces (m > 256 with panel/bsave scratch): for
+// k0 = 0, nb, 2 nb, ...: gje_panel_launch (pivot sweeps of columns
+// [k0, k0+nb)) then gje_update_launch (row exchanges and GEMM update of all
+// other columns); finally gje_finish_launch (column permutation).
+bool gje_blocked(int m, const GjeState& gs);
+int gje_panel_width();
+void gje_panel_launch(double* A, int64_t lda, int m, int k0, int nb, GjeState gs, cudaStream_t st);
+void gje_update_launch(double* A, int64_t lda, int m, int k0, int nb, GjeState gs, cudaStream_t st);
+void gje_finish_launch(double* A, int64_t lda, int m, GjeState gs, cudaStream_t st);
 int sign_combine_grid(int m);
 void sign_combine_launch(double* Hk, const double* Hinv, int64_t ld, int m, double c,
                          double* partial, int grid, cudaStream_t st);

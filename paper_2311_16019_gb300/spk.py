@@ -329,7 +329,8 @@ def solve_batched(problems, *, concurrency: int = 8, device: int = 0, stream=Non
     C2 as scipy CSR / arrays) by concurrent workers on the device.
 
     Options are common (**opts) unless opts_list gives one dict per
-    instance.  Returns (status, [SolveResult or None per instance])."""
+    instance.  Returns (status, [SolveResult per instance]); an instance that
+    failed has X1 = X2 = None and its own status."""
     torch = _torch()
     h = handle(device)
     keep = []
@@ -350,10 +351,12 @@ def solve_batched(problems, *, concurrency: int = 8, device: int = 0, stream=Non
         if outs[i].status in (SPK_OK, SPK_ERR_NOT_CONVERGED):
             results.append(_result_to_py(h.lib, outs[i]))
         else:
-            results.append(None)
+            results.append(SolveResult(outs[i].status, 0, 0, False, float("nan"), float("nan"),
+                                       None, None, [], [], 0, 0, 0, 0.0, 0.0, 0.0))
         h.lib.spk_result_free(C.byref(outs[i]))
+    msg = h.error() if rc != SPK_OK else ""
     if rc != SPK_OK and raise_on_error:
-        raise SpkError(rc, h.error())
+        raise SpkError(rc, msg)
     return rc, results
 
 

@@ -37,7 +37,7 @@ def test_batched_equals_single_solves_bitwise():
     assert rc == 0
     for P, o, g in zip(probs, opts, outs):
         single = spk.solve(P.A, P.BT, P.C1, P.C2, raise_on_error=False, **o)
-        assert g is not None and g.iters == single.iters and g.rank == single.rank
+        assert g.X1 is not None and g.iters == single.iters and g.rank == single.rank
         assert torch.equal(g.X1, single.X1) and torch.equal(g.X2, single.X2)
 
 
@@ -65,7 +65,8 @@ def test_batched_invalid_instance_fails_alone():
     opts[1] = dict(opts[1], s=4)          # s < (maxit + 1) r: invalid
     rc, outs = spk.solve_batched(probs, concurrency=2, opts_list=opts, raise_on_error=False)
     assert rc == spk.SPK_ERR_ARG
-    assert outs[1] is None and outs[0] is not None and outs[2] is not None
+    assert outs[1].X1 is None and outs[1].status == spk.SPK_ERR_ARG
+    assert outs[0].X1 is not None and outs[2].X1 is not None
 
 
 def test_projected_spectrum_off_right_half_plane_is_reported():

@@ -273,3 +273,19 @@ def test_truncated_method_converged_same_d():
     o = TP.tpkms(P.A, P.BT, P.C1, P.C2, kA=2, kB=2, tol=1e-8, maxit=300, p=1)
     assert g.converged and abs(g.iters - o["d"]) <= 1
     assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 1e-7
+
+
+def test_check_past_convergence_backtracks():
+    """A first check far past convergence (p = 200 on the 16^3 problem, which
+    converges near d = 60) meets projected eigenvalues off the right half
+    plane; the solver bisects back to a solvable check.  Its factors equal
+    those of a fixed-d solve at the d it reports, and the true residual is at
+    tol."""
+    P = I.workload("cd3d_16_r2")
+    opts = dict(k=3, s=1600, maxit=250, tol=1e-8, seed=0)
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, p=200, **opts)
+    assert g.converged and g.iters < 200, (g.iters, g.hist_d)
+    assert g.hist_d[0] < 200          # the check at d = 200 itself failed
+    f = spk().solve(P.A, P.BT, P.C1, P.C2, p=1, fixed_d=g.iters, **dict(opts, tol=0.0))
+    assert torch.equal(g.X1, f.X1) and torch.equal(g.X2, f.X2)
+    assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 1e-7
