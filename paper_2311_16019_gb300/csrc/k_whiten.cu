@@ -45,11 +45,7 @@ __global__ void __launch_bounds__(256) k_qt_dot(const double* __restrict__ Q, in
 #pragma unroll
       for (int c = 0; c < R; ++c) acc[c] = fma(qi, w[i + c * s], acc[c]);
     }
-#pragma unroll
-    for (int c = 0; c < R; ++c) {
-      const double v = warp_sum(acc[c]);
-      if (lane == 0) tpart[((int64_t)ch * m + j) * R + c] = v;
-    }
+    warp_sum_store<R>(acc, tpart + ((int64_t)ch * m + j) * R);
   }
 }
 
@@ -178,8 +174,9 @@ int grid_for(int64_t work, int block) {
 }  // namespace
 
 int qt_dot_chunks(int64_t s, int m) {
-  // about four waves of 8-warp blocks over 152 SMs, at least 256 rows per chunk
-  const int64_t target = 4LL * 152 * 64;
+  // about two warps' worth of items per resident warp slot (152 SMs x 64),
+  // at least 256 rows per chunk
+  const int64_t target = 2LL * 152 * 64;
   int64_t nc = (target + m - 1) / std::max(1, m);
   nc = std::min<int64_t>(nc, std::max<int64_t>(1, s / 256));
   return (int)std::max<int64_t>(1, std::min<int64_t>(nc, kQtMaxChunks));
