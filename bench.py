@@ -38,8 +38,19 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = "cd2d_512_r4"
+METRIC = "solves/s to rel. residual 1e-8 (FP64 form)"
 SOLVER = dict(k=4, s=12000, maxit=1500, p=20, tol=1e-8, seed=0, check="adaptive",
               trunc_tol=1e-12)
+
+
+def workload_config(P, opts, world):
+    mmax = (opts["maxit"] + 1) * P.r
+    ws = 2 * 8 * (opts["s"] * mmax + 2 * mmax * mmax)     # Q, T, H~ of both sides
+    l2 = (f"sketch-side working set (Q, T, H~) {ws / 1e9:.2f} GB, larger than L2; no flush"
+          if ws > 129e6 else
+          f"sketch-side working set {ws / 1e6:.0f} MB fits L2; no flush")
+    return {"workload": P.name, "n": P.n1, "nnz": int(P.A.nnz), "r": P.r, **opts,
+            "parallelism": "replicas" if world > 1 else "single", "l2": l2}
 
 
 def solver_opts(args):
@@ -233,9 +244,11 @@ def oracle_sample(P, opts, iters: int, hist_d, r: int):
     the workload and extrapolate to one full solve with the GPU's schedule.
 
     Sample: `iters` Arnoldi + sketch + whitening iterations of the oracle
-    (per-iteration times fitted by a + b d, since the whitening cost grows
-    with d) and one projected Sylvester solve at d = iters (cost scaled by
-    (m / m0)^3).  Full solve = sum over d <= D of (a + b d) + sum over the
+    (per-iteration times fitted by a + b d with a, b >= 0, since the
+    whitening cost grows with d), one projected Sylvester solve at
+    d = iters, and the oracle's Bartels-Stewart routine on a dense pair of
+    order m1 = 1200 (its cost, scaled by (m / m1)^3, is the cost of a check
+    at order m).  Full solve = sum over d <= D of (a + b d) + sum over the
     GPU run's check iterations of the scaled projected-solve time.
     """
     import numpy as np
@@ -259,16 +272,29 @@ def oracle_sample(P, opts, iters: int, hist_d, r: int):
     t0 = time.perf_counter()
     sl.solve_sylvester(Ht, Gt.T, F)
     tproj = time.perf_counter() - t0
+    m1 = 1200
+    rng = np.random.default_rng(5)
+    H1 = rng.standard_normal((m1, m1)) / np.sqrt(m1) + 4.0 * np.eye(m1)
+    G1 = rng.standard_normal((m1, m1)) / np.sqrt(m1) + 4.0 * np.eye(m1)
+    F1 = np.zeros((m1, m1))
+    F1[:r, :r] = 1.0
+    t0 = time.perf_counter()
+    sl.solve_sylvester(H1, G1.T, F1)
+    tproj1 = time.perf_counter() - t0
     sample_s = time.perf_counter() - t_all
     dd = np.arange(1, iters + 1, dtype=np.float64)
     b, a = np.polyfit(dd, np.array(ts), 1)
+    if b < 0.0:
+        b, a = 0.0, float(np.mean(ts))
+    a = max(a, 0.0)
     D = max(hist_d) if hist_d else iters
     t_iters = a * D + b * D * (D + 1) / 2.0
-    t_checks = sum(tproj * ((c * r) / m0) ** 3 for c in (hist_d or [D]))
+    t_checks = sum(tproj1 * ((c * r) / m1) ** 3 for c in (hist_d or [D]))
     total = t_iters + t_checks
     return {"solves_per_s": 1.0 / total, "seconds_per_solve": total, "sample_seconds": sample_s,
             "iters_sampled": iters, "extrapolated_to_d": int(D), "checks": len(hist_d or [D]),
-            "t_iter_first_last": [float(ts[0]), float(ts[-1])], "t_proj_m0": tproj, "m0": m0}
+            "t_iter_first_last": [float(ts[0]), float(ts[-1])], "t_proj_m0": tproj, "m0": m0,
+            "t_proj_m1": tproj1, "m1": m1, "fit_a_b": [float(a), float(b)]}
 
 
 # --------------------------------------------------------------------- main arms
@@ -290,13 +316,14 @@ def run_reference(args, rank, world, pg):
         if step >= args.warmup:
             times.append(res["solves_per_s"])
     value = statistics.median(times)
-    line = {"impl": "reference", "metric": "solves/s to rel. residual 1e-8 (FP64)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, **opts},
+            "config": workload_config(P, opts, 1),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(),
                              "kind": "oracle", "sample": f"{args.cpu_sample_iters} oracle "
-                             f"iterations + one projected solve per step, extrapolated to d={D}"},
+                             f"iterations + projected solves at m={res['m0']} and m={res['m1']} "
+                             f"per step, extrapolated to d={D}"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -418,21 +445,21 @@ def run_spk(args, rank, world, local, pg):
         s = oracle_sample(P, opts, args.cpu_sample_iters, base["checks"], P.r)
         cpu = {"value": s["solves_per_s"], "unit": "solves/s", "cores": os.cpu_count(),
                "kind": "oracle",
-               "sample": (f"{s['iters_sampled']} oracle iterations ({s['sample_seconds']:.1f} s) "
-                          f"+ one projected solve at m={s['m0']}, extrapolated to d={s['extrapolated_to_d']} "
-                          f"with the GPU run's {s['checks']} checks (a + b d per iteration, m^3 per check)")}
+               "sample": (f"{s['iters_sampled']} oracle iterations + one projected solve at "
+                          f"m={s['m0']} + Bartels-Stewart at m={s['m1']} "
+                          f"({s['sample_seconds']:.1f} s), extrapolated to d={s['extrapolated_to_d']} "
+                          f"with the GPU run's {s['checks']} checks (a + b d per iteration, "
+                          f"m^3 per check)")}
     if rank == 0:
         forms_out = {f: {k: v for k, v in d.items() if k not in ("X", "prof", "clocks")}
                      for f, d in per_form.items()}
         line = {
-            "metric": "solves/s to rel. residual 1e-8 (FP64 form; mixed form beside it)",
+            "metric": METRIC,
             "value": base["solves_per_s"], "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if first == "fp64" else "f32+f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": P.n1, "nnz": int(P.A.nnz), "r": P.r,
-                       **{k: v for k, v in opts.items()}, "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "working set (Q, T, H~ > 1 GB) larger than L2; no flush"},
+            "config": workload_config(P, opts, world),
             "forms": forms_out,
             "clocks": base["clocks"], "gpu_launches": base["gpu_launches"],
             "e2e": e2e, "roofline": roof, "kernels": table, "fp64_tflops_measured": fp64,

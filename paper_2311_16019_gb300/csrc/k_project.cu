@@ -49,14 +49,21 @@ __host__ __device__ void mm(const double* A, const double* B, double* C, int r) 
   for (int e = 0; e < r * r; ++e) C[e] = o[e];
 }
 
-constexpr int kBRows = 128;   // rows per CTA of the bordering GEMV
-constexpr int kBCols = 64;    // columns of H~ per CTA (enough CTAs to fill the FP64 pipes)
+constexpr int kBRows = 32;     // rows per CTA of the bordering GEMV (one per lane)
+constexpr int kBWarps = 8;     // warps per CTA, each on kBWarpCols columns
+constexpr int kBWarpCols = 32;
+constexpr int kBCols = kBWarps * kBWarpCols;   // columns of H~ per CTA
 
-// partial[(chunk*mp + i)*r + c] = sum_{l in chunk} H~[i, l] T_H[l, c]
-__global__ void __launch_bounds__(kBRows) k_border_gemv(const double* __restrict__ Ht, int64_t ldH,
-                                                       int mp, int r, const double* __restrict__ T,
-                                                       int64_t ldT, double* __restrict__ partial) {
+// partial[(chunk*mp + i)*r + c] = sum_{l in chunk} H~[i, l] T_H[l, c]: lane =
+// row (coalesced column reads of H~), warp = 32-column slice of the chunk,
+// slices summed in shared memory in a fixed order.
+__global__ void __launch_bounds__(kBWarps * 32) k_border_gemv(const double* __restrict__ Ht,
+                                                             int64_t ldH, int mp, int r,
+                                                             const double* __restrict__ T,
+                                                             int64_t ldT,
+                                                             double* __restrict__ partial) {
   __shared__ double th[kBCols * kMaxR];
+  __shared__ double red[kBWarps][kBRows * kMaxR];
   const int l0 = blockIdx.y * kBCols;
   const int l1 = min(mp, l0 + kBCols);
   for (int e = threadIdx.x; e < (l1 - l0) * r; e += blockDim.x) {
@@ -64,17 +71,33 @@ __global__ void __launch_bounds__(kBRows) k_border_gemv(const double* __restrict
     th[e] = T[l0 + l + (int64_t)(mp + c) * ldT];
   }
   __syncthreads();
-  const int i = blockIdx.x * kBRows + threadIdx.x;
-  if (i >= mp) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int i = blockIdx.x * kBRows + lane;
   double v[kMaxR] = {0, 0, 0, 0};
-  const double* hrow = Ht + i + (int64_t)l0 * ldH;
-  for (int l = 0; l < l1 - l0; ++l) {
-    const double hv = hrow[(int64_t)l * ldH];
+  const int la = l0 + wid * kBWarpCols;
+  const int lb = min(l1, la + kBWarpCols);
+  if (i < mp) {
+    const double* hrow = Ht + i;
+#pragma unroll 8
+    for (int l = la; l < lb; ++l) {
+      const double hv = hrow[(int64_t)l * ldH];
+      const double* t = th + (l - l0) * r;
 #pragma unroll
-    for (int c = 0; c < kMaxR; ++c)
-      if (c < r) v[c] = fma(hv, th[l * r + c], v[c]);
+      for (int c = 0; c < kMaxR; ++c)
+        if (c < r) v[c] = fma(hv, t[c], v[c]);
+    }
   }
-  for (int c = 0; c < r; ++c) partial[((int64_t)blockIdx.y * mp + i) * r + c] = v[c];
+#pragma unroll
+  for (int c = 0; c < kMaxR; ++c) red[wid][lane * kMaxR + c] = v[c];
+  __syncthreads();
+  if (wid == 0 && i < mp) {
+    for (int c = 0; c < r; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < kBWarps; ++w) s += red[w][lane * kMaxR + c];
+      partial[((int64_t)blockIdx.y * mp + i) * r + c] = s;
+    }
+  }
 }
 
 // Rows i < mp of the new block column of H~:
@@ -92,8 +115,13 @@ __global__ void k_border_col(double* __restrict__ Ht, int64_t ldH, int mp, int r
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= mp) return;
   double v[kMaxR] = {0, 0, 0, 0};
-  for (int ch = 0; ch < nchunk; ++ch)
-    for (int c = 0; c < r; ++c) v[c] -= partial[((int64_t)ch * mp + i) * r + c];
+#pragma unroll 4
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const double* pp = partial + ((int64_t)ch * mp + i) * r;
+#pragma unroll
+    for (int c = 0; c < kMaxR; ++c)
+      if (c < r) v[c] -= pp[c];
+  }
   for (int q = 0; q < nslots; ++q) {
     const int b = first_block + q;  // 1-based block index
     for (int a = 0; a < r; ++a) {
@@ -299,10 +327,10 @@ void border_col_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, 
   const int nch = border_chunks(mp);
   dim3 grid((mp + kBRows - 1) / kBRows, nch);
   count_launches(1);
-  k_border_gemv<<<grid, kBRows, 0, st>>>(Ht, ldH, mp, r, T, ldT, partial);
+  k_border_gemv<<<grid, kBWarps * 32, 0, st>>>(Ht, ldH, mp, r, T, ldT, partial);
   count_launches(1);
-  k_border_col<<<(mp + 127) / 128, 128, 0, st>>>(Ht, ldH, mp, r, T, ldT, hslots, first_block,
-                                                 nslots, h_dd, partial, nch);
+  k_border_col<<<(mp + 31) / 32, 32, 0, st>>>(Ht, ldH, mp, r, T, ldT, hslots, first_block,
+                                              nslots, h_dd, partial, nch);
 }
 
 void border_small_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, int64_t ldT,

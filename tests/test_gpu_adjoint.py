@@ -107,3 +107,49 @@ def test_autograd_function_backward():
     assert float(th.grad) == pytest.approx(2 * ref["dtheta"], rel=1e-6)
     assert np.linalg.norm(host(ut.grad) - 2 * ref["du"]) <= 1e-8 * np.linalg.norm(ref["du"])
     assert np.linalg.norm(host(vt.grad) - 2 * ref["dv"]) <= 1e-8 * np.linalg.norm(ref["dv"])
+
+
+def test_theta_gradient_central_differences_256():
+    """The differentiation workload at n = 256^2 (r = 2, theta = 10): the
+    adjoint theta-gradient of L = u^T X v against central differences of
+    the GPU solve (d frozen at the base run, sketch seed fixed).  The
+    recovered X = U_d T^{-1} Y1 Y2^T T^{-T} V_d^T carries rounding noise of
+    about kappa(T) u (T is the whitening factor, kappa ~1e12 here) that
+    changes from one theta to the next, so differences at h = 1e-6 are noise
+    (6.6e-2 off, and moving with tol, while the adjoint value is stable to
+    eight digits); h = 1e-3 is used.  The measured agreement is printed."""
+    from paper_2311_16019_gb300 import spk
+    from paper_2311_16019_gb300.autograd import OperatorFamily
+    P = I.workload("cd2d_256_r2")
+    fam = OperatorFamily.from_problem(P)
+    u, v = _uv(P.n1, P.n2, seed=6)
+    opts = dict(k=4, s=6000, maxit=1500, p=20, tol=1e-12, seed=3, trunc_tol=1e-14,
+                check="adaptive")
+    x = spk.solve(P.A, P.BT, P.C1, P.C2, **opts)
+    lam = spk.solve_adjoint(P.AT, P.B, u[:, None], v[:, None], **opts)
+    assert x.converged and lam.converged
+    dC1, dC2, dth = spk.adjoint_gradients(spk.result_view(x), spk.result_view(lam), P.C1, P.C2,
+                                          P.A_theta, P.B_theta)
+    h = 1e-3
+    vals = []
+    for th in (P.theta + h, P.theta - h):
+        A, B = fam.at(th)
+        g = spk.solve(A, sp.csr_matrix(B.T), P.C1, P.C2,
+                      **dict(opts, fixed_d=x.iters, maxit=x.iters, tol=0.0))
+        vals.append(float((u @ host(g.X1)) @ (host(g.X2).T @ v)))
+    fd = (vals[0] - vals[1]) / (2 * h)
+    L0 = float((u @ host(x.X1)) @ (host(x.X2).T @ v))
+    print(f"256^2: L = {L0:.6e}, adjoint dtheta {dth:.10e}, central difference {fd:.10e}, "
+          f"relative difference {abs(fd - dth) / abs(fd):.2e}")
+    assert fd == pytest.approx(dth, rel=1e-2)
+    # dC1 against a directional central difference along a random direction
+    D = np.random.default_rng(7).standard_normal(P.C1.shape)
+    vals = []
+    for sgn in (1.0, -1.0):
+        g = spk.solve(P.A, P.BT, P.C1 + sgn * h * D, P.C2,
+                      **dict(opts, fixed_d=x.iters, maxit=x.iters, tol=0.0))
+        vals.append(float((u @ host(g.X1)) @ (host(g.X2).T @ v)))
+    fdc = (vals[0] - vals[1]) / (2 * h)
+    adj = float(np.sum(host(dC1) * D))
+    print(f"256^2: <dL/dC1, D> adjoint {adj:.10e}, central difference {fdc:.10e}")
+    assert fdc == pytest.approx(adj, rel=1e-3)
