@@ -38,7 +38,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = "cd2d_512_r4"
-METRIC = "solves/s to rel. residual 1e-8 (FP64 form)"
+def metric_name(tol: float) -> str:
+    m, e = f"{tol:.0e}".split("e")
+    return f"solves/s to rel. residual {m}e{int(e)} (FP64 form)"
 SOLVER = dict(k=4, s=12000, maxit=1500, p=20, tol=1e-8, seed=0, check="adaptive",
               trunc_tol=1e-12)
 
@@ -54,7 +56,8 @@ def workload_config(P, opts, world):
 
 
 def solver_opts(args):
-    o = dict(SOLVER, s=args.s, maxit=args.maxit, p=args.p, k=args.k)
+    o = dict(SOLVER, s=args.s, maxit=args.maxit, p=args.p, k=args.k, tol=args.tol,
+             check=args.check)
     if args.fixed_d > 0:
         o.update(fixed_d=args.fixed_d, tol=0.0)
     return o
@@ -71,6 +74,8 @@ def parse():
     ap.add_argument("--s", type=int, default=SOLVER["s"])
     ap.add_argument("--p", type=int, default=SOLVER["p"])
     ap.add_argument("--k", type=int, default=SOLVER["k"])
+    ap.add_argument("--tol", type=float, default=SOLVER["tol"])
+    ap.add_argument("--check", default=SOLVER["check"], choices=["adaptive", "every_p"])
     ap.add_argument("--fixed-d", type=int, default=0,
                     help="run exactly this many iterations (small profiling cases)")
     ap.add_argument("--forms", default="fp64,mixed_fp32")
@@ -316,7 +321,7 @@ def run_reference(args, rank, world, pg):
         if step >= args.warmup:
             times.append(res["solves_per_s"])
     value = statistics.median(times)
-    line = {"impl": "reference", "metric": METRIC,
+    line = {"impl": "reference", "metric": metric_name(opts["tol"]),
             "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": workload_config(P, opts, 1),
@@ -454,7 +459,7 @@ def run_spk(args, rank, world, local, pg):
         forms_out = {f: {k: v for k, v in d.items() if k not in ("X", "prof", "clocks")}
                      for f, d in per_form.items()}
         line = {
-            "metric": METRIC,
+            "metric": metric_name(opts["tol"]),
             "value": base["solves_per_s"], "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

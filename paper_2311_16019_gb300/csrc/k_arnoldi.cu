@@ -292,8 +292,8 @@ template <typename TB>
 __global__ void __launch_bounds__(256) k_x_accumulate(double* __restrict__ X, int64_t n, int ell, int r,
                                                       WindowPtrs blocks,
                                                       const double* __restrict__ Wrows, int64_t ldw) {
-  __shared__ double Ws[kMaxWin * kMaxR][kXCols];
-  __shared__ double Us[kXRows][kMaxWin * kMaxR + 1];
+  __shared__ double Ws[kXMaxBlocks * kMaxR][kXCols];
+  __shared__ double Us[kXRows][kXMaxBlocks * kMaxR + 1];
   const int kr = blocks.nwin * r;
   const int c0 = blockIdx.y * kXCols;
   const int64_t i0 = (int64_t)blockIdx.x * kXRows;

@@ -939,7 +939,7 @@ struct Solver {
       // second sweep: U_1 from C, then U_{j+1} from the stored coefficients
       int last = 0;
       for (int j = 1; j <= d; ++j) {
-        if (j - last == sd.k || j == d) {
+        if (j - last == std::min(sd.k, kXMaxBlocks) || j == d) {
           WindowPtrs blocks{};
           blocks.nwin = j - last;
           for (int q = 0; q < blocks.nwin; ++q) blocks.blk[q] = sd.block(last + 1 + q);

@@ -16,7 +16,8 @@
 namespace spk {
 
 constexpr int kMaxR = 4;      // block width r supported by the fused kernels
-constexpr int kMaxWin = 8;    // largest truncation window k
+constexpr int kMaxWin = 16;   // largest truncation window k
+constexpr int kXMaxBlocks = 8; // blocks per factor-accumulation launch
 
 // Device-side status word bits (written by kernels, read by the host).
 enum : uint32_t {

@@ -206,6 +206,51 @@ def _wind_c3_B(x, y, z):
     return (1.0, -1.0, 0.0)
 
 
+def _central(N: int, h: float) -> sp.csr_matrix:
+    e = np.ones(N)
+    return sp.diags([-e[:-1], e[:-1]], [-1, 1], format="csr") / (2.0 * h)
+
+
+def centered_convdiff(N: int, dim: int, nu: float, wind: Callable) -> sp.csr_matrix:
+    """-nu Lap_h + w . grad_h with centred differences for both terms
+    (the operators of the paper's Examples 6.1 and 6.3): N^dim interior
+    nodes of the unit square or cube, h = 1/(N+1), Dirichlet, x fastest."""
+    h = 1.0 / (N + 1)
+    coords = _grid(N, dim)
+    w = wind(*coords)
+    A = nu * laplacian(N, dim)
+    for ax in range(dim):
+        wa = np.broadcast_to(np.asarray(w[ax], dtype=np.float64), coords[0].shape)
+        A = A + sp.diags(wa) @ _kron_axis(_central(N, h), ax, dim, N)
+    return _csr(A)
+
+
+def _wind_ex61_A(x, y):
+    return (1.0, 1.0)
+
+
+def _wind_ex61_B(x, y):
+    return (3.0 * y * (1.0 - x * x), -2.0 * x * (1.0 - y * y))
+
+
+def _wind_ex63_A(x, y, z):
+    return (x * np.sin(x), y * np.cos(y), np.exp(z * z - 1.0))
+
+
+def _wind_ex63_B(x, y, z):
+    return ((1.0 - x * x) * y * z, 1.0, np.exp(z))
+
+
+def _unit_rhs(n1, n2, r, seed):
+    """N(0,1) factors scaled so that ||C1 C2^T||_F = 1 (as in the paper's
+    examples)."""
+    C1, C2 = rhs_factors(n1, n2, r, seed)
+    _, R1 = np.linalg.qr(C1)
+    _, R2 = np.linalg.qr(C2)
+    nrm = np.linalg.norm(R1 @ R2.T)
+    return C1 / np.sqrt(nrm), C2 / np.sqrt(nrm)
+
+
 def _conv2d_problem(name, N, theta, r, seed) -> Problem:
     A, CA = convdiff_2d(N, theta, _wind_c2_A)
     B, CB = convdiff_2d(N, theta, _wind_c2_B)
@@ -222,6 +267,9 @@ def workload(name: str) -> Problem:
     cd3d_96_r2    : 3-D conv-diff 96^3 (n=884736), theta=20, r=2, seed 2
     cd2d_256_r2   : 2-D conv-diff 256x256 (n=65536), theta=10, r=2, seed 3
     small variants for fast tests: lap16_r1, cd2d_32_r2, cd2d_64_r4, cd3d_16_r2
+    ex61_<N>_nu<nu>_r<r> : Example 6.1 (centred FD, nu, w_A = (1,1),
+                           w_B = (3y(1-x^2), -2x(1-y^2))), ||C1 C2^T||_F = 1
+    ex63_<N>             : Example 6.3 (3-D centred FD, nu = 0.005), r = 1
     """
     if name.startswith("lap"):
         N = int(name[3:].split("_")[0])
@@ -234,6 +282,23 @@ def workload(name: str) -> Problem:
         r = int(name.split("_r")[1])
         seed = {512: 1, 256: 3}.get(N, 7)
         return _conv2d_problem(name, N, 10.0, r, seed)
+    if name.startswith("ex61_"):
+        # ex61_<N>_nu<nu>_r<r>: Example 6.1's 2-D operators, N^2 nodes
+        parts = name.split("_")
+        N = int(parts[1])
+        nu = float(parts[2][2:])
+        r = int(parts[3][1:])
+        A = centered_convdiff(N, 2, nu, _wind_ex61_A)
+        B = centered_convdiff(N, 2, nu, _wind_ex61_B)
+        C1, C2 = _unit_rhs(A.shape[0], B.shape[0], r, 61)
+        return Problem(name, A, B, C1, C2, meta={"N": N, "dim": 2, "nu": nu})
+    if name.startswith("ex63_"):
+        # ex63_<N>: Example 6.3's 3-D operators (nu = 0.005), N^3 nodes, r = 1
+        N = int(name.split("_")[1])
+        A = centered_convdiff(N, 3, 0.005, _wind_ex63_A)
+        B = centered_convdiff(N, 3, 0.005, _wind_ex63_B)
+        C1, C2 = _unit_rhs(A.shape[0], B.shape[0], 1, 63)
+        return Problem(name, A, B, C1, C2, meta={"N": N, "dim": 3, "nu": 0.005})
     if name.startswith("cd3d_"):
         N = int(name.split("_")[1])
         r = int(name.split("_r")[1])

@@ -289,3 +289,27 @@ def test_check_past_convergence_backtracks():
     f = spk().solve(P.A, P.BT, P.C1, P.C2, p=1, fixed_d=g.iters, **dict(opts, tol=0.0))
     assert torch.equal(g.X1, f.X1) and torch.equal(g.X2, f.X2)
     assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 1e-7
+
+
+@pytest.mark.parametrize("name,k,s,d", [("ex61_30_nu0.01_r1", 10, 400, 30),
+                                        ("ex61_24_nu0.1_r3", 12, 500, 20)])
+def test_centred_operators_wide_window_fixed_d(name, k, s, d):
+    """The paper's Example 6.1 operators (centred differences, variable wind
+    for B) with windows wider than the fused four-block pass (k = 10, 12):
+    X within 1e-10 of the oracle at a fixed d."""
+    P = I.workload(name)
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=k, s=s, maxit=d, p=1, tol=0.0, seed=5, fixed_d=d)
+    o = SP.spkms(P.A, P.BT, P.C1, P.C2, k=k, s=s, tol=0.0, maxit=d, p=d, seed=5)
+    err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
+    assert err < TOL_X, err
+    assert g.rho == pytest.approx(o["rho"], rel=1e-8)
+
+
+def test_example_6_1_small_converges_as_oracle():
+    """60 x 60 Example 6.1 operator, nu = 0.01, k = 10, s = 1600, checks every
+    20, tol 1e-6 (the paper's settings at a smaller n): the same stopping
+    iteration as the oracle (140) and the true residual at tol."""
+    P = I.workload("ex61_60_nu0.01_r1")
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=10, s=1600, maxit=700, p=20, tol=1e-6, seed=0)
+    assert g.converged and g.iters == 140, (g.iters, g.hist_d)
+    assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 1e-6
