@@ -58,6 +58,8 @@ def workload_config(P, opts, world):
 def solver_opts(args):
     o = dict(SOLVER, s=args.s, maxit=args.maxit, p=args.p, k=args.k, tol=args.tol,
              check=args.check)
+    if args.method != "sketched":
+        o["method"] = args.method
     if args.fixed_d > 0:
         o.update(fixed_d=args.fixed_d, tol=0.0)
     return o
@@ -75,6 +77,7 @@ def parse():
     ap.add_argument("--p", type=int, default=SOLVER["p"])
     ap.add_argument("--k", type=int, default=SOLVER["k"])
     ap.add_argument("--tol", type=float, default=SOLVER["tol"])
+    ap.add_argument("--method", default="sketched", choices=["sketched", "truncated", "full"])
     ap.add_argument("--check", default=SOLVER["check"], choices=["adaptive", "every_p"])
     ap.add_argument("--fixed-d", type=int, default=0,
                     help="run exactly this many iterations (small profiling cases)")

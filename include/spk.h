@@ -57,7 +57,11 @@ enum { SPK_CHECK_EVERY_P = 0, SPK_CHECK_ADAPTIVE = 1 };
  * SPK_METHOD_TRUNCATED: Algorithm 2 (t-PKSM): the same truncated Arnoldi
  * without sketch or whitening; projected equation with the banded H_d, G_d
  * and the residual bound of Proposition 3.1 (Eq. (3.3)); s is ignored.    */
-enum { SPK_METHOD_SKETCHED = 0, SPK_METHOD_TRUNCATED = 1 };
+/* SPK_METHOD_FULL: full block Arnoldi (Section 2.1) with the Galerkin
+ * projected equation and the exact residual norm; the basis of both spaces
+ * is kept ((maxit+1) r length-n vectors each, FP64 only), s is ignored.
+ * The comparator of the paper's experiments.                               */
+enum { SPK_METHOD_SKETCHED = 0, SPK_METHOD_TRUNCATED = 1, SPK_METHOD_FULL = 2 };
 /* host-side fault injection bits for spk_opts.inject (tests only) */
 enum {
     SPK_INJECT_NAN_C1 = 1u << 0,      /* treat C1 as containing a NaN          */

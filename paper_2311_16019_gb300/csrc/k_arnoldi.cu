@@ -359,7 +359,40 @@ int default_grid(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 4));
 }
 
+// Row-major n x r block <-> columns of a column-major matrix (ld ldv).
+__global__ void k_block_to_cols(const double* __restrict__ B, int64_t n, int r,
+                                double* __restrict__ V, int64_t ldv) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * r;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / r;
+    const int c = (int)(e - i * r);
+    V[i + c * ldv] = B[e];
+  }
+}
+
+__global__ void k_cols_to_block(const double* __restrict__ V, int64_t ldv, int64_t n, int r,
+                                double* __restrict__ B) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * r;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / r;
+    const int c = (int)(e - i * r);
+    B[e] = V[i + c * ldv];
+  }
+}
+
 }  // namespace
+
+void block_to_cols_launch(const double* B, int64_t n, int r, double* V, int64_t ldv,
+                          cudaStream_t st) {
+  count_launches(1);
+  k_block_to_cols<<<default_grid(n * r), 256, 0, st>>>(B, n, r, V, ldv);
+}
+
+void cols_to_block_launch(const double* V, int64_t ldv, int64_t n, int r, double* B,
+                          cudaStream_t st) {
+  count_launches(1);
+  k_cols_to_block<<<default_grid(n * r), 256, 0, st>>>(V, ldv, n, r, B);
+}
 
 template <typename TB, typename TC, typename TV>
 void spmm_dots_launch(const int32_t* rowptr, const int32_t* col, const TV* val, int64_t n, int r,

@@ -212,14 +212,16 @@ __global__ void k_border_correct(double* __restrict__ Ht, int64_t ldH, int m, in
 // Sketched method (TU, TV given), Eq. (3.5) with the whitened subdiagonal
 // blocks hhat = tau_{d+1} h_{d+1,d} tau_d^{-1} (and ghat likewise):
 //   rho = sqrt(||hhat E_d^T Y||_F^2 + ||Y E_d ghat^T||_F^2).
-// Truncated method (TU == nullptr), the bound of Proposition 3.1 (Eq. (3.3)):
-//   rho = sqrt(m) (||h E_d^T Y||_F + ||Y E_d g^T||_F),  h = h_{d+1,d}.
+// Truncated method (TU == nullptr, bound != 0), the bound of Proposition 3.1
+// (Eq. (3.3)):  rho = sqrt(m) (||h E_d^T Y||_F + ||Y E_d g^T||_F),  h = h_{d+1,d}.
+// Full Arnoldi (TU == nullptr, bound == 0), the exact residual norm of the
+// Galerkin solution:  rho = sqrt(||h E_d^T Y||_F^2 + ||Y E_d g^T||_F^2).
 // out3 = {rho, rho / ||beta1 beta2^T||_F, ||beta1 beta2^T||_F}.
 __global__ void k_rho(const double* __restrict__ Y, int64_t ldY, int m, int r,
                       const double* __restrict__ TU, int64_t ldTU, const double* __restrict__ TV,
                       int64_t ldTV, const double* __restrict__ hU, const double* __restrict__ hV,
                       const double* __restrict__ bU, const double* __restrict__ bV,
-                      double* __restrict__ out3) {
+                      int bound, double* __restrict__ out3) {
   __shared__ double hh[kMaxR * kMaxR], gh[kMaxR * kMaxR];
   __shared__ double red[2][32];
   __shared__ double nb;
@@ -279,7 +281,8 @@ __global__ void k_rho(const double* __restrict__ Y, int64_t ldY, int m, int r,
       sH += red[0][w];
       sG += red[1][w];
     }
-    const double rho = sketched ? sqrt(sH + sG) : sqrt((double)m) * (sqrt(sH) + sqrt(sG));
+    const double rho = (sketched || !bound) ? sqrt(sH + sG)
+                                            : sqrt((double)m) * (sqrt(sH) + sqrt(sG));
     out3[0] = rho;
     out3[1] = rho / nb;
     out3[2] = nb;
@@ -316,7 +319,22 @@ __global__ void k_fill_factor(double* L, int64_t ldL, int r, const double* beta)
   L[a + (int64_t)l * ldL] = beta[a * r + l];
 }
 
+// out[a*r + c] = A[row0 + a + (col0 + c)*ld]  (an r x r block, row-major)
+__global__ void k_sub_block(const double* __restrict__ A, int64_t ld, int row0, int col0, int r,
+                            double* __restrict__ out) {
+  const int e = threadIdx.x;
+  if (e >= r * r) return;
+  const int a = e / r, c = e - a * r;
+  out[e] = A[row0 + a + (int64_t)(col0 + c) * ld];
+}
+
 }  // namespace
+
+void sub_block_launch(const double* A, int64_t ld, int row0, int col0, int r, double* out,
+                      cudaStream_t st) {
+  count_launches(1);
+  k_sub_block<<<1, 32, 0, st>>>(A, ld, row0, col0, r, out);
+}
 
 int border_chunks(int mp) { return std::max(1, (mp + kBCols - 1) / kBCols); }
 
@@ -347,9 +365,10 @@ void border_correct_launch(double* Ht, int64_t ldH, int m, int r, const double* 
 
 void rho_launch(const double* Y, int64_t ldY, int m, int r, const double* TU, int64_t ldTU,
                 const double* TV, int64_t ldTV, const double* hU, const double* hV,
-                const double* betaU, const double* betaV, double* out3, cudaStream_t st) {
+                const double* betaU, const double* betaV, int bound, double* out3,
+                cudaStream_t st) {
   count_launches(1);
-  k_rho<<<1, 256, 0, st>>>(Y, ldY, m, r, TU, ldTU, TV, ldTV, hU, hV, betaU, betaV, out3);
+  k_rho<<<1, 256, 0, st>>>(Y, ldY, m, r, TU, ldTU, TV, ldTV, hU, hV, betaU, betaV, bound, out3);
 }
 
 void band_to_dense_launch(const double* hband, int k, int r, int d, double* H, int64_t ldH,

@@ -620,6 +620,8 @@ struct Side {
   double *ell = nullptr, *beta = nullptr, *R1 = nullptr, *R2 = nullptr, *Rinv = nullptr, *tau = nullptr;
   double* partial = nullptr;
   double* qpartial = nullptr;
+  double* V = nullptr;       // full method: n x (maxit+1) r column-major basis
+  double *wn = nullptr, *wn1 = nullptr;   // full method: n x r column-major work
   int grid = 1;
 
   TB* block(int j) const { return win + (size_t)(j % (k + 1)) * n * r; }
@@ -666,6 +668,19 @@ struct Solver {
     SWS(r1inv, double, "r1inv", (size_t)(o.maxit + 2) * r * r);
     SWS(r2inv, double, "r2inv", (size_t)(o.maxit + 2) * r * r);
     const bool sketched = o.method == SPK_METHOD_SKETCHED;
+    if (o.method == SPK_METHOD_FULL) {
+      // the whole basis, the Hessenberg matrix, CGS2 and Cholesky QR work
+      SWS(V, double, "V", (size_t)sd.n * mmax);
+      SWS(wn, double, "wn", (size_t)sd.n * r);
+      SWS(wn1, double, "wn1", (size_t)sd.n * r);
+      SWS(Ht, double, "Ht", (size_t)sd.ldH * sd.ldH);
+      SWS(t1, double, "t1", (size_t)mmax * r);
+      SWS(t2, double, "t2", (size_t)mmax * r);
+      SWS(qpartial, double, "qpartial",
+          std::max((size_t)q_update_chunks((int)mmax) * sd.n * r,
+                   (size_t)qt_dot_partial_doubles((int)mmax, r)));
+      CK(cudaMemsetAsync(sd.Ht, 0, sizeof(double) * sd.ldH * sd.ldH, st));
+    }
     if (sketched) {
       SWS(T, double, "T", (size_t)sd.ldT * sd.ldT);
       SWS(Ht, double, "Ht", (size_t)sd.ldH * sd.ldH);
@@ -741,9 +756,11 @@ struct Solver {
     chol_small_launch(sd.partial, sd.grid, r, sd.R2, sd.R2inv(0), h->flags, 1e-28, st);
     combine_small_launch(sd.R2, sd.R1, sd.ell, r, 0, st);
     scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(0), sd.block(1), st);
-    if (o.method == SPK_METHOD_TRUNCATED) {
-      // Algorithm 2: C = U_1 beta with beta = ell
+    if (o.method != SPK_METHOD_SKETCHED) {
+      // Algorithm 2 and full Arnoldi: C = U_1 beta with beta = ell
       CK(cudaMemcpyAsync(sd.beta, sd.ell, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+      if (o.method == SPK_METHOD_FULL)
+        block_to_cols_launch(reinterpret_cast<const double*>(sd.block(1)), sd.n, r, sd.V, sd.n, st);
       return SPK_OK;
     }
     // T_1 = R factor of S U_1 (reading of Algorithm 1's first step), beta = T_1 ell
@@ -814,6 +831,65 @@ struct Solver {
     }
   }
 
+  // Full block Arnoldi step d (Section 2.1): U~ = A U_d against all previous
+  // blocks by block CGS2 (the whitening kernels with n rows), Cholesky QR
+  // twice for U_{d+1} and h_{d+1,d}; block column d of the Hessenberg H_d.
+  void arnoldi_full(Side<TB, TC, TV>& sd, int d) {
+    const int m = d * r;
+    const int64_t n = sd.n;
+    WindowPtrs none{};
+    none.nwin = 0;
+    const double nr = (double)n * r;
+    {
+      ProfScope ps(h, F_SPMM, st, (double)sd.op->nnz * 12 + 2.0 * nr * 8, 2.0 * sd.op->nnz * r);
+      spmm_dots_launch<TB, TC, TV>(sd.op->rowptr_dev, sd.op->col_dev, sd.vals, n, r, sd.block(d),
+                                   sd.W, none, sd.partial, sd.grid, st);
+    }
+    block_to_cols_launch(reinterpret_cast<const double*>(sd.W), n, r, sd.wn, n, st);
+    const int nch = q_update_chunks(m);
+    const double nm8 = 8.0 * n * m, nr8 = 8.0 * nr;
+    {
+      ProfScope ps(h, F_QTDOT, st, nm8 + nr8, 2.0 * n * m * r);
+      qt_dot_launch(sd.V, n, n, m, sd.wn, r, sd.t1, sd.qpartial, st);
+    }
+    {
+      ProfScope ps(h, F_QUPDATE, st, nm8 + 2 * nr8, 2.0 * n * m * r);
+      q_update_launch(sd.V, n, n, m, sd.t1, r, sd.wn, sd.wn1, sd.qpartial, nch, st);
+    }
+    {
+      ProfScope ps(h, F_QTDOT, st, nm8 + nr8, 2.0 * n * m * r);
+      qt_dot_launch(sd.V, n, n, m, sd.wn1, r, sd.t2, sd.qpartial, st);
+    }
+    {
+      ProfScope ps(h, F_QUPDATE, st, nm8 + 2 * nr8, 2.0 * n * m * r);
+      q_update_launch(sd.V, n, n, m, sd.t2, r, sd.wn1, sd.wn, sd.qpartial, nch, st);
+    }
+    {
+      ProfScope ps(h, F_TSQR, st, 6 * nr8, 6.0 * nr * r);
+      tall_qr(sd.wn, n, sd.V + (int64_t)m * n, n);
+      // block column d of H_d: h_{i,d} = t1 + t2 (rows < m), h_{d+1,d} = tau
+      t_write_launch(sd.Ht - (int64_t)r * sd.ldH, sd.ldH, m, r, sd.t1, sd.t2, sd.tau, st);
+      cols_to_block_launch(sd.V + (int64_t)m * n, n, n, r,
+                           reinterpret_cast<double*>(sd.block(d + 1)), st);
+    }
+  }
+
+  // Cholesky QR twice of an n x r column-major block w (ld n): out tau = w,
+  // out written with leading dimension ldo; tau (r x r, row-major) in sd.tau
+  // of the side being processed (set by the caller through `cur`).
+  Side<TB, TC, TV>* cur = nullptr;
+  void tall_qr(double* w, int64_t n, double* out, int64_t ldo) {
+    auto& sd = *cur;
+    const int g = std::max(1, std::min<int>((int)((n + 255) / 256), h->sm_count * 2));
+    ts_gram_launch(w, n, r, sd.partial, g, st);
+    chol_small_launch(sd.partial, g, r, sd.R1, sd.Rinv, h->flags, kBreakdownFloor, st);
+    ts_scale_launch(w, n, r, sd.Rinv, w, n, st);
+    ts_gram_launch(w, n, r, sd.partial, g, st);
+    chol_small_launch(sd.partial, g, r, sd.R2, sd.Rinv, h->flags, 1e-28, st);
+    ts_scale_launch(w, n, r, sd.Rinv, out, ldo, st);
+    combine_small_launch(sd.R2, sd.R1, sd.tau, r, 0, st);
+  }
+
   // Sketch of U_{d+1}, QR update of S U_{d+1}, T column, bordering update of H~.
   void whiten_and_border(Side<TB, TC, TV>& sd, int d) {
     const int m = d * r;
@@ -873,7 +949,8 @@ struct Solver {
     WS(F, double, "pj_F", (size_t)m * m);
     WS(out3, double, "pj_out3", 4);
     const bool sketched = o.method == SPK_METHOD_SKETCHED;
-    if (sketched) {
+    const bool full = o.method == SPK_METHOD_FULL;
+    if (sketched || full) {
       copy_matrix_launch(S[0].Ht, S[0].ldH, Hk, m, m, m, st);
       copy_matrix_launch(S[1].Ht, S[1].ldH, Gk, m, m, m, st);
     } else {
@@ -897,9 +974,20 @@ struct Solver {
     TRY(sign_solve(h, m, Hk, Gk, F, o.max_newton, st, newton_iters, Lf, Rf, r, qcap));
     {
       ProfScope ps(h, F_RHO, st, 16.0 * m * r, 8.0 * m * r * r);
+      // the newest subdiagonal blocks: h_{d+1,d} (hband slot, or the Cholesky
+      // factor of the full method, read from block column d of H)
+      const double* hU = S[0].hslot(d, S[0].k);
+      const double* hV = S[1].hslot(d, S[1].k);
+      if (full) {
+        WS(hsub, double, "pj_hsub", 2 * (size_t)r * r);
+        sub_block_launch(S[0].Ht, S[0].ldH, m, m - r, r, hsub, st);
+        sub_block_launch(S[1].Ht, S[1].ldH, m, m - r, r, hsub + r * r, st);
+        hU = hsub;
+        hV = hsub + r * r;
+      }
       rho_launch(F, m, m, r, sketched ? S[0].T : nullptr, S[0].ldT, sketched ? S[1].T : nullptr,
-                 S[1].ldT, S[0].hslot(d, S[0].k), S[1].hslot(d, S[1].k), S[0].beta, S[1].beta,
-                 out3, st);
+                 S[1].ldT, hU, hV, S[0].beta, S[1].beta, o.method == SPK_METHOD_TRUNCATED, out3,
+                 st);
     }
     CK(cudaMemcpyAsync(rho3, out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     TRY(wait_stream(h, st, (o.inject & SPK_INJECT_TIMEOUT) ? 0.0 : h->host_wait_s));
@@ -935,6 +1023,12 @@ struct Solver {
         return fail(h, SPK_ERR_ALLOC, "cannot allocate factor X%d", side + 1);
       }
       if (side == 0) out->X1_dev = X; else out->X2_dev = X;
+      if (o.method == SPK_METHOD_FULL) {
+        // the basis is kept: X (n x ell, row-major) = (V_d W)^T in column-major terms
+        ProfScope ps(h, F_XACC, st, (double)sd.n * (8.0 * m + 8.0 * ell), 2.0 * sd.n * m * ell);
+        gemm_f64('T', 'T', ell, (int)sd.n, m, 1.0, Wf[side], m, sd.V, sd.n, 0.0, X, ell, st);
+        continue;
+      }
       CK(cudaMemsetAsync(X, 0, sizeof(double) * sd.n * ell, st));
       // second sweep: U_1 from C, then U_{j+1} from the stored coefficients
       int last = 0;
@@ -1025,6 +1119,11 @@ struct Solver {
     const int dmax = o.fixed_d > 0 ? std::min(o.fixed_d, o.maxit) : o.maxit;
     for (d = 1; d <= dmax; ++d) {
       for (int side = 0; side < 2; ++side) {
+        if (o.method == SPK_METHOD_FULL) {
+          cur = &S[side];
+          arnoldi_full(S[side], d);
+          continue;
+        }
         arnoldi_basis(S[side], d, false);
         if (o.method == SPK_METHOD_SKETCHED) whiten_and_border(S[side], d);
       }
@@ -1126,8 +1225,10 @@ struct Solver {
     // Y of the last check is in pj_F
     double* Y = static_cast<double*>(h->bufs["pj_F"].p);
     cudaEventRecord(er0, st);
-    TRY(replay_start(S[0], C1use));
-    TRY(replay_start(S[1], C2));
+    if (o.method != SPK_METHOD_FULL) {
+      TRY(replay_start(S[0], C1use));
+      TRY(replay_start(S[1], C2));
+    }
     TRY(recover(d, Y, out));
     cudaEventRecord(er1, st);
     TRY(wait_stream(h, st, h->host_wait_s));
@@ -1150,7 +1251,9 @@ struct Solver {
       out->hist_d_host[i] = hd[i];
       out->hist_rel_host[i] = hrel[i];
     }
-    out->mem_basis_vectors = (int64_t)(o.k_left + 1 + o.k_right + 1) * r;
+    out->mem_basis_vectors = o.method == SPK_METHOD_FULL
+                                 ? (int64_t)2 * (d + 1) * r
+                                 : (int64_t)(o.k_left + 1 + o.k_right + 1) * r;
     out->ms_project = ms_proj;
     out->ms_arnoldi = std::max(0.0, (double)ms_loop - ms_proj);
     out->ms_recover = ms_rec;
@@ -1175,9 +1278,12 @@ int validate(spk_handle* h, const spk_csr* A, const spk_csr* BT, const double* C
   if (o->same_sketch && A->nrows != BT->nrows)
     return fail(h, SPK_ERR_ARG, "same_sketch needs n1 == n2");
   const int64_t mmax = (int64_t)(o->maxit + 1) * r;
-  if (o->method != SPK_METHOD_SKETCHED && o->method != SPK_METHOD_TRUNCATED)
+  if (o->method != SPK_METHOD_SKETCHED && o->method != SPK_METHOD_TRUNCATED &&
+      o->method != SPK_METHOD_FULL)
     return fail(h, SPK_ERR_ARG, "unknown method");
-  if (o->method == SPK_METHOD_TRUNCATED) {
+  if (o->method == SPK_METHOD_FULL && o->precision != SPK_PREC_FP64)
+    return fail(h, SPK_ERR_UNSUPPORTED, "the full Arnoldi method is FP64 only");
+  if (o->method != SPK_METHOD_SKETCHED) {
     // no sketch
   } else if (o->sketch_kind == SPK_SKETCH_IDENTITY) {
     if (A->nrows < mmax || BT->nrows < mmax)

@@ -235,10 +235,19 @@ void border_correct_launch(double* Ht, int64_t ldH, int m, int r, const double* 
                            const double* h_next, cudaStream_t st);
 void rho_launch(const double* Y, int64_t ldY, int m, int r, const double* TU, int64_t ldTU,
                 const double* TV, int64_t ldTV, const double* hU, const double* hV,
-                const double* betaU, const double* betaV, double* out3, cudaStream_t st);
+                const double* betaU, const double* betaV, int bound, double* out3,
+                cudaStream_t st);
 // Dense block Hessenberg H_d (m = d r, column-major, zeroed beforehand) from
 // the stored coefficients hband ((k+1) r x r row-major slots per column).
 void band_to_dense_launch(const double* hband, int k, int r, int d, double* H, int64_t ldH,
+                          cudaStream_t st);
+// out (r x r row-major) = A[row0 .. row0+r-1, col0 .. col0+r-1] (column-major A).
+void sub_block_launch(const double* A, int64_t ld, int row0, int col0, int r, double* out,
+                      cudaStream_t st);
+// Row-major n x r FP64 block <-> r columns of a column-major matrix.
+void block_to_cols_launch(const double* B, int64_t n, int r, double* V, int64_t ldv,
+                          cudaStream_t st);
+void cols_to_block_launch(const double* V, int64_t ldv, int64_t n, int r, double* B,
                           cudaStream_t st);
 // Top r x r block of a column-major m x q factor from a row-major r x r beta.
 void fill_factor_launch(double* L, int64_t ldL, int r, const double* beta, cudaStream_t st);

@@ -30,7 +30,7 @@ SPK_ERR_UNSUPPORTED = -9
 
 SKETCH = {"srht": 0, "identity": 1}
 PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_bf16": 2}
-METHOD = {"sketched": 0, "truncated": 1}
+METHOD = {"sketched": 0, "truncated": 1, "full": 2}
 CHECK = {"every_p": 0, "adaptive": 1}
 INJECT_NAN_C1, INJECT_RANK_DEFICIENT, INJECT_TIMEOUT, INJECT_SINGULAR = 1, 2, 4, 8
 

@@ -313,3 +313,32 @@ def test_example_6_1_small_converges_as_oracle():
     g = spk().solve(P.A, P.BT, P.C1, P.C2, k=10, s=1600, maxit=700, p=20, tol=1e-6, seed=0)
     assert g.converged and g.iters == 140, (g.iters, g.hist_d)
     assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 1e-6
+
+
+@pytest.mark.parametrize("name,d", [("lap16_r1", 12), ("cd2d_24_r2", 20), ("cd2d_20_r3", 15),
+                                    ("cd2d_20_r4", 10)])
+def test_full_arnoldi_fixed_d_parity(name, d):
+    """The full block Arnoldi comparator (Section 2.1): Galerkin X and the
+    exact residual norm against the oracle's full Arnoldi at a fixed d."""
+    from oracle import arnoldi as AR
+    P = I.workload(name)
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, maxit=d, p=1, tol=0.0, fixed_d=d, method="full",
+                    trunc_tol=1e-14)
+    o = AR.galerkin(P.A, P.BT, P.C1, P.C2, d)
+    assert g.iters == d
+    err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
+    assert err < TOL_X, err
+    assert g.rho == pytest.approx(o["rho"], rel=1e-8)
+    # the residual estimate of the Galerkin solution is its true residual
+    tres = M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2))
+    assert tres == pytest.approx(g.rel_rho, rel=1e-6)
+
+
+def test_full_arnoldi_converged_same_d():
+    from oracle import arnoldi as AR
+    P = I.workload("lap32_r1")
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, maxit=200, p=1, tol=1e-8, method="full")
+    o = AR.galerkin(P.A, P.BT, P.C1, P.C2, 200, tol=1e-8, p=1)
+    assert g.converged and abs(g.iters - o["d"]) <= 1
+    assert g.mem_basis_vectors == 2 * (g.iters + 1)
+    assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 1e-8
