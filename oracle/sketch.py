@@ -1,4 +1,4 @@
-"""Subsampled randomized Hadamard sketch (Section 2.2), oracle side.
+"""Subsampled randomized trigonometric sketches (Section 2.2), oracle side.
 
 The paper builds S = sqrt(s/n) D N E: E a random +-1 diagonal, N a
 trigonometric transform (DFT, DCT or Walsh-Hadamard are all allowed), D a
@@ -13,6 +13,10 @@ printed factor sqrt(s/n) would shrink norms by s/n; the solution X does not
 depend on any scalar multiple of S -- T, beta and Y scale together -- and the
 stopping test is taken relative to ||beta_1 beta_2^T||, so only the sketched
 residual's units depend on the reading.)
+
+The DCT sketch of the paper's experiments (Section 6) is also provided
+(`dct_*`): N = the orthonormal DCT-II on the n rows themselves (no padding),
+scale sqrt(n/s), rows drawn over [0, n) from the same streams.
 
 Random draws (the paper leaves them unspecified) come from the SplitMix64
 generator of Steele, Lea and Flood (OOPSLA 2014) as published by Vigna: the
@@ -123,8 +127,49 @@ def srht_apply(X: np.ndarray, s: int, seed: int, sketch_id: int, scale: float | 
     return fwht(Z)[rows] * scale
 
 
+def dct_draws(n: int, s: int, seed: int, sketch_id: int):
+    """(rows int64[s] ascending, signs int8[n]) of the DCT sketch: the same
+    SplitMix64 streams as the SRHT, with the row keys taken over the n rows
+    themselves (no padding)."""
+    if not (1 <= s <= n):
+        raise ValueError("need 1 <= s <= n")
+    keys = splitmix64_stream(stream_state(seed, sketch_id, 0), n)
+    order = np.argsort(keys, kind="stable")
+    rows = np.sort(order[:s]).astype(np.int64)
+    sbits = splitmix64_stream(stream_state(seed, sketch_id, 1), n) >> np.uint64(63)
+    signs = (1 - 2 * sbits.astype(np.int64)).astype(np.int8)
+    return rows, signs
+
+
+def dct_dense(n: int, s: int, seed: int, sketch_id: int, scale: float | None = None) -> np.ndarray:
+    """The explicit s x n DCT sketch (the paper's choice of N in its
+    experiments, Section 6): S = scale * D N E with N the orthonormal DCT-II,
+    N[k, i] = a_k cos(pi k (2 i + 1) / (2 n)), a_0 = sqrt(1/n), a_k = sqrt(2/n);
+    scale sqrt(n/s) keeps norms in expectation (the reading of the printed
+    constant, as for the SRHT)."""
+    rows, signs = dct_draws(n, s, seed, sketch_id)
+    if scale is None:
+        scale = np.sqrt(n / s)
+    k = rows.astype(np.float64)[:, None]
+    i = np.arange(n, dtype=np.float64)[None, :]
+    a = np.where(rows == 0, np.sqrt(1.0 / n), np.sqrt(2.0 / n))[:, None]
+    return scale * a * np.cos(np.pi * k * (2.0 * i + 1.0) / (2.0 * n)) * signs[None, :]
+
+
+def dct_apply(X: np.ndarray, s: int, seed: int, sketch_id: int, scale: float | None = None) -> np.ndarray:
+    """S @ X for the DCT sketch: sign, orthonormal DCT-II (SciPy), select, scale."""
+    import scipy.fft as sfft
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    rows, signs = dct_draws(n, s, seed, sketch_id)
+    if scale is None:
+        scale = np.sqrt(n / s)
+    Z = X * (signs.reshape((n,) + (1,) * (X.ndim - 1)))
+    return sfft.dct(Z, type=2, norm="ortho", axis=0)[rows] * scale
+
+
 class Sketch:
-    """S as an operator: kind 'srht' or 'identity' (S = I_n, s = n)."""
+    """S as an operator: kind 'srht', 'dct' or 'identity' (S = I_n, s = n)."""
 
     def __init__(self, n: int, s: int, seed: int, sketch_id: int, kind: str = "srht",
                  scale: float | None = None):
@@ -136,15 +181,23 @@ class Sketch:
             self.s = s
             self.seed, self.sketch_id = seed, sketch_id
             self.scale = (1.0 / np.sqrt(s)) if scale is None else scale
+        elif kind == "dct":
+            self.s = s
+            self.seed, self.sketch_id = seed, sketch_id
+            self.scale = np.sqrt(n / s) if scale is None else scale
         else:
             raise ValueError(kind)
 
     def __call__(self, X: np.ndarray) -> np.ndarray:
         if self.kind == "identity":
             return np.array(X, dtype=np.float64) * self.scale
+        if self.kind == "dct":
+            return dct_apply(X, self.s, self.seed, self.sketch_id, self.scale)
         return srht_apply(X, self.s, self.seed, self.sketch_id, self.scale)
 
     def dense(self) -> np.ndarray:
         if self.kind == "identity":
             return np.eye(self.n) * self.scale
+        if self.kind == "dct":
+            return dct_dense(self.n, self.s, self.seed, self.sketch_id, self.scale)
         return srht_dense(self.n, self.s, self.seed, self.sketch_id, self.scale)

@@ -50,7 +50,7 @@ def test_P2_dense_bartels_stewart():
     assert M.true_residual(P.A, P.B, P.C1, P.C2, res["X1"], res["X2"]) < 5e-10
 
 
-@pytest.mark.parametrize("kind", ["identity", "full_srht"])
+@pytest.mark.parametrize("kind", ["identity", "full_srht", "full_dct"])
 @pytest.mark.parametrize("k", [1, 3])
 def test_P3_reduction_to_galerkin(kind, k):
     """With an orthogonal sketch (S = I, or the SRHT with s = n' = n) the
@@ -60,6 +60,8 @@ def test_P3_reduction_to_galerkin(kind, k):
     d = 12
     if kind == "identity":
         res = _run(P, k=k, s=256, maxit=d, sketch="identity", store_basis=True, trunc_tol=0)
+    elif kind == "full_dct":
+        res = _run(P, k=k, s=256, maxit=d, sketch="dct", store_basis=True, trunc_tol=0)
     else:
         res = _run(P, k=k, s=256, maxit=d, store_basis=True, trunc_tol=0)
     g = AR.galerkin(P.A, P.BT, P.C1, P.C2, d)

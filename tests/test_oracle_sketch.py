@@ -83,3 +83,29 @@ def test_embedding_distortion_on_krylov_basis():
     sv = np.linalg.svd(SQ, compute_uv=False)
     # squared singular values = extreme distortions over the subspace
     assert sv.max() ** 2 < 1.0 + 0.9 and sv.min() ** 2 > 1.0 - 0.9
+
+
+def test_dct_sketch_matches_its_dense_definition():
+    """dct_apply (SciPy's DCT) equals the explicit cosine formula S[j, i] =
+    sqrt(n/s) a_k cos(pi k (2i+1) / (2n)) e_i, k = rho_j."""
+    for n, s in ((60, 17), (97, 40), (128, 128)):
+        X = np.random.default_rng(n).standard_normal((n, 3))
+        got = SK.dct_apply(X, s, seed=4, sketch_id=1)
+        want = SK.dct_dense(n, s, seed=4, sketch_id=1) @ X
+        assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+
+
+def test_full_dct_sketch_is_orthogonal():
+    """With s = n every row is selected: S = N E, an orthogonal matrix."""
+    S = SK.dct_dense(90, 90, seed=2, sketch_id=0)
+    assert np.abs(S.T @ S - np.eye(90)).max() < 1e-12
+
+
+def test_dct_draws_properties():
+    rows, signs = SK.dct_draws(1000, 123, seed=7, sketch_id=3)
+    assert len(rows) == 123 and np.all(np.diff(rows) > 0)
+    assert rows.min() >= 0 and rows.max() < 1000
+    assert set(np.unique(signs)) <= {-1, 1}
+    # the same sign stream as the SRHT of the same length
+    _, s2 = SK.srht_draws(1000, 5, seed=7, sketch_id=3)
+    assert np.array_equal(signs, s2)
