@@ -60,6 +60,8 @@ def solver_opts(args):
              check=args.check)
     if args.method != "sketched":
         o["method"] = args.method
+    if args.sketch != "srht":
+        o["sketch"] = args.sketch
     if args.fixed_d > 0:
         o.update(fixed_d=args.fixed_d, tol=0.0)
     return o
@@ -78,6 +80,7 @@ def parse():
     ap.add_argument("--k", type=int, default=SOLVER["k"])
     ap.add_argument("--tol", type=float, default=SOLVER["tol"])
     ap.add_argument("--method", default="sketched", choices=["sketched", "truncated", "full"])
+    ap.add_argument("--sketch", default="srht", choices=["srht", "dct"])
     ap.add_argument("--check", default=SOLVER["check"], choices=["adaptive", "every_p"])
     ap.add_argument("--fixed-d", type=int, default=0,
                     help="run exactly this many iterations (small profiling cases)")

@@ -50,7 +50,12 @@ enum {
 };
 
 /* ---- option enums ------------------------------------------------------ */
-enum { SPK_SKETCH_SRHT = 0, SPK_SKETCH_IDENTITY = 1 };
+/* SPK_SKETCH_SRHT: subsampled randomized Walsh-Hadamard transform on n'
+ * (Section 2.2, N = Hadamard, zero padding); SPK_SKETCH_DCT: the orthonormal
+ * DCT-II on n rows as in the paper's experiments (Section 6; n must be
+ * f1 f2 with f1, f2 <= 1024 built from 2, 3, 5; s <= n);
+ * SPK_SKETCH_IDENTITY: S = I (tests).                                     */
+enum { SPK_SKETCH_SRHT = 0, SPK_SKETCH_IDENTITY = 1, SPK_SKETCH_DCT = 2 };
 enum { SPK_PREC_FP64 = 0, SPK_PREC_MIXED_FP32 = 1, SPK_PREC_MIXED_BF16 = 2 };
 enum { SPK_CHECK_EVERY_P = 0, SPK_CHECK_ADAPTIVE = 1 };
 /* SPK_METHOD_SKETCHED: Algorithm 1 (s-PKSM, whitened by the sketch).
@@ -203,6 +208,18 @@ int spk_sketch_draws(spk_handle* h, int64_t n, int32_t s, uint64_t seed,
 int spk_sketch_apply(spk_handle* h, int64_t n, int32_t s, uint64_t seed,
                      int32_t sketch_id, const double* X_dev, int32_t r,
                      double* SX_dev, void* stream);
+/* The DCT sketch of the paper's experiments (Section 6):
+ * SX = sqrt(n/s) (N E X)[rows, :], N the orthonormal DCT-II on the n rows,
+ * rows drawn over [0, n) (same SplitMix64 streams as the SRHT), signs as for
+ * the SRHT.  X_dev n x r row-major, SX_dev s x r column-major; n must be
+ * f1 f2 with f1, f2 <= 1024 built from the factors 2, 3, 5
+ * (SPK_ERR_UNSUPPORTED otherwise), 1 <= s <= n.                           */
+int spk_dct_sketch_draws(spk_handle* h, int64_t n, int32_t s, uint64_t seed,
+                         int32_t sketch_id, int32_t* rows_dev, int8_t* signs_dev,
+                         void* stream);
+int spk_dct_sketch_apply(spk_handle* h, int64_t n, int32_t s, uint64_t seed,
+                         int32_t sketch_id, const double* X_dev, int32_t r, double* SX_dev,
+                         void* stream);
 /* Y = A X for CSR A and X_dev (ncols x r row-major), Y_dev (nrows x r).   */
 int spk_spmm(spk_handle* h, const spk_csr* A, const double* X_dev, int32_t r,
              double* Y_dev, void* stream);

@@ -211,18 +211,20 @@ static size_t cand_cap(int64_t npad, int32_t s) {
   return cap;
 }
 
-size_t sketch_draws_scratch_bytes(int64_t n, int32_t s) {
-  const int64_t npad = next_pow2(n);
+size_t sketch_draws_scratch_bytes(int64_t n, int32_t s, int64_t range) {
+  const int64_t npad = range > 0 ? range : next_pow2(n);
   const size_t cap = cand_cap(npad, s);
   return 256 + cap * (sizeof(int32_t) + sizeof(uint64_t) + sizeof(int8_t)) + 3 * 256;
 }
 
 int sketch_draws_launch(int64_t n, int32_t s, uint64_t seed, int32_t sketch_id, int32_t* rows,
                         int8_t* signs, void* scratch, size_t scratch_bytes, cudaStream_t st,
-                        char* err, size_t errlen) {
-  const int64_t npad = next_pow2(n);
+                        char* err, size_t errlen, int64_t range) {
+  // rows are drawn over [0, range): the padded length n' for the SRHT, n for
+  // the DCT sketch
+  const int64_t npad = range > 0 ? range : next_pow2(n);
   if (s < 1 || s > npad) {
-    snprintf(err, errlen, "sketch rows s=%d must lie in [1, n'=%lld]", s, (long long)npad);
+    snprintf(err, errlen, "sketch rows s=%d must lie in [1, %lld]", s, (long long)npad);
     return SPK_ERR_ARG;
   }
   const uint64_t x0r = seed + (uint64_t)(1 + 2 * sketch_id + 0) * kStream;
@@ -230,7 +232,7 @@ int sketch_draws_launch(int64_t n, int32_t s, uint64_t seed, int32_t sketch_id, 
   count_launches(1);
   k_sign_draws<<<grid_for(n, 256), 256, 0, st>>>(n, x0s, signs);
   const size_t cap = cand_cap(npad, s);
-  if (scratch_bytes < sketch_draws_scratch_bytes(n, s)) {
+  if (scratch_bytes < sketch_draws_scratch_bytes(n, s, range)) {
     snprintf(err, errlen, "sketch scratch too small");
     return SPK_ERR_ARG;
   }
@@ -302,6 +304,10 @@ void sketch_apply_launch(const SketchDev& sk, const TB* X, int r, double* SX, TC
   if (sk.identity) {
     count_launches(1);
     k_identity_sketch<TB><<<grid_for(sk.n * r, 256), 256, 0, st>>>(X, sk.n, r, sk.scale, SX);
+    return;
+  }
+  if (sk.is_dct) {
+    dct_apply_launch<TB>(sk, X, r, SX, sk.cwork, st);
     return;
   }
   const size_t smem = (size_t)sk.n2 * sizeof(TC);

@@ -620,6 +620,7 @@ struct Side {
   double *ell = nullptr, *beta = nullptr, *R1 = nullptr, *R2 = nullptr, *Rinv = nullptr, *tau = nullptr;
   double* partial = nullptr;
   double* qpartial = nullptr;
+  double* cwork = nullptr;   // DCT sketch: 2 n r doubles of complex work
   double* V = nullptr;       // full method: n x (maxit+1) r column-major basis
   double *wn = nullptr, *wn1 = nullptr;   // full method: n x r column-major work
   int grid = 1;
@@ -681,10 +682,27 @@ struct Solver {
                    (size_t)qt_dot_partial_doubles((int)mmax, r)));
       CK(cudaMemsetAsync(sd.Ht, 0, sizeof(double) * sd.ldH * sd.ldH, st));
     }
+    const bool dct = sketched && o.sketch_kind == SPK_SKETCH_DCT;
     if (sketched) {
       SWS(T, double, "T", (size_t)sd.ldT * sd.ldT);
       SWS(Ht, double, "Ht", (size_t)sd.ldH * sd.ldH);
       sketch_geometry(sd.sk, sd.n, s_rows, o.sketch_kind == SPK_SKETCH_IDENTITY, (int)sizeof(TC), r);
+      if (dct) {
+        // the DCT sketch of the paper's experiments: rows over [0, n), scale sqrt(n/s)
+        sd.sk.is_dct = 1;
+        sd.sk.npad = sd.n;
+        sd.sk.scale = std::sqrt((double)sd.n / (double)s_rows);
+        if (!dct_geometry(sd.n, sd.sk.dct))
+          return fail(h, SPK_ERR_UNSUPPORTED,
+                      "DCT sketch needs n = f1 f2 with f1, f2 <= 1024 built from 2, 3, 5 (n=%lld)",
+                      (long long)sd.n);
+        SWS(cwork, double, "dct_work", 2 * (size_t)sd.n * r);
+        sd.sk.cwork = sd.cwork;
+        double* tabs = static_cast<double*>(ws_get(h, p + "dct_tables",
+                                                   sizeof(double) * dct_table_doubles(sd.n, sd.sk.dct)));
+        if (!tabs) return fail(h, SPK_ERR_ALLOC, "cannot allocate DCT tables");
+        dct_tables_launch(sd.n, sd.sk.dct, tabs, st);
+      }
     } else {
       sketch_geometry(sd.sk, sd.n, 1, 1, (int)sizeof(TC), r);
     }
@@ -715,14 +733,22 @@ struct Solver {
     if (sketched && !sd.sk.identity) {
       int32_t* rows = static_cast<int32_t*>(ws_get(h, p + "rows", sizeof(int32_t) * s));
       int8_t* signs = static_cast<int8_t*>(ws_get(h, p + "signs", (size_t)sd.n));
-      const size_t sb = sketch_draws_scratch_bytes(sd.n, s);
+      const int64_t range = dct ? sd.n : 0;
+      const size_t sb = sketch_draws_scratch_bytes(sd.n, s, range);
       void* scratch = ws_get(h, "sk_draw_scratch", sb);
       if (!rows || !signs || !scratch) return fail(h, SPK_ERR_ALLOC, "cannot allocate sketch draws");
       char e[256] = {0};
-      int rc = sketch_draws_launch(sd.n, (int32_t)s, o.seed, sketch_id, rows, signs, scratch, sb, st, e, sizeof e);
+      int rc = sketch_draws_launch(sd.n, (int32_t)s, o.seed, sketch_id, rows, signs, scratch, sb, st,
+                                   e, sizeof e, range);
       if (rc != SPK_OK) return fail(h, rc, "%s", e);
       sd.sk.rows = rows;
       sd.sk.signs = signs;
+      if (dct) {
+        int32_t* selpos = static_cast<int32_t*>(ws_get(h, p + "selpos", sizeof(int32_t) * (size_t)sd.n));
+        if (!selpos) return fail(h, SPK_ERR_ALLOC, "cannot allocate DCT row positions");
+        dct_selpos_launch(rows, (int32_t)s, sd.n, selpos, st);
+        sd.sk.selpos = selpos;
+      }
     }
     if (sketched) {
       CK(cudaMemsetAsync(sd.T, 0, sizeof(double) * sd.ldT * sd.ldT, st));
@@ -1288,9 +1314,11 @@ int validate(spk_handle* h, const spk_csr* A, const spk_csr* BT, const double* C
   } else if (o->sketch_kind == SPK_SKETCH_IDENTITY) {
     if (A->nrows < mmax || BT->nrows < mmax)
       return fail(h, SPK_ERR_ARG, "identity sketch needs n >= (maxit+1) r");
-  } else if (o->sketch_kind == SPK_SKETCH_SRHT) {
+  } else if (o->sketch_kind == SPK_SKETCH_SRHT || o->sketch_kind == SPK_SKETCH_DCT) {
     if (o->s < mmax)
       return fail(h, SPK_ERR_ARG, "sketch rows s=%d must be >= (maxit+1) r = %lld", o->s, (long long)mmax);
+    if (o->sketch_kind == SPK_SKETCH_DCT && (o->s > A->nrows || o->s > BT->nrows))
+      return fail(h, SPK_ERR_ARG, "DCT sketch rows s=%d must be <= n", o->s);
   } else {
     return fail(h, SPK_ERR_ARG, "unknown sketch kind");
   }
@@ -1581,6 +1609,54 @@ int spk_sketch_apply(spk_handle* h, int64_t n, int32_t s, uint64_t seed, int32_t
   sk.rows = rows;
   sk.signs = signs;
   sketch_apply_launch<double, double>(sk, X, r, SX, scratch, st);
+  TRY(wait_stream(h, st, h->host_wait_s));
+  CK(cudaGetLastError());
+  return SPK_OK;
+}
+
+int spk_dct_sketch_draws(spk_handle* h, int64_t n, int32_t s, uint64_t seed, int32_t sketch_id,
+                         int32_t* rows, int8_t* signs, void* stream) {
+  if (!h || !rows || !signs || n < 1) return SPK_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t sb = sketch_draws_scratch_bytes(n, s, n);
+  void* scratch = ws_get(h, "sk_draw_scratch", sb);
+  if (!scratch) return fail(h, SPK_ERR_ALLOC, "cannot allocate sketch scratch");
+  char e[256] = {0};
+  int rc = sketch_draws_launch(n, s, seed, sketch_id, rows, signs, scratch, sb, st, e, sizeof e, n);
+  if (rc != SPK_OK) return fail(h, rc, "%s", e);
+  return wait_stream(h, st, h->host_wait_s);
+}
+
+int spk_dct_sketch_apply(spk_handle* h, int64_t n, int32_t s, uint64_t seed, int32_t sketch_id,
+                         const double* X, int32_t r, double* SX, void* stream) {
+  if (!h || !X || !SX || n < 1 || r < 1 || r > kMaxR || s < 1 || s > n) return SPK_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SketchDev sk;
+  sk.n = n;
+  sk.npad = n;
+  sk.s = s;
+  sk.is_dct = 1;
+  sk.scale = std::sqrt((double)n / (double)s);
+  if (!dct_geometry(n, sk.dct))
+    return fail(h, SPK_ERR_UNSUPPORTED, "DCT sketch: n=%lld is not f1 f2 with f1, f2 <= 1024 "
+                "built from 2, 3, 5", (long long)n);
+  int32_t* rows = static_cast<int32_t*>(ws_get(h, "sa_rows", sizeof(int32_t) * s));
+  int8_t* signs = static_cast<int8_t*>(ws_get(h, "sa_signs", (size_t)n));
+  int32_t* selpos = static_cast<int32_t*>(ws_get(h, "sa_selpos", sizeof(int32_t) * (size_t)n));
+  double* cwork = static_cast<double*>(ws_get(h, "sa_dct_work", sizeof(double) * 2 * (size_t)n * r));
+  double* tabs = static_cast<double*>(ws_get(h, "sa_dct_tables",
+                                             sizeof(double) * dct_table_doubles(n, sk.dct)));
+  if (!rows || !signs || !selpos || !cwork || !tabs)
+    return fail(h, SPK_ERR_ALLOC, "cannot allocate sketch buffers");
+  int rc = spk_dct_sketch_draws(h, n, s, seed, sketch_id, rows, signs, stream);
+  if (rc != SPK_OK) return rc;
+  dct_tables_launch(n, sk.dct, tabs, st);
+  dct_selpos_launch(rows, s, n, selpos, st);
+  sk.rows = rows;
+  sk.signs = signs;
+  sk.selpos = selpos;
+  sk.cwork = cwork;
+  dct_apply_launch<double>(sk, X, r, SX, cwork, st);
   TRY(wait_stream(h, st, h->host_wait_s));
   CK(cudaGetLastError());
   return SPK_OK;

@@ -148,6 +148,23 @@ __device__ __forceinline__ void block_sum_store(double (&acc)[NV], double* out) 
 }
 
 // ---------------------------------------------------------------- sketch
+// Mixed-radix plan of one DCT sub-transform length (radices 4, 2, 3, 5).
+constexpr int kFftMax = 1024;
+constexpr int kFftMaxStages = 10;
+struct FftPlan {
+  int32_t len = 1;
+  int32_t nst = 0;
+  int8_t radix[kFftMaxStages] = {};
+};
+// DCT sketch geometry: n = p1.len * p2.len and device twiddle tables.
+struct DctDev {
+  FftPlan p1, p2;
+  const double2* tw1 = nullptr;   // exp(-2 pi i t / f1)
+  const double2* tw2 = nullptr;   // exp(-2 pi i t / f2)
+  const double2* twn = nullptr;   // exp(-2 pi i t / n)
+  const double2* post = nullptr;  // exp(-i pi k / (2 n))
+};
+
 struct SketchDev {
   int64_t n = 0;        // rows of the sketched blocks
   int64_t npad = 0;     // n' = 2^ceil(log2 n)
@@ -159,13 +176,31 @@ struct SketchDev {
   double scale = 1.0;   // 1/sqrt(s) (SRHT) or 1 (identity)
   int32_t* rows = nullptr;   // s selected rows, ascending
   int8_t* signs = nullptr;   // n Rademacher signs
+  // DCT sketch (is_dct): rows drawn over [0, n), selpos[k] = position of row
+  // k in rows or -1, cwork = 2 n r doubles of complex work
+  int32_t is_dct = 0;
+  DctDev dct;
+  int32_t* selpos = nullptr;
+  double* cwork = nullptr;
 };
 
 // Launchers (k_sketch.cu)
+// DCT sketch: geometry (false if n is not a product of two lengths <= 1024
+// built from the radices 2, 3, 5), twiddle tables (dct_table_doubles
+// doubles, kept alive by the caller), row positions, and the application.
+bool dct_geometry(int64_t n, DctDev& dd);
+size_t dct_table_doubles(int64_t n, const DctDev& dd);
+void dct_tables_launch(int64_t n, DctDev& dd, double* tables, cudaStream_t st);
+void dct_selpos_launch(const int32_t* rows, int32_t s, int64_t n, int32_t* selpos, cudaStream_t st);
+template <typename TB>
+void dct_apply_launch(const SketchDev& sk, const TB* X, int r, double* SX, double* cwork,
+                      cudaStream_t st);
+
 int sketch_draws_launch(int64_t n, int32_t s, uint64_t seed, int32_t sketch_id,
                         int32_t* rows, int8_t* signs, void* scratch, size_t scratch_bytes,
-                        cudaStream_t st, char* err, size_t errlen);
-size_t sketch_draws_scratch_bytes(int64_t n, int32_t s);
+                        cudaStream_t st, char* err, size_t errlen,
+                        int64_t range = 0);
+size_t sketch_draws_scratch_bytes(int64_t n, int32_t s, int64_t range = 0);
 void sketch_geometry(SketchDev& sk, int64_t n, int32_t s, int identity, int elem_bytes, int r);
 size_t sketch_apply_scratch_bytes(const SketchDev& sk, int r);
 // SX (s x r column-major, FP64) = S X, X row-major n x r of type TB.

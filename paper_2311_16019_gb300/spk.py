@@ -28,7 +28,7 @@ SPK_ERR_NOT_CONVERGED = -7
 SPK_ERR_TIMEOUT = -8
 SPK_ERR_UNSUPPORTED = -9
 
-SKETCH = {"srht": 0, "identity": 1}
+SKETCH = {"srht": 0, "identity": 1, "dct": 2}
 PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_bf16": 2}
 METHOD = {"sketched": 0, "truncated": 1, "full": 2}
 CHECK = {"every_p": 0, "adaptive": 1}
@@ -101,6 +101,8 @@ def load() -> C.CDLL:
         "spk_profile_read": (i32, [vp, C.c_int, P(C.c_char_p), P(dbl), P(i64), P(i64), P(dbl), P(dbl)]),
         "spk_fp64_peak": (i32, [vp, P(dbl), vp]),
         "spk_solve_batched": (i32, [vp, i32, P(Problem), i32, vp, P(Result)]),
+        "spk_dct_sketch_draws": (i32, [vp, i64, i32, u64, i32, vp, vp, vp]),
+        "spk_dct_sketch_apply": (i32, [vp, i64, i32, u64, i32, vp, i32, vp, vp]),
         "spk_sketch_apply_static": (i32, [i64, i32, u64, i32, vp, i32, vp, vp, C.c_char_p,
                                           C.c_size_t]),
     }
@@ -396,6 +398,31 @@ def sketch_apply(X, s: int, seed: int, sketch_id: int, device: int = 0):
     SX = torch.empty((r, s), dtype=torch.float64, device="cuda")  # column-major s x r
     rc = h.lib.spk_sketch_apply(h.h, n, s, seed, sketch_id, C.c_void_p(x.data_ptr()), r,
                                 C.c_void_p(SX.data_ptr()), _stream_ptr())
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+    return SX.t()
+
+
+def dct_sketch_draws(n: int, s: int, seed: int, sketch_id: int, device: int = 0):
+    torch = _torch()
+    h = handle(device)
+    rows = torch.empty(s, dtype=torch.int32, device="cuda")
+    signs = torch.empty(n, dtype=torch.int8, device="cuda")
+    rc = h.lib.spk_dct_sketch_draws(h.h, n, s, seed, sketch_id, C.c_void_p(rows.data_ptr()),
+                                    C.c_void_p(signs.data_ptr()), _stream_ptr())
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+    return rows, signs
+
+
+def dct_sketch_apply(X, s: int, seed: int, sketch_id: int, device: int = 0):
+    torch = _torch()
+    h = handle(device)
+    x = _block(X)
+    n, r = x.shape
+    SX = torch.empty((r, s), dtype=torch.float64, device="cuda")  # column-major s x r
+    rc = h.lib.spk_dct_sketch_apply(h.h, n, s, seed, sketch_id, C.c_void_p(x.data_ptr()), r,
+                                    C.c_void_p(SX.data_ptr()), _stream_ptr())
     if rc != SPK_OK:
         raise SpkError(rc, h.error())
     return SX.t()

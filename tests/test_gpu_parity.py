@@ -342,3 +342,34 @@ def test_full_arnoldi_converged_same_d():
     assert g.converged and abs(g.iters - o["d"]) <= 1
     assert g.mem_basis_vectors == 2 * (g.iters + 1)
     assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 1e-8
+
+
+@pytest.mark.parametrize("n,s,seed,sid", [(24, 7, 0, 0), (90, 90, 3, 1), (1000, 123, 5, 0),
+                                          (3600, 1600, 2, 1), (90000, 1600, 7, 0)])
+def test_dct_sketch_draws_bit_exact(n, s, seed, sid):
+    rows, signs = spk().dct_sketch_draws(n, s, seed, sid)
+    orows, osigns = SK.dct_draws(n, s, seed, sid)
+    assert np.array_equal(host(rows).astype(np.int64), orows)
+    assert np.array_equal(host(signs).astype(np.int8), osigns)
+
+
+@pytest.mark.parametrize("n,r,s", [(24, 1, 10), (60, 3, 60), (1000, 4, 200), (3600, 2, 1600),
+                                   (90000, 3, 1600), (884736, 2, 3200)])
+def test_dct_sketch_apply_against_oracle(n, r, s):
+    """The GPU DCT sketch (Makhoul reordering, four-step mixed-radix FFT)
+    against the oracle's SciPy DCT, FP64."""
+    X = np.random.default_rng(n + r).standard_normal((n, r))
+    got = host(spk().dct_sketch_apply(X, s, seed=3, sketch_id=1))
+    want = SK.dct_apply(X, s, seed=3, sketch_id=1)
+    assert np.linalg.norm(got - want) <= 1e-13 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("name,k,s,d", [("cd2d_24_r2", 3, 300, 20), ("ex61_30_nu0.01_r1", 10, 600, 25)])
+def test_dct_sketch_fixed_d_parity(name, k, s, d):
+    P = I.workload(name)
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=k, s=s, maxit=d, p=1, tol=0.0, seed=7,
+                    sketch="dct", fixed_d=d)
+    o = SP.spkms(P.A, P.BT, P.C1, P.C2, k=k, s=s, tol=0.0, maxit=d, p=d, seed=7, sketch="dct")
+    err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
+    assert err < TOL_X, err
+    assert g.rho == pytest.approx(o["rho"], rel=1e-8)
