@@ -244,7 +244,8 @@ int spk_sylvester_dense(spk_handle* h, int32_t m, const double* H_dev,
  * current) looks up the array's device address; make it before any stream
  * capture.  All calls on a device share the array and leave their data in
  * it; calls whose device work overlaps race and must be ordered by the
- * caller.  Synchronises `stream` before returning.                       */
+ * caller.  Waits for `stream` before returning (SPK_ERR_TIMEOUT after
+ * 600 s).                                                                 */
 int spk_sketch_apply_static(int64_t n, int32_t s, uint64_t seed, int32_t sketch_id,
                             const double* X_dev, int32_t r, double* SX_dev, void* stream,
                             char* err, size_t errlen);

@@ -742,11 +742,12 @@ double fp64_fma_probe(int sm_count, double* scratch, cudaStream_t st) {
   count_launches(1);
   k_fp64_fma<<<blocks, 256, 0, st>>>(scratch, iters, 0.999999, 1e-7);
   cudaEventRecord(b, st);
-  cudaEventSynchronize(b);
+  const int w = bounded_event_wait(b, kHostWaitSeconds);
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, a, b);
+  if (w == 0) cudaEventElapsedTime(&ms, a, b);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  if (w != 0 || !(ms > 0.f)) return 0.0;
   const double flops = 2.0 * 8.0 * iters * (double)blocks * 256.0;
   return flops / (ms * 1e-3) / 1e12;
 }

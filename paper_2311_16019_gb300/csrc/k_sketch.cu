@@ -253,7 +253,12 @@ int sketch_draws_launch(int64_t n, int32_t s, uint64_t seed, int32_t sketch_id, 
     int32_t hcnt = 0;
     if (cudaMemcpyAsync(&hcnt, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
       return SPK_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return SPK_ERR_CUDA;
+    const int w = bounded_stream_wait(st, kHostWaitSeconds);
+    if (w == 1) {
+      snprintf(err, errlen, "sketch row selection: device work did not finish");
+      return SPK_ERR_TIMEOUT;
+    }
+    if (w != 0) return SPK_ERR_CUDA;
     if (hcnt < s) { frac = frac * 1.5 + 1e-12; continue; }
     if ((size_t)hcnt > cap) { frac = frac * 0.8; continue; }
     const int g = grid_for(hcnt, 256);

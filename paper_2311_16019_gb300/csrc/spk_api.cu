@@ -32,6 +32,31 @@ namespace spk {
 static std::atomic<int64_t> g_launches{0};
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+template <typename Q>
+int bounded_poll(Q query, double budget_s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = query();
+    if (e == cudaSuccess) return 0;
+    if (e != cudaErrorNotReady) return 2;
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el >= budget_s) return 1;
+    if (el > 1e-3) {
+      struct timespec ts{0, 50000};
+      nanosleep(&ts, nullptr);
+    }
+  }
+}
+}  // namespace
+
+int bounded_stream_wait(cudaStream_t st, double budget_s) {
+  return bounded_poll([st]() { return cudaStreamQuery(st); }, budget_s);
+}
+int bounded_event_wait(cudaEvent_t ev, double budget_s) {
+  return bounded_poll([ev]() { return cudaEventQuery(ev); }, budget_s);
+}
 }  // namespace spk
 
 struct Buf {
@@ -73,7 +98,7 @@ struct Profiler {
   }
   void resolve() {
     for (auto& p : pend) {
-      cudaEventSynchronize(p.b);
+      bounded_event_wait(p.b, kHostWaitSeconds);
       float ms = 0.f;
       cudaEventElapsedTime(&ms, p.a, p.b);
       auto& a = acc[p.f];
@@ -1741,7 +1766,8 @@ int spk_inspect(spk_handle* h, const char* name, double* dst, int64_t count, int
   const int64_t n = (int64_t)(it->second.bytes / sizeof(double));
   if (avail) *avail = n;
   if (dst && count > 0) {
-    CK(cudaDeviceSynchronize());
+    if (bounded_stream_wait(0, h->host_wait_s) != 0)
+      return fail(h, SPK_ERR_TIMEOUT, "inspect: device work did not finish");
     CK(cudaMemcpy(dst, it->second.p, sizeof(double) * std::min(n, count), cudaMemcpyDeviceToHost));
   }
   return SPK_OK;

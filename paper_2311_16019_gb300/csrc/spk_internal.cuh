@@ -29,6 +29,11 @@ enum : uint32_t {
 // Number of kernel launches issued by the library since it was loaded.
 void count_launches(int64_t n);
 int64_t launch_count();
+// Bounded host waits: poll until the stream (event) completes, an error
+// appears, or budget_s seconds pass.  0 = done, 1 = timed out, 2 = error.
+int bounded_stream_wait(cudaStream_t st, double budget_s);
+int bounded_event_wait(cudaEvent_t ev, double budget_s);
+constexpr double kHostWaitSeconds = 600.0;
 
 // ---------------------------------------------------------------- storage
 template <typename T> struct Store;

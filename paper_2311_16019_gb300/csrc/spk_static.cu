@@ -125,7 +125,12 @@ extern "C" int spk_sketch_apply_static(int64_t n, int32_t s, uint64_t seed, int3
   sk.rows = rows;
   sk.signs = signs;
   spk::sketch_apply_launch<double, double>(sk, X_dev, r, SX_dev, transform, st);
-  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+  const int w = spk::bounded_stream_wait(st, spk::kHostWaitSeconds);
+  if (w == 1) {
+    set_err(err, errlen, "spk_sketch_apply_static: device work did not finish");
+    return SPK_ERR_TIMEOUT;
+  }
+  if (w != 0 || cudaGetLastError() != cudaSuccess) {
     set_err(err, errlen, "spk_sketch_apply_static: kernel failed");
     return SPK_ERR_CUDA;
   }
