@@ -93,7 +93,8 @@ def parse():
     ap.add_argument("--m", type=int, default=4200, help="size of the dense case")
     ap.add_argument("--batched", action="store_true",
                     help="time the batched form on the 64-instance workload instead")
-    ap.add_argument("--concurrency", type=int, default=8, help="batched-form workers")
+    ap.add_argument("--concurrency", type=int, default=0,
+                    help="batched-form workers (0: chosen by the autotuner)")
     return ap.parse_args()
 
 
@@ -542,6 +543,11 @@ def run_batched(args):
         o.C1 = torch.as_tensor(P.C1, device="cuda")
         o.C2 = torch.as_tensor(P.C2, device="cuda")
         insts.append(o)
+    conc = args.concurrency
+    if conc <= 0:
+        # worker count by measurement on a short probe of the same batch
+        conc = spk.autotune_concurrency(insts, opts_list=opts)
+    args.concurrency = conc
     for _ in range(args.warmup):
         spk.solve_batched(insts, concurrency=args.concurrency, opts_list=opts, raise_on_error=False)
     torch.cuda.synchronize()

@@ -362,6 +362,32 @@ def solve_batched(problems, *, concurrency: int = 8, device: int = 0, stream=Non
     return rc, results
 
 
+def autotune_concurrency(problems, *, candidates=(2, 4, 8, 16), probe_iters: int = 40,
+                         device: int = 0, opts_list=None, **opts) -> int:
+    """Pick the batched form's worker count by measurement: every candidate
+    runs the whole batch for a fixed, short number of iterations (one check
+    at the end) and the fastest is returned.  The probe shortens only the
+    iteration count; instance sizes, ranks and options stay as given."""
+    import time
+    torch = _torch()
+    base = opts_list if opts_list is not None else [opts] * len(problems)
+    probe = []
+    for o in base:
+        d = max(1, min(probe_iters, o.get("maxit", 300)))
+        probe.append(dict(o, fixed_d=d, maxit=d, tol=0.0))
+    best, best_t = candidates[0], float("inf")
+    for c in candidates:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solve_batched(problems, concurrency=c, device=device, opts_list=probe,
+                      raise_on_error=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        if t < best_t:
+            best, best_t = c, t
+    return best
+
+
 def result_view(sol: "SolveResult") -> Result:
     """A Result struct whose factor pointers view sol.X1, sol.X2 (tensors the
     caller keeps alive), for spk_adjoint_gradients."""

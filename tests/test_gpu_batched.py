@@ -81,3 +81,17 @@ def test_projected_spectrum_off_right_half_plane_is_reported():
                   fixed_d=12)
     assert e.value.code == spk.SPK_ERR_SINGULAR_PROJECTED
     assert "right half plane" in str(e.value)
+
+
+def test_autotuned_concurrency_is_a_candidate_and_results_do_not_depend_on_it():
+    from paper_2311_16019_gb300 import spk
+    probs = I.batched_instances(count=6, seed=12, nmin=12, nmax=30)
+    opts = [_opts(P, maxit=60) for P in probs]
+    c = spk.autotune_concurrency(probs, candidates=(1, 3, 6), probe_iters=10, opts_list=opts)
+    assert c in (1, 3, 6)
+    _, a = spk.solve_batched(probs, concurrency=c, opts_list=opts, raise_on_error=False)
+    _, b = spk.solve_batched(probs, concurrency=1, opts_list=opts, raise_on_error=False)
+    for x, y in zip(a, b):
+        assert x.status == y.status and x.iters == y.iters
+        if x.X1 is not None:
+            assert torch.equal(x.X1, y.X1) and torch.equal(x.X2, y.X2)

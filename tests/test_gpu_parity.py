@@ -373,3 +373,30 @@ def test_dct_sketch_fixed_d_parity(name, k, s, d):
     err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
     assert err < TOL_X, err
     assert g.rho == pytest.approx(o["rho"], rel=1e-8)
+
+
+def test_rectangular_sylvester_n1_ne_n2():
+    """A and B of different orders (n1 = 400, n2 = 576): X is n1 x n2."""
+    PA = I.workload("cd2d_20_r2")
+    PB = I.workload("cd2d_24_r2")
+    A, BT = PA.A, PB.BT
+    C1, C2 = PA.C1, PB.C2
+    g = spk().solve(A, BT, C1, C2, k=3, s=300, maxit=20, p=1, tol=0.0, seed=2, fixed_d=20)
+    o = SP.spkms(A, BT, C1, C2, k=3, s=300, tol=0.0, maxit=20, p=20, seed=2)
+    assert g.X1.shape[0] == 400 and g.X2.shape[0] == 576
+    err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
+    assert err < TOL_X, err
+
+
+def test_full_srht_equals_full_arnoldi_on_gpu():
+    """With s = n' = n the SRHT is orthogonal and the sketched-and-truncated
+    solution is the Galerkin solution of full Arnoldi for any k (the
+    reduction pinned on the oracle side), here on the GPU pipeline against
+    the oracle's full Arnoldi directly."""
+    P = I.workload("cd2d_16_r2")          # n = 256 = n'
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=2, s=256, maxit=12, p=1, tol=0.0, fixed_d=12,
+                    trunc_tol=1e-14)
+    o = AR.galerkin(P.A, P.BT, P.C1, P.C2, 12)
+    err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
+    assert err < 1e-9, err
+    assert g.rho == pytest.approx(o["rho"], rel=1e-7)
