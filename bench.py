@@ -178,14 +178,17 @@ def fp64_alu_peak(sm_count: int):
     return sm_count * 4 * mhz * 1e6 / 1e12, mhz
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend: str = "nccl"):
+    """One process per GPU (torchrun environment); replicas of the solve,
+    no data-path collective.  The backend is NCCL on GPUs (gloo in the CPU
+    tests of this helper)."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     pg = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend)
         pg = dist
     return rank, world, local, pg
 
@@ -199,9 +202,16 @@ def max_over_ranks(pg, value: float) -> float:
     if pg is None:
         return value
     import torch
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cpu" if pg.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(world: int, steps: int, ms_max: float) -> float:
+    """Whole-job solves/s of `world` replicas, each timing `steps` solves,
+    over the slowest rank's time."""
+    return world * steps / (ms_max * 1e-3)
 
 
 def pick_roofline(prof: dict, hbm_gbs: float, fp64_tflops: float):
@@ -399,7 +409,7 @@ def run_spk(args, rank, world, local, pg):
         X1, X2 = g.X1.cpu().numpy(), g.X2.cpu().numpy()
         tres = true_residual(P.A, P.B, P.C1, P.C2, X1, X2)
         per_form[form] = dict(ms_per_step=ms_max / args.steps,
-                              solves_per_s=world * args.steps / (ms_max * 1e-3),
+                              solves_per_s=replica_throughput(world, args.steps, ms_max),
                               iters=g.iters, rank=g.rank, converged=g.converged,
                               rel_rho=g.rel_rho, true_rel_residual=tres, checks=g.hist_d,
                               ms_phases=dict(arnoldi=g.ms_arnoldi, project=g.ms_project,
