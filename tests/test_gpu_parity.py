@@ -400,3 +400,37 @@ def test_full_srht_equals_full_arnoldi_on_gpu():
     err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
     assert err < 1e-9, err
     assert g.rho == pytest.approx(o["rho"], rel=1e-7)
+
+
+def _bench_solver():
+    import importlib.util, os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_cfg", os.path.join(root, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return dict(mod.SOLVER)
+
+
+def test_bench_workload_full_size_properties():
+    """The timed workload at full size (512^2, r = 4, bench.py's settings):
+    too large for the oracle, so the checks are properties that hold at any
+    size -- converged, true relative residual at tol (in factored form),
+    factors finite, and the checks' history decreasing to the stop."""
+    P = I.workload("cd2d_512_r4")
+    o = _bench_solver()
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, **o)
+    assert g.converged and g.status == 0
+    X1, X2 = host(g.X1), host(g.X2)
+    assert np.all(np.isfinite(X1)) and np.all(np.isfinite(X2))
+    res = M.true_residual(P.A, P.B, P.C1, P.C2, X1, X2)
+    assert res < 2 * o["tol"], res
+    assert g.hist_rel[-1] < o["tol"] and g.hist_rel[-1] < g.hist_rel[0]
+
+
+def test_three_d_workload_full_size_properties():
+    """96^3, r = 2, k = 3, s = 3200: converged in FP64, true residual at tol."""
+    P = I.workload("cd3d_96_r2")
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=3, s=3200, maxit=800, p=20, tol=1e-8, seed=0,
+                    check="adaptive")
+    assert g.converged
+    assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 2e-8
