@@ -574,6 +574,88 @@ __global__ void k_col_abs_sums(const double* __restrict__ A, int64_t lda, int M,
   if (lane == 0) out[warp] = s;
 }
 
+// ---- Power iteration: spectral-radius estimates for the Newton scaling
+// y = M x for up to four m x m matrices at once, split over CTAs of kPwRows
+// rows and kPwChunk columns; the chunks' partial sums are added in a fixed
+// order by k_power_finish, so the estimates are reproducible.
+constexpr int kPwRows = 128;
+constexpr int kPwChunk = 256;
+
+struct PowerMats {
+  const double* M[4];
+};
+
+// Start vector: positive entries in [0.5, 1.5) from a multiplicative hash of
+// the index (not aligned with any coordinate direction).
+__device__ __forceinline__ double power_start(int j) {
+  return 0.5 + (double)(((uint32_t)(j + 1) * 2654435761u) >> 22) * (1.0 / 1024.0);
+}
+
+// part[(chunk * 4 + mat) * m + i] = sum over the chunk's columns j of
+// M[i, j] x[j], with x = y / ||y|| (||y||^2 = the sum of nrm_part's tiles),
+// or x = the start vector / sqrt(m) at the first step.
+__global__ void __launch_bounds__(kPwRows) k_power_gemv(PowerMats pm, int m, int64_t ld,
+                                                        const double* __restrict__ y,
+                                                        const double* __restrict__ nrm_part,
+                                                        int tiles, int first,
+                                                        double* __restrict__ part) {
+  const int mat = blockIdx.z;
+  const int j0 = blockIdx.y * kPwChunk;
+  const int j1 = min(m, j0 + kPwChunk);
+  __shared__ double xs[kPwChunk];
+  __shared__ double scale;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    if (!first)
+      for (int t = 0; t < tiles; ++t) s += nrm_part[mat * tiles + t];
+    scale = first ? rsqrt((double)m) : (s > 0.0 ? 1.0 / sqrt(s) : 0.0);
+  }
+  for (int j = j0 + threadIdx.x; j < j1; j += kPwRows)
+    xs[j - j0] = first ? power_start(j) : y[(int64_t)mat * m + j];
+  __syncthreads();
+  const int i = blockIdx.x * kPwRows + threadIdx.x;
+  if (i >= m) return;
+  const double* __restrict__ a = pm.M[mat] + i;
+  double acc = 0.0;
+#pragma unroll 8
+  for (int j = j0; j < j1; ++j) acc = fma(a[(int64_t)j * ld], xs[j - j0], acc);
+  part[((int64_t)blockIdx.y * 4 + mat) * m + i] = acc * scale;
+}
+
+// y[mat * m + i] = the sum of the chunks' partials (fixed order);
+// nrm_part[mat * tiles + tile] = the sum of y^2 over the tile's rows.
+__global__ void __launch_bounds__(kPwRows) k_power_finish(const double* __restrict__ part, int m,
+                                                          int chunks, double* __restrict__ y,
+                                                          double* __restrict__ nrm_part,
+                                                          int tiles) {
+  const int mat = blockIdx.y;
+  const int i = blockIdx.x * kPwRows + threadIdx.x;
+  double v = 0.0;
+  if (i < m) {
+    for (int c = 0; c < chunks; ++c) v += part[((int64_t)c * 4 + mat) * m + i];
+    y[(int64_t)mat * m + i] = v;
+  }
+  __shared__ double ws[kPwRows / 32];
+  const double w = warp_sum(v * v);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < kPwRows / 32; ++q) s += ws[q];
+    nrm_part[mat * tiles + blockIdx.x] = s;
+  }
+}
+
+// out[mat] = ||y_mat|| (the tiles summed in order).
+__global__ void k_power_norms(const double* __restrict__ nrm_part, int tiles, int nmat,
+                              double* __restrict__ out) {
+  const int mat = threadIdx.x;
+  if (mat >= nmat) return;
+  double s = 0.0;
+  for (int t = 0; t < tiles; ++t) s += nrm_part[mat * tiles + t];
+  out[mat] = sqrt(s);
+}
+
 // FP64 FMA throughput probe: 8 independent dependency chains per thread.
 __global__ void __launch_bounds__(256) k_fp64_fma(double* out, int iters, double b, double c) {
   double a[8];
@@ -729,6 +811,30 @@ void col_abs_sums_launch(const double* A, int64_t lda, int M, int N, double* out
   if (N <= 0) return;
   count_launches(1);
   k_col_abs_sums<<<(N + 7) / 8, 256, 0, st>>>(A, lda, M, N, out);
+}
+
+size_t power_work_doubles(int m) {
+  const size_t tiles = (m + kPwRows - 1) / kPwRows, chunks = (m + kPwChunk - 1) / kPwChunk;
+  return 4 * (size_t)m + 4 * (size_t)m * chunks + 4 * tiles;
+}
+
+void power_radius_launch(const double* const* M, int nmat, int m, int64_t ld, int steps,
+                         double* work, double* out, cudaStream_t st) {
+  if (m <= 0 || nmat < 1 || nmat > 4 || steps < 2) return;
+  const int tiles = (m + kPwRows - 1) / kPwRows, chunks = (m + kPwChunk - 1) / kPwChunk;
+  PowerMats pm{};
+  for (int q = 0; q < nmat; ++q) pm.M[q] = M[q];
+  double* y = work;
+  double* part = y + 4 * (size_t)m;
+  double* nrm = part + 4 * (size_t)m * chunks;
+  for (int k = 0; k < steps; ++k) {
+    count_launches(2);
+    k_power_gemv<<<dim3(tiles, chunks, nmat), kPwRows, 0, st>>>(pm, m, ld, y, nrm, tiles, k == 0,
+                                                                 part);
+    k_power_finish<<<dim3(tiles, nmat), kPwRows, 0, st>>>(part, m, chunks, y, nrm, tiles);
+  }
+  count_launches(1);
+  k_power_norms<<<1, 32, 0, st>>>(nrm, tiles, nmat, out);
 }
 
 double fp64_fma_probe(int sm_count, double* scratch, cudaStream_t st) {

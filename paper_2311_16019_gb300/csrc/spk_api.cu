@@ -68,12 +68,13 @@ struct Buf {
 // the launching stream around each group of launches).
 enum ProfFam {
   F_SPMM, F_UPDATE, F_SCALE, F_SKETCH, F_QTDOT, F_QUPDATE, F_TSQR, F_BORDER,
-  F_GJE, F_GEMM, F_SIGNCOMB, F_RHO, F_TRUNC, F_TRSM, F_XACC, F_GJE_PANEL, F_GJE_UPDATE, F_COUNT
+  F_GJE, F_GEMM, F_SIGNCOMB, F_RHO, F_TRUNC, F_TRSM, F_XACC, F_GJE_PANEL, F_GJE_UPDATE,
+  F_SIGNSCALE, F_COUNT
 };
 static const char* kFamNames[F_COUNT] = {
   "spmm_dots", "gs_update", "cholqr_scale", "sketch_srht", "whiten_qt_dot", "whiten_q_update",
   "whiten_cholqr", "border_update", "gje_invert", "gemm_f64", "sign_combine", "rho", "truncate_svd",
-  "trsm", "x_accumulate", "gje_panel_H", "gje_update_H"};
+  "trsm", "x_accumulate", "gje_panel_H", "gje_update_H", "sign_scaling"};
 
 struct ProfAcc {
   double ms = 0, bytes = 0, flops = 0;
@@ -272,9 +273,13 @@ int grid_rows(spk_handle* h, int64_t n) {
 // for the matrix sign function of Z = [[H, -F], [0, -G^T]] (Roberts):
 //   H <- (c H + H^{-1}/c)/2,  G <- (c G + G^{-1}/c)/2,
 //   F <- (c F + H^{-1} F G^{-T} / c)/2,    Y = F_inf / 2,
-// with one scalar c for the whole of Z, the 1-norm scaling
-//   c = (||H^{-1}||_1 ||G^{-1}||_1 / (||H||_1 ||G||_1))^{1/4}
-// while the iterates still change by more than 1e-2, c = 1 afterwards.
+// with one scalar c for the whole of Z while the iterates still change by
+// more than 1e-2, c = 1 afterwards.  c is the spectral scaling of Kenney and
+// Laub, c = (|lambda|_min |lambda|_max)^{-1/2} over the eigenvalues of H and
+// G together, with the two moduli estimated by power iteration on H, G,
+// H^{-1} and G^{-1} (kPowerSteps products each; an error of a few percent
+// in c costs nothing measurable); if an estimate is not finite and positive,
+// the 1-norm scaling c = (||H^{-1}||_1 ||G^{-1}||_1 / (||H||_1 ||G||_1))^{1/4}.
 // Quadratic convergence: once an update changes H and G by less than 1e-8
 // (relative Frobenius), the next error is below 1e-16 and the loop stops.
 // Requires the spectra of H and G in the open right half plane (true for
@@ -288,6 +293,8 @@ int grid_rows(spk_handle* h, int64_t n) {
 // which doubles the column count per step at 4 m^2 q flops instead of the
 // 8 m^3 of the two dense products; once 2q would pass qcap (the factors'
 // capacity) the product is formed and the iteration continues densely.
+constexpr int kPowerSteps = 10;
+
 int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_newton,
                cudaStream_t st, int* iters_out, double* Lf = nullptr, double* Rf = nullptr,
                int q0 = 0, int qcap = 0) {
@@ -302,14 +309,15 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
   WS(cvecG, double, "sg_cvecG", 2 * (size_t)m);
   WS(scalH, double, "sg_scalH", 8);
   WS(scalG, double, "sg_scalG", 8);
-  WS(cs, double, "sg_colsums", 4 * (size_t)m);
-  WS(gpanel, double, "sg_panel", (size_t)m * 64);
-  WS(gbsave, double, "sg_bsave", (size_t)m * 64);
-  WS(gpanelG, double, "sg_panelG", (size_t)m * 64);
-  WS(gbsaveG, double, "sg_bsaveG", (size_t)m * 64);
+  WS(cs, double, "sg_colsums", 4 * (size_t)m + 4);
+  WS(pwork, double, "sg_power", power_work_doubles(m));
+  WS(gpanel, double, "sg_panel", (size_t)m * gje_panel_width());
+  WS(gbsave, double, "sg_bsave", (size_t)m * gje_panel_width());
+  WS(gpanelG, double, "sg_panelG", (size_t)m * gje_panel_width());
+  WS(gbsaveG, double, "sg_bsaveG", (size_t)m * gje_panel_width());
   const int sgrid = sign_combine_grid(m);
   WS(part, double, "sg_part", 4 * (size_t)sgrid);
-  std::vector<double> hpart(4 * (size_t)sgrid), hcs(4 * (size_t)m);
+  std::vector<double> hpart(4 * (size_t)sgrid), hcs(4 * (size_t)m + 4);
   double delta_prev = 1e300;
   bool converged = false;
   int it = 0;
@@ -357,7 +365,13 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
       col_abs_sums_launch(Hinv, m, m, m, cs + m, st);
       col_abs_sums_launch(Gk, m, m, m, cs + 2 * m, st);
       col_abs_sums_launch(Ginv, m, m, m, cs + 3 * m, st);
-      CK(cudaMemcpyAsync(hcs.data(), cs, sizeof(double) * 4 * m, cudaMemcpyDeviceToHost, st));
+      {
+        const double mm2 = (double)m * m;
+        ProfScope ps(h, F_SIGNSCALE, st, kPowerSteps * 4 * 8.0 * mm2, kPowerSteps * 4 * 2.0 * mm2);
+        const double* mats[4] = {Hk, Gk, Hinv, Ginv};
+        power_radius_launch(mats, 4, m, m, kPowerSteps, pwork, cs + 4 * m, st);
+      }
+      CK(cudaMemcpyAsync(hcs.data(), cs, sizeof(double) * (4 * m + 4), cudaMemcpyDeviceToHost, st));
     }
     TRY(wait_stream(h, st, h->host_wait_s));
     CK(cudaGetLastError());
@@ -368,10 +382,15 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
       return fail(h, SPK_ERR_SINGULAR_PROJECTED, "zero pivot in sign iteration %d (m=%d)", it, m);
     }
     if (scale) {
-      double n1[4] = {0, 0, 0, 0};
-      for (int q = 0; q < 4; ++q)
-        for (int j = 0; j < m; ++j) n1[q] = std::max(n1[q], hcs[(size_t)q * m + j]);
-      c = std::pow((n1[1] * n1[3]) / (n1[0] * n1[2]), 0.25);
+      // rad: estimates of rho(H), rho(G), rho(H^{-1}), rho(G^{-1})
+      const double* rad = hcs.data() + 4 * (size_t)m;
+      c = std::sqrt(std::max(rad[2], rad[3]) / std::max(rad[0], rad[1]));
+      if (!std::isfinite(c) || c <= 0.0) {
+        double n1[4] = {0, 0, 0, 0};
+        for (int q = 0; q < 4; ++q)
+          for (int j = 0; j < m; ++j) n1[q] = std::max(n1[q], hcs[(size_t)q * m + j]);
+        c = std::pow((n1[1] * n1[3]) / (n1[0] * n1[2]), 0.25);
+      }
       if (!std::isfinite(c) || c <= 0.0) c = 1.0;
     }
     if (fact && 2 * q > qcap) {

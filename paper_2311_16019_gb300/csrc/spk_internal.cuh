@@ -337,6 +337,13 @@ void gather_cols_launch(const double* A, int64_t lda, int M, const int* idx, con
                         int ncols, double* out, int64_t ldo, cudaStream_t st);
 // out[j] = column absolute sums of A (M x N, column-major)
 void col_abs_sums_launch(const double* A, int64_t lda, int M, int N, double* out, cudaStream_t st);
+// Spectral-radius estimates of nmat <= 4 matrices (m x m, column-major,
+// leading dimension ld) by `steps` >= 2 power-iteration steps from a fixed
+// start vector: out[q] (device) = ||M_q x|| with x the normalised iterate
+// after steps - 1 products.  work: power_work_doubles(m) doubles.
+size_t power_work_doubles(int m);
+void power_radius_launch(const double* const* M, int nmat, int m, int64_t ld, int steps,
+                         double* work, double* out, cudaStream_t st);
 // out2_dev = {trace(A), trace(B)}, A and B m x m column-major.
 void diag_sums_launch(const double* A, int64_t lda, const double* B, int64_t ldb, int m,
                       double* out2_dev, cudaStream_t st);

@@ -92,6 +92,32 @@ def test_sylvester_dense_against_bartels_stewart(m):
     assert it < 60
 
 
+def _two_eigenvalue_matrix(m, seed, a, b):
+    rng = np.random.default_rng(seed)
+    Qm, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    lam = np.where(np.arange(m) < m // 2, a, b)
+    return (Qm * lam[None, :]) @ Qm.T
+
+
+@pytest.mark.parametrize("m", [64, 300])
+@pytest.mark.parametrize("a,b", [(1.0, 1e4), (3.0, 50.0)])
+def test_sylvester_dense_spectral_scaling(m, a, b):
+    """H and G symmetric with the two eigenvalues a and b only.  With the
+    spectral scaling c = (|lambda|_min |lambda|_max)^{-1/2} the first Newton
+    step maps both eigenvalues to (sqrt(b/a) + sqrt(a/b)) / 2, the second to
+    1, and the third changes nothing: three steps.  (The 1-norm scaling
+    takes four at these sizes, so the count shows that the power-iteration
+    estimates of the two moduli are in use.)"""
+    H = _two_eigenvalue_matrix(m, 1, a, b)
+    G = _two_eigenvalue_matrix(m, 2, a, b)
+    F = np.zeros((m, m))
+    F[:3, :3] = np.random.default_rng(4).standard_normal((3, 3))
+    Y, it = spk().sylvester_dense(H, G, F)
+    Yref = sl.solve_sylvester(H, G.T, F)
+    assert np.linalg.norm(Y - Yref) <= 1e-11 * np.linalg.norm(Yref)
+    assert it == 3
+
+
 CASES = [
     # workload, k, s, d, sketch
     ("lap16_r1", 2, 64, 12, "srht"),
