@@ -114,7 +114,7 @@ constexpr int kGjeThreads = 256;
 constexpr int kGjePanelThreads = 128;
 constexpr int kGjeBatch = 8;     // rows per thread per load batch
 constexpr size_t kGemmReserve = 42 * 1024;
-constexpr int kGjeNb = 64;      // panel width of the blocked path
+constexpr int kGjeNb = 128;     // panel width of the blocked path
 constexpr int kGjeBlockedMin = 256;
 
 // Block-wide argmax of per-thread (best |value|, index) pairs, ties to the

@@ -295,6 +295,12 @@ int grid_rows(spk_handle* h, int64_t n) {
 // capacity) the product is formed and the iteration continues densely.
 constexpr int kPowerSteps = 10;
 
+// Adaptive check schedule (see the solver loop): fraction of the
+// extrapolated remaining iterations taken per step, and the largest step
+// relative to d.
+constexpr double kCheckStepFraction = 0.85;
+constexpr double kCheckGrowth = 0.5;
+
 int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_newton,
                cudaStream_t st, int* iters_out, double* Lf = nullptr, double* Rf = nullptr,
                int q0 = 0, int qcap = 0) {
@@ -1269,9 +1275,14 @@ struct Solver {
       last_good = d;
       if (o.check_schedule == SPK_CHECK_ADAPTIVE && o.fixed_d <= 0) {
         // Doubling warm-up (checks at p, 2p, 4p, ...) until log(rho) has
-        // decreased over two checks; then extrapolate log(rho) linearly in d
-        // from the last two checks and check next at the predicted
-        // convergence iteration plus 5% (rounded up to a multiple of p).
+        // decreased over two checks.  Then the step to the next check is
+        // kCheckStepFraction times the iterations that the straight line
+        // through the last two log(rho) values needs to reach tol (+5%), at
+        // most kCheckGrowth * d, rounded up to a multiple of p.  log(rho)
+        // steepens as d grows (the convergence is superlinear), so the line
+        // through two checks overestimates what is left, and checks spaced
+        // at most geometrically keep the slope estimate local; a check costs
+        // O((d r)^3), so the early, closer checks are cheap.
         int nxt = 2 * d;
         const size_t nh = hrel.size();
         if (nh >= 3 && hrel[nh - 1] < hrel[nh - 2] && hrel[nh - 2] < hrel[nh - 3] &&
@@ -1279,8 +1290,9 @@ struct Solver {
           const double slope = (std::log(hrel[nh - 1]) - std::log(hrel[nh - 2])) /
                                (double)(hd[nh - 1] - hd[nh - 2]);
           if (slope < 0) {
-            const double need = (std::log(o.tol) - std::log(hrel[nh - 1])) / slope;
-            int pred = d + (int)std::ceil(need * 1.05) + 1;
+            const double need = (std::log(o.tol) - std::log(hrel[nh - 1])) / slope * 1.05;
+            const double step = std::min(kCheckStepFraction * need, kCheckGrowth * d);
+            int pred = d + (int)std::ceil(step);
             pred = ((pred + o.p - 1) / o.p) * o.p;
             nxt = std::max(pred, d + o.p);
           }

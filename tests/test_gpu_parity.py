@@ -81,7 +81,7 @@ def _rhp_matrix(m, seed, nonnormal=0.3):
 @pytest.mark.parametrize("m", [1, 8, 65, 200, 300, 700])
 def test_sylvester_dense_against_bartels_stewart(m):
     """Small sizes use the unblocked Gauss-Jordan inversion, m > 256 the
-    blocked one (64-column panels; 300 and 700 leave a ragged last panel)."""
+    blocked one (128-column panels; 300 and 700 leave a ragged last panel)."""
     H = _rhp_matrix(m, 1)
     G = _rhp_matrix(m, 2)
     F = np.zeros((m, m))
