@@ -296,10 +296,8 @@ int grid_rows(spk_handle* h, int64_t n) {
 constexpr int kPowerSteps = 10;
 
 // Adaptive check schedule (see the solver loop): fraction of the
-// extrapolated remaining iterations taken per step, and the largest step
-// relative to d.
-constexpr double kCheckStepFraction = 0.85;
-constexpr double kCheckGrowth = 0.5;
+// extrapolated remaining iterations taken per step.
+constexpr double kCheckStepFraction = 0.7;
 
 int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_newton,
                cudaStream_t st, int* iters_out, double* Lf = nullptr, double* Rf = nullptr,
@@ -1277,12 +1275,12 @@ struct Solver {
         // Doubling warm-up (checks at p, 2p, 4p, ...) until log(rho) has
         // decreased over two checks.  Then the step to the next check is
         // kCheckStepFraction times the iterations that the straight line
-        // through the last two log(rho) values needs to reach tol (+5%), at
-        // most kCheckGrowth * d, rounded up to a multiple of p.  log(rho)
-        // steepens as d grows (the convergence is superlinear), so the line
-        // through two checks overestimates what is left, and checks spaced
-        // at most geometrically keep the slope estimate local; a check costs
-        // O((d r)^3), so the early, closer checks are cheap.
+        // through the last two log(rho) values needs to reach tol (+5%),
+        // rounded up to a multiple of p.  log(rho) steepens as d grows (the
+        // convergence is superlinear), so the line through two checks
+        // overestimates what is left; a check costs a chain of O(d r)
+        // dependent launches plus O((d r)^3) flops, so it pays to check a
+        // little early rather than add more checks.
         int nxt = 2 * d;
         const size_t nh = hrel.size();
         if (nh >= 3 && hrel[nh - 1] < hrel[nh - 2] && hrel[nh - 2] < hrel[nh - 3] &&
@@ -1291,7 +1289,7 @@ struct Solver {
                                (double)(hd[nh - 1] - hd[nh - 2]);
           if (slope < 0) {
             const double need = (std::log(o.tol) - std::log(hrel[nh - 1])) / slope * 1.05;
-            const double step = std::min(kCheckStepFraction * need, kCheckGrowth * d);
+            const double step = kCheckStepFraction * need;
             int pred = d + (int)std::ceil(step);
             pred = ((pred + o.p - 1) / o.p) * o.p;
             nxt = std::max(pred, d + o.p);
