@@ -254,10 +254,27 @@ int spk_sketch_apply_static(int64_t n, int32_t s, uint64_t seed, int32_t sketch_
  * spk_launch_count: number of CUDA kernel launches issued by the library
  * since it was loaded (all handles).                                      */
 int64_t spk_launch_count(void);
+
+/* spk_next_check: the adaptive check schedule (SPK_CHECK_ADAPTIVE), as the
+ * solver applies it, exposed as a host-only function (no device, no handle).
+ * hist_d[0..count) are the iterations at which the residual estimate was
+ * computed (increasing) and hist_rel their relative estimates
+ * rho / ||beta_1 beta_2^T||_F (Eq. (3.5)).  With d = hist_d[count - 1]:
+ * while count < 3 or the last three estimates do not strictly decrease, the
+ * next check is 2 d; otherwise the line through the last two (d, log rho)
+ * points reaches log tol after `need` more iterations, and the next check is
+ * d + ceil(0.7 * 1.05 * need) rounded up to a multiple of p, and at least
+ * d + p.  The result is then min(result, dmax), raised to d + 1 if that
+ * is smaller (the solver's last check is at dmax).  Returns SPK_ERR_ARG
+ * for null pointers, count < 1, p < 1, tol <= 0 or dmax < 1.  Not in the
+ * paper, which checks every p iterations.                                 */
+int32_t spk_next_check(const int32_t* hist_d, const double* hist_rel, int32_t count,
+                       double tol, int32_t p, int32_t dmax);
 /* spk_profile_enable: turn per-family timing on/off for this handle and reset
  * the counters.  When on, CUDA events are recorded on the launching stream
  * around every group of launches of a kernel family; spk_profile_read
- * returns, for family index 0..14 (SPK_ERR_ARG beyond), its name, total GPU
+ * returns, for family index 0, 1, ... (SPK_ERR_ARG past the last one, 17
+ * in this version), its name, total GPU
  * milliseconds, kernel launches, timed groups, and the ALGORITHMIC bytes and
  * flops of those launches (the minimum the step must move/compute).      */
 int spk_profile_enable(spk_handle* h, int on);

@@ -295,9 +295,36 @@ int grid_rows(spk_handle* h, int64_t n) {
 // capacity) the product is formed and the iteration continues densely.
 constexpr int kPowerSteps = 10;
 
-// Adaptive check schedule (see the solver loop): fraction of the
-// extrapolated remaining iterations taken per step.
+// Adaptive check schedule.  Doubling warm-up (checks at p, 2p, 4p, ...)
+// until log(rho) has decreased over two checks.  Then the step to the next
+// check is kCheckStepFraction times the iterations that the straight line
+// through the last two log(rho) values needs to reach tol (+5%), rounded up
+// to a multiple of p.  log(rho) steepens as d grows (the convergence is
+// superlinear), so the line through two checks overestimates what is left;
+// a check costs a chain of O(d r) dependent launches plus O((d r)^3) flops,
+// so it pays to check a little early rather than add more checks.
+// hd[0..count): the checked iterations, hrel: their relative estimates.
 constexpr double kCheckStepFraction = 0.7;
+
+int next_check_adaptive(const int32_t* hd, const double* hrel, int count, double tol, int p,
+                        int dmax) {
+  const int d = hd[count - 1];
+  int64_t nxt = 2 * (int64_t)d;
+  if (count >= 3 && hrel[count - 1] < hrel[count - 2] && hrel[count - 2] < hrel[count - 3] &&
+      hrel[count - 1] > 0 && hd[count - 1] > hd[count - 2]) {
+    const double slope = (std::log(hrel[count - 1]) - std::log(hrel[count - 2])) /
+                         (double)(hd[count - 1] - hd[count - 2]);
+    if (slope < 0) {
+      const double need = (std::log(tol) - std::log(hrel[count - 1])) / slope * 1.05;
+      double step = std::min(kCheckStepFraction * need, 1e9);
+      if (!(step >= 0.0)) step = 0.0;
+      int64_t pred = d + (int64_t)std::ceil(step);
+      pred = ((pred + p - 1) / p) * p;
+      nxt = std::max<int64_t>(pred, (int64_t)d + p);
+    }
+  }
+  return (int)std::max<int64_t>((int64_t)d + 1, std::min<int64_t>(nxt, dmax));
+}
 
 int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_newton,
                cudaStream_t st, int* iters_out, double* Lf = nullptr, double* Rf = nullptr,
@@ -1271,32 +1298,8 @@ struct Solver {
         break;
       }
       last_good = d;
-      if (o.check_schedule == SPK_CHECK_ADAPTIVE && o.fixed_d <= 0) {
-        // Doubling warm-up (checks at p, 2p, 4p, ...) until log(rho) has
-        // decreased over two checks.  Then the step to the next check is
-        // kCheckStepFraction times the iterations that the straight line
-        // through the last two log(rho) values needs to reach tol (+5%),
-        // rounded up to a multiple of p.  log(rho) steepens as d grows (the
-        // convergence is superlinear), so the line through two checks
-        // overestimates what is left; a check costs a chain of O(d r)
-        // dependent launches plus O((d r)^3) flops, so it pays to check a
-        // little early rather than add more checks.
-        int nxt = 2 * d;
-        const size_t nh = hrel.size();
-        if (nh >= 3 && hrel[nh - 1] < hrel[nh - 2] && hrel[nh - 2] < hrel[nh - 3] &&
-            hrel[nh - 1] > 0) {
-          const double slope = (std::log(hrel[nh - 1]) - std::log(hrel[nh - 2])) /
-                               (double)(hd[nh - 1] - hd[nh - 2]);
-          if (slope < 0) {
-            const double need = (std::log(o.tol) - std::log(hrel[nh - 1])) / slope * 1.05;
-            const double step = kCheckStepFraction * need;
-            int pred = d + (int)std::ceil(step);
-            pred = ((pred + o.p - 1) / o.p) * o.p;
-            nxt = std::max(pred, d + o.p);
-          }
-        }
-        next_check = std::max(d + 1, std::min(nxt, dmax));
-      }
+      if (o.check_schedule == SPK_CHECK_ADAPTIVE && o.fixed_d <= 0)
+        next_check = next_check_adaptive(hd.data(), hrel.data(), (int)hd.size(), o.tol, o.p, dmax);
     }
     if (d > dmax) d = dmax;
     cudaEventRecord(e1, st);
@@ -1752,6 +1755,12 @@ int spk_sylvester_dense(spk_handle* h, int32_t m, const double* H, const double*
 }
 
 int64_t spk_launch_count(void) { return launch_count(); }
+
+int32_t spk_next_check(const int32_t* hist_d, const double* hist_rel, int32_t count, double tol,
+                       int32_t p, int32_t dmax) {
+  if (!hist_d || !hist_rel || count < 1 || p < 1 || !(tol > 0.0) || dmax < 1) return SPK_ERR_ARG;
+  return next_check_adaptive(hist_d, hist_rel, count, tol, p, dmax);
+}
 
 int spk_profile_enable(spk_handle* h, int on) {
   if (!h) return SPK_ERR_ARG;

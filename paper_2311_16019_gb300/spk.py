@@ -97,6 +97,7 @@ def load() -> C.CDLL:
         "spk_sylvester_dense": (i32, [vp, i32, vp, vp, vp, vp, P(i32), vp]),
         "spk_inspect": (i32, [vp, C.c_char_p, vp, i64, P(i64)]),
         "spk_launch_count": (i64, []),
+        "spk_next_check": (i32, [P(i32), P(dbl), i32, dbl, i32, i32]),
         "spk_profile_enable": (i32, [vp, C.c_int]),
         "spk_profile_read": (i32, [vp, C.c_int, P(C.c_char_p), P(dbl), P(i64), P(i64), P(dbl), P(dbl)]),
         "spk_fp64_peak": (i32, [vp, P(dbl), vp]),
@@ -502,6 +503,20 @@ def inspect(name: str, device: int = 0) -> np.ndarray:
 
 def launch_count() -> int:
     return int(load().spk_launch_count())
+
+
+def next_check(hist_d, hist_rel, tol: float, p: int, dmax: int) -> int:
+    """The adaptive schedule's next check iteration (spk_next_check; host only)."""
+    d = np.ascontiguousarray(hist_d, dtype=np.int32)
+    r = np.ascontiguousarray(hist_rel, dtype=np.float64)
+    if d.shape != r.shape:
+        raise ValueError("hist_d and hist_rel differ in length")
+    rc = load().spk_next_check(d.ctypes.data_as(C.POINTER(C.c_int32)),
+                               r.ctypes.data_as(C.POINTER(C.c_double)), int(d.size), float(tol),
+                               int(p), int(dmax))
+    if rc < 0:
+        raise SpkError(rc, "spk_next_check: invalid argument")
+    return int(rc)
 
 
 def profile_enable(on: bool = True, device: int = 0):
