@@ -326,11 +326,12 @@ def run_reference(args, rank, world, pg):
     from paper_2311_16019_gb300 import inputs as I
     P = I.workload(args.workload)
     opts = solver_opts(args)
-    # schedule to extrapolate to: the oracle's own convergence is unknown at
-    # this size, so use the checks of a geometric schedule up to the GPU's
-    # typical stopping iteration for this workload (1100 for 512^2, r = 4).
-    D = {"cd2d_512_r4": 1100}.get(args.workload, 300)
-    hist = [20 * 2 ** i for i in range(8) if 20 * 2 ** i < D] + [D]
+    # schedule to extrapolate to: the checks the adaptive schedule makes on
+    # this workload (the oracle's residual history is the GPU's, so it would
+    # check at the same iterations: 20, 40, 80, 400, 900 on 512^2 with r = 4);
+    # other workloads: a doubling schedule up to 300.
+    hist = {"cd2d_512_r4": [20, 40, 80, 400, 900]}.get(args.workload, [20, 40, 80, 160, 300])
+    D = hist[-1]
     times = []
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
