@@ -296,3 +296,76 @@ def test_converged_lap32_matches_full_arnoldi_iterations():
     g = AR.galerkin(P.A, P.BT, P.C1, P.C2, 300, tol=1e-8)
     assert res["converged"] and abs(res["d"] - g["d"]) <= 0.05 * g["d"] + 1
     assert M.true_residual(P.A, P.B, P.C1, P.C2, res["X1"], res["X2"]) < 5e-8
+
+
+def _cd2d_small(N, r, seed):
+    A, _ = I.convdiff_2d(N, 10.0, lambda x, y: (x, y))
+    B, _ = I.convdiff_2d(N, 10.0, lambda x, y: (y, -x))
+    C1, C2 = I.rhs_factors(A.shape[0], B.shape[0], r, seed)
+    return A, B, sp.csr_matrix(B.T), C1, C2
+
+
+def test_P13_galerkin_exact_when_krylov_space_is_everything():
+    """Full block Arnoldi (Eq. (2.1)) on a non-normal operator: once d r = n
+    the bases are square and orthogonal, so the Galerkin solution is the
+    exact solution of Eq. (1.1) and the residual (3.6) vanishes."""
+    A, B, BT, C1, C2 = _cd2d_small(7, 7, 5)          # n = 49 = 7 blocks of 7
+    X = ADJ.dense_solve(A, B, C1, C2)
+    g = AR.galerkin(A, BT, C1, C2, 7)
+    assert np.linalg.norm(g["X1"] @ g["X2"].T - X) < 1e-12 * np.linalg.norm(X)
+    assert g["rel"] < 1e-12
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_P13b_sketched_exact_when_krylov_space_is_everything(k):
+    """Algorithm 1 with a subsampled (not orthogonal) SRHT, s = 56 of n' = 64
+    rows for n = 49: S is injective on R^n, so once U_d and V_d span R^n the
+    sketched Petrov-Galerkin condition S_U R S_V^T = 0 forces R = 0.  (With
+    r = 1 the truncated basis stays well enough conditioned at d = n.)"""
+    A, B, BT, C1, C2 = _cd2d_small(7, 1, 5)
+    X = ADJ.dense_solve(A, B, C1, C2)
+    res = SP.spkms(A, BT, C1, C2, k=k, s=56, tol=0.0, maxit=49, p=49, seed=3, trunc_tol=0)
+    assert np.linalg.norm(res["X1"] @ res["X2"].T - X) < 1e-11 * np.linalg.norm(X)
+    assert res["rel_rho"] < 1e-12
+
+
+def test_P14_tpkms_with_full_window_is_full_arnoldi():
+    """Algorithm 2 with k_A, k_B >= d orthogonalises against every block, so
+    its bases, H, G and X are full Arnoldi's (Section 2.1), and its residual
+    bound (3.3) brackets the exact residual norm (3.6):
+    ||R|| <= rho_tr / sqrt(dr) <= sqrt(2) ||R||."""
+    P = I.workload("cd2d_16_r2")
+    d = 10
+    t = TP.tpkms(P.A, P.BT, P.C1, P.C2, kA=d, kB=d, tol=0.0, maxit=d)
+    g = AR.galerkin(P.A, P.BT, P.C1, P.C2, d)
+    Xt, Xg = t["X1"] @ t["X2"].T, g["X1"] @ g["X2"].T
+    assert np.linalg.norm(Xt - Xg) < 1e-12 * np.linalg.norm(Xg)
+    R = P.A @ Xg + Xg @ P.B - P.C1 @ P.C2.T
+    assert g["rho"] == pytest.approx(np.linalg.norm(R), rel=1e-9)
+    scaled = t["hist"][-1][1] / np.sqrt(d * P.r)
+    assert g["rho"] * (1 - 1e-12) <= scaled <= np.sqrt(2) * g["rho"] * (1 + 1e-12)
+
+
+def test_P15_truncated_arnoldi_relation_and_local_orthogonality():
+    """Algorithm 2's truncated block Arnoldi: A U_d = U_{d+1} H_(d+1 x d) with
+    H banded (k - 1 blocks above the diagonal), and each new block
+    orthonormal against the k blocks it was orthogonalised against, but not
+    against older ones."""
+    P = I.workload("cd2d_16_r2")
+    d, k, r = 12, 2, 2
+    blocks, H, beta = TP._truncated(P.A, P.C1, k, d)
+    Ud = np.hstack([blocks[j] for j in range(1, d + 1)])
+    Ud1 = np.hstack([blocks[j] for j in range(1, d + 2)])
+    Hb = block_hessenberg(H, d, r)
+    assert np.linalg.norm(P.A @ Ud - Ud1 @ Hb) < 1e-13 * np.linalg.norm(P.A @ Ud)
+    for (i, j) in H:
+        assert j - k + 1 <= i <= j + 1
+    assert np.allclose(blocks[1] @ beta, P.C1, atol=1e-13 * np.abs(P.C1).max())
+    far = 0.0
+    for j in range(2, d + 2):
+        assert np.allclose(blocks[j].T @ blocks[j], np.eye(r), atol=1e-13)
+        for i in range(max(1, j - k), j):
+            assert np.abs(blocks[i].T @ blocks[j]).max() < 1e-13
+        if j - k - 1 >= 1:
+            far = max(far, np.abs(blocks[j - k - 1].T @ blocks[j]).max())
+    assert far > 1e-3          # the truncation is real: older blocks are not orthogonal
