@@ -316,15 +316,18 @@ def test_P13_galerkin_exact_when_krylov_space_is_everything():
     assert g["rel"] < 1e-12
 
 
-@pytest.mark.parametrize("k", [2, 3])
-def test_P13b_sketched_exact_when_krylov_space_is_everything(k):
-    """Algorithm 1 with a subsampled (not orthogonal) SRHT, s = 56 of n' = 64
-    rows for n = 49: S is injective on R^n, so once U_d and V_d span R^n the
-    sketched Petrov-Galerkin condition S_U R S_V^T = 0 forces R = 0.  (With
-    r = 1 the truncated basis stays well enough conditioned at d = n.)"""
-    A, B, BT, C1, C2 = _cd2d_small(7, 1, 5)
+@pytest.mark.parametrize("r", [2, 3])
+def test_P13b_sketched_exact_when_krylov_space_is_everything(r):
+    """Algorithm 1 with a subsampled (not orthogonal) SRHT, s = 60 of n' = 64
+    rows for n = 36: S is injective on R^n, so once U_d and V_d span R^n
+    (d r = 36) the sketched Petrov-Galerkin condition S_U R S_V^T = 0 forces
+    R = 0.  (k = 3 keeps T's condition number near 1e9 (r = 2) and 1e7
+    (r = 3) at d r = n; with k = 2 and r = 2 it reaches 1e16 and the
+    recovered X is lost to rounding.)"""
+    A, B, BT, C1, C2 = _cd2d_small(6, r, 5)
     X = ADJ.dense_solve(A, B, C1, C2)
-    res = SP.spkms(A, BT, C1, C2, k=k, s=56, tol=0.0, maxit=49, p=49, seed=3, trunc_tol=0)
+    d = 36 // r
+    res = SP.spkms(A, BT, C1, C2, k=3, s=60, tol=0.0, maxit=d, p=d, seed=3, trunc_tol=0)
     assert np.linalg.norm(res["X1"] @ res["X2"].T - X) < 1e-11 * np.linalg.norm(X)
     assert res["rel_rho"] < 1e-12
 
