@@ -173,6 +173,27 @@ def test_diagonal_closed_form_gpu():
     assert np.linalg.norm(Xg - X) < 1e-10 * np.linalg.norm(X)
 
 
+@pytest.mark.parametrize("r", [2, 3])
+def test_exact_at_krylov_exhaustion_gpu(r):
+    """The largest d a problem admits: d r = n = 36 on a non-normal
+    convection-diffusion pair, with a subsampled SRHT (s = 60 of n' = 64, so
+    S is injective but not orthogonal).  The bases then span R^n and the
+    sketched Petrov-Galerkin condition forces R = 0: X is the exact solution
+    (the oracle's pin P13b reaches it to 1e-14)."""
+    A, _ = I.convdiff_2d(6, 10.0, lambda x, y: (x, y))
+    B, _ = I.convdiff_2d(6, 10.0, lambda x, y: (y, -x))
+    BT = sp.csr_matrix(B.T)
+    C1, C2 = I.rhs_factors(36, 36, r, 5)
+    d = 36 // r
+    g = spk().solve(A, BT, C1, C2, k=3, s=60, maxit=d, p=1, tol=0.0, seed=3, fixed_d=d,
+                    trunc_tol=1e-15)
+    assert g.iters == d
+    X = sl.solve_sylvester(A.toarray(), B.toarray(), C1 @ C2.T)
+    Xg = host(g.X1) @ host(g.X2).T
+    assert np.linalg.norm(Xg - X) < 1e-8 * np.linalg.norm(X)
+    assert g.rel_rho < 1e-8
+
+
 def test_symmetry_gpu():
     P = I.workload("lap16_r1")
     g = spk().solve(P.A, P.BT, P.C1, P.C1, k=2, s=128, maxit=40, p=1, tol=0.0, fixed_d=40,
