@@ -14,12 +14,20 @@ import scipy.linalg as sl
 
 
 def dense_solve(A, B, C1, C2):
+    """X of Eq. (1.1), densely, by SciPy's Bartels-Stewart routine (the
+    method of the lyap solver the paper's experiments use for the projected
+    equations, Section 6).  Small n only."""
     A = np.asarray(A.todense() if hasattr(A, "todense") else A)
     B = np.asarray(B.todense() if hasattr(B, "todense") else B)
     return sl.solve_sylvester(A, B, C1 @ C2.T)
 
 
 def dense_gradient(A, B, A_theta, B_theta, C1, C2, u, v):
+    """L = u^T X v and its gradients by the formulas of this module's
+    docstring: Lambda from the transposed equation of Eq. (1.1),
+    A^T Lambda + Lambda B^T = u v^T, then dL/dC1 = Lambda C2,
+    dL/dC2 = Lambda^T C1, dL/dtheta = -<Lambda, A_theta X + X B_theta>_F.
+    The paper has no adjoint; this differentiates its Eq. (1.1) directly."""
     A = np.asarray(A.todense() if hasattr(A, "todense") else A)
     B = np.asarray(B.todense() if hasattr(B, "todense") else B)
     At = np.asarray(A_theta.todense() if hasattr(A_theta, "todense") else A_theta)

@@ -69,15 +69,19 @@ def galerkin(A, BT, C1, C2, d: int, tol: float = 0.0, p: int = 1):
 
 
 def memory_vectors_full(d: int, r: int) -> int:
-    """Length-n vectors held by full Arnoldi: both bases, (d+1) r each."""
+    """Length-n vectors held by full Arnoldi: both bases, (d+1) r each
+    (the memory table of Section 5, tab_memory; the "Mem" column of the
+    Section 6 tables)."""
     return 2 * (d + 1) * r
 
 
 def memory_vectors_spkms(rank: int) -> int:
-    """Length-n vectors of the s-PKSM solution factors X1, X2 (rank each)."""
+    """Length-n vectors of the s-PKSM solution factors X1, X2 (rank each),
+    as the Section 6 tables count them."""
     return 2 * rank
 
 
 def memory_vectors_tpkms(kA: int, kB: int, r: int) -> int:
-    """Length-n vectors of the two truncated windows, k_A r + k_B r."""
+    """Length-n vectors of the two truncated windows, k_A r + k_B r, as the
+    t-PKSM table of Example 6.1 (tab2:ex2) counts them."""
     return (kA + kB) * r

@@ -52,6 +52,9 @@ def splitmix64_stream(x0: int, count: int, start: int = 0) -> np.ndarray:
 
 
 def stream_state(seed: int, sketch_id: int, sub: int) -> int:
+    """Start state of the SplitMix64 stream of one sketch (sketch_id 0 for
+    S_U, 1 for S_V) and one kind of draw (sub 0: row keys of D, 1: signs of
+    E).  Section 2.2 leaves the random draws of D and E unspecified."""
     return (seed + (1 + 2 * sketch_id + sub) * _STREAM) % (1 << 64)
 
 
@@ -77,6 +80,9 @@ def srht_draws(n: int, s: int, seed: int, sketch_id: int):
 
 
 def _popcount_parity(a: np.ndarray) -> np.ndarray:
+    """Parity of the number of set bits of each entry, one bit at a time:
+    the Walsh-Hadamard entry H[j, i] (Sylvester ordering) is
+    (-1)^parity(j & i), the N of Section 2.2's S = D N E."""
     a = a.astype(np.uint64)
     par = np.zeros(a.shape, dtype=np.uint64)
     while np.any(a):
@@ -189,6 +195,7 @@ class Sketch:
             raise ValueError(kind)
 
     def __call__(self, X: np.ndarray) -> np.ndarray:
+        """S X for the columns of X (Section 2.2)."""
         if self.kind == "identity":
             return np.array(X, dtype=np.float64) * self.scale
         if self.kind == "dct":
@@ -196,6 +203,7 @@ class Sketch:
         return srht_apply(X, self.s, self.seed, self.sketch_id, self.scale)
 
     def dense(self) -> np.ndarray:
+        """The explicit s x n matrix S, for brute-force checks."""
         if self.kind == "identity":
             return np.eye(self.n) * self.scale
         if self.kind == "dct":

@@ -63,7 +63,10 @@ class SideState:
 
 
 def _init_side(op, C, k, S, store_basis) -> SideState:
-    # Algorithm 1, first step: skinny QR of C and of the sketch of U_1.
+    """Algorithm 1's first step for one side: the skinny QR U_1 ell = C
+    (positive diagonal), the QR of the sketch S U_1 = Q_1 T_1 (so T_1 is the
+    R factor of S U_1, the reading taken above), and beta = T_1 ell, the R
+    factor of S C that enters the projected right-hand side of Eq. (3.4)."""
     U1, ell = qr_pos(C)
     U1 = right_solve_upper(C, ell)  # U_1 = C ell^{-1}, reproducible in the replay
     Q1, T1 = qr_pos(S(U1))

@@ -16,6 +16,10 @@ from .linalg import qr_pos, right_solve_upper, block_hessenberg
 
 
 def _truncated(op, C, k, d):
+    """Algorithm 2's truncated block Arnoldi (Appendix A): A U_j is
+    orthogonalised by modified Gram-Schmidt against U_{j-k+1}, ..., U_j only,
+    then U_{j+1} h_{j+1,j} is its positive-diagonal skinny QR.  Returns all
+    blocks {j: U_j}, the banded H {(i, j): h_ij} and beta (C = U_1 beta)."""
     U1, beta = qr_pos(C)
     blocks = {1: U1}
     H = {}
@@ -32,6 +36,12 @@ def _truncated(op, C, k, d):
 
 
 def tpkms(A, BT, C1, C2, *, kA: int, kB: int, tol: float, maxit: int, p: int = 1):
+    """Run Algorithm 2 (t-PKSM, Appendix A): truncated bases of K_d(A, C1)
+    and K_d(B^T, C2) with windows k_A and k_B, then every p iterations the
+    projected equation H_d Y + Y G_d^T = E_1 beta_1 beta_2^T E_1^T with the
+    banded H_d, G_d, and the residual bound of Proposition 3.1 (Eq. (3.3)),
+    tested against tol relative to ||beta_1 beta_2^T||_F.  Returns
+    X1 = U_d Y and X2 = V_d (Y not truncated), the history and the bases."""
     C1 = np.atleast_2d(np.asarray(C1, dtype=np.float64).T).T
     C2 = np.atleast_2d(np.asarray(C2, dtype=np.float64).T).T
     r = C1.shape[1]
