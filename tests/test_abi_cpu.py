@@ -93,3 +93,39 @@ def test_package_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, flags=re.M), f
                 assert "oracle/" not in txt, f
+
+
+def test_plain_c_program_links_and_calls_the_library(lib):
+    """A C99 program (no C++, no torch) includes spk.h, links libspk.so and
+    calls it: the host-only schedule function and spk_create, which without a
+    GPU must return SPK_ERR_CUDA instead of aborting."""
+    import torch
+    from paper_2311_16019_gb300 import spk
+    src = r'''
+#include <stdio.h>
+#include "spk.h"
+int main(void) {
+  const int32_t d[3] = {20, 40, 80};
+  const double rel[3] = {1e-2, 1e-3, 1e-4};
+  int32_t next = spk_next_check(d, rel, 3, 1e-8, 20, 1500);
+  spk_handle* h = NULL;
+  int rc = spk_create(&h, 0);
+  if (rc == SPK_OK) spk_destroy(h);
+  printf("%d %d %d\n", (int)next, rc, h == NULL);
+  return 0;
+}
+'''
+    libdir = os.path.dirname(spk.LIB_PATH)
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "t")
+        subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I",
+                               os.path.join(ROOT, "include"), c, "-o", exe,
+                               "-L", libdir, "-lspk", "-Wl,-rpath," + libdir])
+        nxt, rc, null = (int(x) for x in subprocess.check_output([exe]).split())
+    # the line through (40, -3) and (80, -4) in (d, log10 rel) reaches -8
+    # 160 iterations after 80; 80 + ceil(0.7 * 1.05 * 160) = 198 -> 200 (p = 20)
+    assert nxt == 200
+    if not torch.cuda.is_available():
+        assert rc == -2 and null == 1
