@@ -372,3 +372,26 @@ def test_P15_truncated_arnoldi_relation_and_local_orthogonality():
         if j - k - 1 >= 1:
             far = max(far, np.abs(blocks[j - k - 1].T @ blocks[j]).max())
     assert far > 1e-3          # the truncation is real: older blocks are not orthogonal
+
+
+def test_truncation_rule_is_the_best_low_rank_approximation():
+    """Reading c7 (Section 5's low-rank factors of Y): keep the singular
+    triplets with sigma_i > eps sigma_1 and split sqrt(Sigma) between the
+    factors.  Y1 Y2^T is then the best rank-l approximation (Eckart-Young:
+    spectral error sigma_{l+1}), Y1^T Y1 = Y2^T Y2 = Sigma_l, and the count
+    follows the threshold exactly, on a matrix with known singular values."""
+    rng = np.random.default_rng(11)
+    m = 40
+    Pm, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    Qm, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    sig = 0.5 * 10.0 ** (-np.arange(m) / 4.0)          # sigma_1 / sigma_40 = 1e9.75
+    Y = (Pm * sig[None, :]) @ Qm.T
+    for eps, ell in ((10 ** (-2.5 / 4), 3), (10 ** (-20.5 / 4), 21), (0.0, m)):
+        Y1, Y2, s = SP.truncate(Y, eps)
+        assert Y1.shape == (m, ell) and Y2.shape == (m, ell)
+        assert np.allclose(s, sig, rtol=1e-5)
+        E = Y - Y1 @ Y2.T
+        tail = sig[ell] if ell < m else 0.0
+        assert np.linalg.norm(E, 2) <= tail * (1 + 1e-6) + 1e-15
+        assert np.allclose(Y1.T @ Y1, np.diag(sig[:ell]), atol=1e-13)
+        assert np.allclose(Y2.T @ Y2, np.diag(sig[:ell]), atol=1e-13)
