@@ -220,11 +220,16 @@ int spk_dct_sketch_draws(spk_handle* h, int64_t n, int32_t s, uint64_t seed,
 int spk_dct_sketch_apply(spk_handle* h, int64_t n, int32_t s, uint64_t seed,
                          int32_t sketch_id, const double* X_dev, int32_t r, double* SX_dev,
                          void* stream);
-/* Y = A X for CSR A and X_dev (ncols x r row-major), Y_dev (nrows x r).   */
+/* Y = A X for CSR A and X_dev (ncols x r row-major), Y_dev (nrows x r):
+ * the product A U_d that starts each step of Algorithm 1 (Eq. (2.3)), any
+ * r >= 1.  SPK_ERR_ARG for null pointers or r < 1.                        */
 int spk_spmm(spk_handle* h, const spk_csr* A, const double* X_dev, int32_t r,
              double* Y_dev, void* stream);
 /* Small dense Sylvester solve H Y + Y G^T = F (column-major m x m, device)
- * by the scaled Newton sign iteration; Y_dev m x m column-major.          */
+ * by the scaled Newton sign iteration: the projected equation of Eq. (3.4)
+ * with H = H~_d, G = G~_d.  Y_dev m x m column-major; *newton_iters_host
+ * receives the Newton steps taken.  SPK_ERR_SINGULAR_PROJECTED when a pivot
+ * vanishes or the spectra are not in the open right half plane.          */
 int spk_sylvester_dense(spk_handle* h, int32_t m, const double* H_dev,
                         const double* G_dev, const double* F_dev, double* Y_dev,
                         int32_t* newton_iters_host, void* stream);
