@@ -129,3 +129,34 @@ int main(void) {
     assert nxt == 200
     if not torch.cuda.is_available():
         assert rc == -2 and null == 1
+
+
+def test_binding_constants_match_header_enums():
+    """The binding's status codes and option values are the header's enums
+    (compiled from spk.h, not parsed), so a renumbering on either side fails
+    here instead of selecting the wrong sketch, precision or method."""
+    from paper_2311_16019_gb300 import spk
+    names = ["SPK_OK", "SPK_ERR_ARG", "SPK_ERR_CUDA", "SPK_ERR_ALLOC", "SPK_ERR_BREAKDOWN",
+             "SPK_ERR_SINGULAR_PROJECTED", "SPK_ERR_NONFINITE", "SPK_ERR_NOT_CONVERGED",
+             "SPK_ERR_TIMEOUT", "SPK_ERR_UNSUPPORTED"]
+    enums = {"SPK_SKETCH_SRHT": spk.SKETCH["srht"], "SPK_SKETCH_IDENTITY": spk.SKETCH["identity"],
+             "SPK_SKETCH_DCT": spk.SKETCH["dct"], "SPK_PREC_FP64": spk.PRECISION["fp64"],
+             "SPK_PREC_MIXED_FP32": spk.PRECISION["mixed_fp32"],
+             "SPK_PREC_MIXED_BF16": spk.PRECISION["mixed_bf16"],
+             "SPK_CHECK_EVERY_P": spk.CHECK["every_p"], "SPK_CHECK_ADAPTIVE": spk.CHECK["adaptive"],
+             "SPK_METHOD_SKETCHED": spk.METHOD["sketched"],
+             "SPK_METHOD_TRUNCATED": spk.METHOD["truncated"], "SPK_METHOD_FULL": spk.METHOD["full"],
+             "SPK_INJECT_NAN_C1": spk.INJECT_NAN_C1,
+             "SPK_INJECT_RANK_DEFICIENT": spk.INJECT_RANK_DEFICIENT,
+             "SPK_INJECT_TIMEOUT": spk.INJECT_TIMEOUT, "SPK_INJECT_SINGULAR": spk.INJECT_SINGULAR}
+    enums.update({n: getattr(spk, n) for n in names})
+    keys = sorted(enums)
+    body = "".join(f'  printf("%ld\\n", (long){k});\n' for k in keys)
+    src = '#include <stdio.h>\n#include "spk.h"\nint main(void) {\n' + body + "  return 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "e.c")
+        open(c, "w").write(src)
+        exe = os.path.join(d, "e")
+        subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        got = [int(x) for x in subprocess.check_output([exe]).split()]
+    assert dict(zip(keys, got)) == {k: enums[k] for k in keys}
