@@ -1,0 +1,91 @@
+"""Host-side arithmetic of bench.py, checked on the CPU: the roofline of the
+dominant kernel family, the clock record's parsing, the FP64 ALU peak from
+unit counts and clocks, and the factored true residual."""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_host", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_roofline_picks_the_dominant_family_and_its_bound(bench):
+    # 1 TFLOP/s FP64 and 5000 GB/s: balance 0.2 flop/byte
+    prof = {
+        "dense": {"ms": 300.0, "groups": 10, "launches": 100, "bytes": 1e9, "flops": 2.4e11},
+        "stream": {"ms": 100.0, "groups": 100, "launches": 200, "bytes": 4e11, "flops": 1e10},
+    }
+    roof, table = bench.pick_roofline(prof, hbm_gbs=5000.0, fp64_tflops=1.0)
+    assert roof["kernel"] == "dense" and roof["bound"] == "alu"
+    assert roof["achieved"] == pytest.approx(2.4e11 / 0.3 / 1e12)      # 0.8 TFLOP/s
+    assert roof["frac"] == pytest.approx(0.8)
+    assert roof["avg_launch_ms"] == pytest.approx(3.0)
+    assert roof["algorithmic_flops_per_launch"] == pytest.approx(2.4e9)
+    assert roof["traffic"] is None
+    assert sum(v["share"] for v in table.values()) == pytest.approx(1.0, abs=1e-3)
+    assert list(table) == ["dense", "stream"]
+    # the same families with the streaming one dominant: an HBM bound
+    prof["stream"]["ms"] = 1000.0
+    roof, _ = bench.pick_roofline(prof, hbm_gbs=5000.0, fp64_tflops=1.0)
+    assert roof["kernel"] == "stream" and roof["bound"] == "hbm"
+    assert roof["achieved"] == pytest.approx(400.0) and roof["unit"] == "GB/s"
+    assert roof["frac"] == pytest.approx(400.0 / 5000.0)
+    assert bench.pick_roofline({}, 5000.0, 1.0) == (None, {})
+
+
+def test_fp64_alu_peak_from_units_and_clock(bench):
+    peak, mhz = bench.fp64_alu_peak(152)
+    assert peak == pytest.approx(152 * 2 * 2 * mhz * 1e6 / 1e12)
+    assert mhz > 1000.0
+
+
+def test_clock_record_parsing(bench):
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    cs = bench.ClockSampler(0)
+    cs.proc = FakeProc()
+    cs.lines = [
+        "0, 2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.1, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    rec = cs.stop()
+    assert rec["sm_mhz"] == 2070.0 and rec["sm_max_mhz"] == 2070.0
+    assert rec["samples"] == 3
+    assert rec["reasons"] == ["sw_power_cap"]
+    assert bench.ClockSampler(0).stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_true_residual_in_factored_form(bench):
+    rng = np.random.default_rng(3)
+    n1, n2, r, ell = 60, 45, 2, 5
+    A = sp.random(n1, n1, density=0.1, random_state=1, format="csr") + sp.identity(n1) * 3
+    B = sp.random(n2, n2, density=0.1, random_state=2, format="csr") + sp.identity(n2) * 3
+    C1, C2 = rng.standard_normal((n1, r)), rng.standard_normal((n2, r))
+    X1, X2 = rng.standard_normal((n1, ell)), rng.standard_normal((n2, ell))
+    X = X1 @ X2.T
+    R = A @ X + X @ B - C1 @ C2.T
+    want = np.linalg.norm(R) / np.linalg.norm(C1 @ C2.T)
+    assert bench.true_residual(A, B, C1, C2, X1, X2) == pytest.approx(want, rel=1e-12)
+
+
+def test_replica_throughput_is_whole_job(bench):
+    # 4 replicas, 3 solves each, slowest rank 6 s -> 2 solves/s for the job
+    assert bench.replica_throughput(4, 3, 6000.0) == pytest.approx(2.0)
