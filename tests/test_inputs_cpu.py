@@ -197,3 +197,19 @@ def test_batched_sweep_distribution():
     for p, q in zip(batch[:3], again):
         assert p.meta["N"] == q.meta["N"] and p.theta == q.theta
         assert np.array_equal(p.C1, q.C1)
+
+
+def test_operator_family_reassembles_the_convection_sweep():
+    """The autograd path rebuilds A(theta) = A0 + theta A_theta and
+    B(theta) on the host: at the problem's own theta it gives back A and B,
+    and at another theta the generator's operators for that theta."""
+    from paper_2311_16019_gb300.autograd import OperatorFamily
+    P = I.workload("cd2d_32_r2")
+    fam = OperatorFamily.from_problem(P)
+    A, B = fam.at(P.theta)
+    assert abs(A - P.A).max() < 1e-10 * abs(P.A).max()
+    assert abs(B - P.B).max() < 1e-10 * abs(P.B).max()
+    A3, _ = fam.at(3.0)
+    want, _ = I.convdiff_2d(32, 3.0, lambda x, y: (x, y))
+    assert abs(A3 - want).max() < 1e-10 * abs(want).max()
+    assert A3.has_sorted_indices and B.has_sorted_indices
