@@ -61,7 +61,7 @@ enum { SPK_CHECK_EVERY_P = 0, SPK_CHECK_ADAPTIVE = 1 };
 /* SPK_METHOD_SKETCHED: Algorithm 1 (s-PKSM, whitened by the sketch).
  * SPK_METHOD_TRUNCATED: Algorithm 2 (t-PKSM): the same truncated Arnoldi
  * without sketch or whitening; projected equation with the banded H_d, G_d
- * and the residual bound of Proposition 3.1 (Eq. (3.3)); s is ignored.    */
+ * and the residual bound of Proposition 3.1 (Eq. (3.2)); s is ignored.    */
 /* SPK_METHOD_FULL: full block Arnoldi (Section 2.1) with the Galerkin
  * projected equation and the exact residual norm; the basis of both spaces
  * is kept ((maxit+1) r length-n vectors each, FP64 only), s is ignored.
@@ -90,7 +90,7 @@ typedef struct spk_csr {
  * implementation's choices.  spk_opts_default fills every field. */
 typedef struct spk_opts {
     int32_t k_left;          /* truncation k for K(A, C1): orthogonalise the new
-                                block against the last k blocks (Eq. (2.3))    */
+                                block against the last k blocks (Eq. (2.4))    */
     int32_t k_right;         /* truncation k for K(B^T, C2)                    */
     int32_t s;               /* sketch rows (SRHT); ignored for IDENTITY       */
     int32_t maxit;           /* maximum number of iterations d                 */
@@ -221,7 +221,7 @@ int spk_dct_sketch_apply(spk_handle* h, int64_t n, int32_t s, uint64_t seed,
                          int32_t sketch_id, const double* X_dev, int32_t r, double* SX_dev,
                          void* stream);
 /* Y = A X for CSR A and X_dev (ncols x r row-major), Y_dev (nrows x r):
- * the product A U_d that starts each step of Algorithm 1 (Eq. (2.3)), any
+ * the product A U_d that starts each step of Algorithm 1 (Eq. (2.4)), any
  * r >= 1.  SPK_ERR_ARG for null pointers or r < 1.                        */
 int spk_spmm(spk_handle* h, const spk_csr* A, const double* X_dev, int32_t r,
              double* Y_dev, void* stream);

@@ -16,7 +16,7 @@ Modules
   sketch   - subsampled randomized Hadamard transform from SplitMix64 draws
   spkms    - Algorithm 1 step by step (plus the Section 5 bordering update)
   tpkms    - Algorithm 2 (truncated Arnoldi, no sketch)
-  arnoldi  - full block Arnoldi / Galerkin (Eq. (2.1), Eq. (3.5))
+  arnoldi  - full block Arnoldi / Galerkin (Eq. (2.1), Eq. (3.7))
   measure  - gauge-free distances and true residuals of low-rank factors
   adjoint  - dense FP64 gradient of u^T X v for the adjoint checks
 

@@ -1,4 +1,4 @@
-"""Full block Arnoldi and the Galerkin solution (Section 2.1, Eq. (3.6)).
+"""Full block Arnoldi and the Galerkin solution (Section 2.1, Eq. (3.7)).
 
 Test infrastructure: see oracle/__init__.py.
 

@@ -3,8 +3,8 @@
 Test infrastructure: see oracle/__init__.py.
 
 The method solves A X + X B = C1 C2^T (Eq. (1.1)) by truncated block Arnoldi
-(Eq. (2.3)) on K_d(A, C1) and K_d(B^T, C2), whitens the non-orthogonal bases
-through the QR factorisations of their sketches (Proposition 2.1, Eq. (2.4)),
+(Eq. (2.4)) on K_d(A, C1) and K_d(B^T, C2), whitens the non-orthogonal bases
+through the QR factorisations of their sketches (Proposition 2.1, Eqs. (2.5)-(2.6)),
 solves the sketched Galerkin problem (Eq. (3.4)) and estimates the sketched
 residual norm (Eq. (3.5)); the factors are recovered by a second Arnoldi sweep
 that replays the stored coefficients (Section 5).
@@ -107,7 +107,7 @@ def _arnoldi_step(st: SideState, d: int) -> None:
 
 
 def projected_matrix(st: SideState, d: int):
-    """H~_d = Hhat_d + Hhat E_d^T of Eq. (2.5), formed directly.
+    """H~_d = Hhat_d + Hhat E_d^T of Eqs. (2.9)-(2.10), formed directly.
 
     Hhat_d = T_d H_d T_d^{-1}, Hhat = T_H h_{d+1,d} tau_d^{-1}; returns
     (H~_d, hhat) with hhat = tau_{d+1} h_{d+1,d} tau_d^{-1}.

@@ -4,7 +4,7 @@ Test infrastructure: see oracle/__init__.py.
 
 Truncated block Arnoldi with windows k_A, k_B (modified Gram-Schmidt over
 the last k blocks), projected equation H_d Y + Y G_d^T = E1 beta1 beta2^T E1^T
-(Section 3), and the residual bound of Proposition 3.1 (Eq. (3.3)):
+(Section 3), and the residual bound of Proposition 3.1 (Eq. (3.2)):
     rho = sqrt(dr) (||Y E_d g_{d+1,d}^T||_F + ||h_{d+1,d} E_d^T Y||_F).
 """
 from __future__ import annotations
@@ -39,7 +39,7 @@ def tpkms(A, BT, C1, C2, *, kA: int, kB: int, tol: float, maxit: int, p: int = 1
     """Run Algorithm 2 (t-PKSM, Appendix A): truncated bases of K_d(A, C1)
     and K_d(B^T, C2) with windows k_A and k_B, then every p iterations the
     projected equation H_d Y + Y G_d^T = E_1 beta_1 beta_2^T E_1^T with the
-    banded H_d, G_d, and the residual bound of Proposition 3.1 (Eq. (3.3)),
+    banded H_d, G_d, and the residual bound of Proposition 3.1 (Eq. (3.2)),
     tested against tol relative to ||beta_1 beta_2^T||_F.  Returns
     X1 = U_d Y and X2 = V_d (Y not truncated), the history and the bases."""
     C1 = np.atleast_2d(np.asarray(C1, dtype=np.float64).T).T

@@ -1,4 +1,4 @@
-// Truncated block Arnoldi kernels (Algorithm 1's basis loop; Eq. (2.3)).
+// Truncated block Arnoldi kernels (Algorithm 1's basis loop; Eq. (2.4)).
 //
 // Per iteration d and operator (A, U) or (B^T, V):
 //   spmm_dots   : U~ = A U_d (thread per CSR row; the r-wide row of U is one

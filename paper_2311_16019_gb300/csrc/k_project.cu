@@ -1,4 +1,4 @@
-// Projected matrices and the residual estimate (Eq. (2.5), Section 5, Eq. (3.5)).
+// Projected matrices and the residual estimate (Eqs. (2.9)-(2.10), Section 5, Eq. (3.5)).
 //
 // H~_d = Hhat_d + Hhat E_d^T with Hhat_d = T_d H_d T_d^{-1} and
 // Hhat = T_H h_{d+1,d} tau_d^{-1} is kept up to date by the bordering update of
@@ -213,7 +213,7 @@ __global__ void k_border_correct(double* __restrict__ Ht, int64_t ldH, int m, in
 // blocks hhat = tau_{d+1} h_{d+1,d} tau_d^{-1} (and ghat likewise):
 //   rho = sqrt(||hhat E_d^T Y||_F^2 + ||Y E_d ghat^T||_F^2).
 // Truncated method (TU == nullptr, bound != 0), the bound of Proposition 3.1
-// (Eq. (3.3)):  rho = sqrt(m) (||h E_d^T Y||_F + ||Y E_d g^T||_F),  h = h_{d+1,d}.
+// (Eq. (3.2)):  rho = sqrt(m) (||h E_d^T Y||_F + ||Y E_d g^T||_F),  h = h_{d+1,d}.
 // Full Arnoldi (TU == nullptr, bound == 0), the exact residual norm of the
 // Galerkin solution:  rho = sqrt(||h E_d^T Y||_F^2 + ||Y E_d g^T||_F^2).
 // out3 = {rho, rho / ||beta1 beta2^T||_F, ||beta1 beta2^T||_F}.

@@ -55,7 +55,7 @@ def test_P2_dense_bartels_stewart():
 def test_P3_reduction_to_galerkin(kind, k):
     """With an orthogonal sketch (S = I, or the SRHT with s = n' = n) the
     sketched-and-truncated approximation equals full Arnoldi's Galerkin one
-    for any k (Section 2.3 RGS equivalence; Eq. (3.6)) and rho = ||R||_F."""
+    for any k (Section 2.3 RGS equivalence; Eq. (3.7)) and rho = ||R||_F."""
     P = I.workload("cd2d_16_r2")  # n = 256 = n'
     d = 12
     if kind == "identity":
@@ -94,7 +94,7 @@ def test_P4_rho_equals_sketched_residual_bruteforce():
 
 
 def test_P5_polynomial_exactness():
-    """Eq. (4.8): Uhat_d p(H~_d) E_1 beta_1 = p(A) C1 for deg p <= d-1."""
+    """Eq. (4.11): Uhat_d p(H~_d) E_1 beta_1 = p(A) C1 for deg p <= d-1."""
     P = I.workload("cd2d_24_r2")
     d = 8
     res = _run(P, k=2, s=120, maxit=d, store_basis=True)
@@ -114,7 +114,7 @@ def test_P5_polynomial_exactness():
 
 
 def test_P6_sketched_arnoldi_relation_and_bordering():
-    """Proposition 2.1 (Eq. (2.4)) with the stored basis; T is the R factor of
+    """Proposition 2.1 (Eqs. (2.5)-(2.6)) with the stored basis; T is the R factor of
     S U_{d+1}; Section 5 bordering update equals T H T^{-1} (with the
     tau_{d+1}^{-1} reading of its last term)."""
     P = I.workload("cd2d_24_r2")
@@ -218,8 +218,8 @@ def test_P10_tpkms_residual_bound():
         assert np.linalg.norm(R) <= res["hist"][-1][1] * (1 + 1e-12)
 
 
-def test_P11_example_4_1_arnoldi_relation():
-    """Example 4.1's deterministic part: for the n = 30 Toeplitz matrix and
+def test_P11_example_4_2_arnoldi_relation():
+    """Example 4.2's deterministic part: for the n = 30 Toeplitz matrix and
     b = ones/sqrt(n), the QR of the Krylov matrix gives A V(:,1:d-1) = V H with
     H = R(1:d,2:d) R(1:d-1,1:d-1)^{-1}; full Arnoldi must produce the same H
     (up to the column signs fixed by the positive-diagonal convention)."""
@@ -395,3 +395,29 @@ def test_truncation_rule_is_the_best_low_rank_approximation():
         assert np.linalg.norm(E, 2) <= tail * (1 + 1e-6) + 1e-15
         assert np.allclose(Y1.T @ Y1, np.diag(sig[:ell]), atol=1e-13)
         assert np.allclose(Y2.T @ Y2, np.diag(sig[:ell]), atol=1e-13)
+
+
+@pytest.mark.parametrize("s,d", [(400, 10), (500, 20)])
+def test_P16_sketched_residual_bound_of_appendix_B(s, d):
+    """Eq. (3.6) via Theorem B.3: the residual lies in span(U_{d+1}) x
+    span(V_{d+1}) (Arnoldi relations), so rho = ||S_U R S_V^T||_F and ||R||_F
+    differ at most by the extreme singular values of the sketched orthonormal
+    bases, and (1+et)^-1 rho^2 <= ||R||^2 <= (1-et)^-1 rho^2 with
+    et = eps (2 + eps), eps the measured embedding distortion of the two
+    (d+1) r dimensional Krylov spaces (squared-norm definition, Eq. (2.2))."""
+    P = I.workload("cd2d_24_r2")
+    res = _run(P, k=2, s=s, maxit=d, p=d, store_basis=True)
+    X = SP.dense_solution(res)
+    R = P.A @ X + X @ P.B - P.C1 @ P.C2.T
+    eps, lo, hi = 0.0, 1.0, 1.0
+    for blocks, S in ((res["U_blocks"], res["SU"]), (res["V_blocks"], res["SV"])):
+        basis = sl.orth(np.hstack([blocks[j] for j in range(1, d + 2)]))
+        assert basis.shape[1] == (d + 1) * P.r
+        sv = np.linalg.svd(S.dense() @ basis, compute_uv=False)
+        eps = max(eps, float(np.max(np.abs(sv ** 2 - 1.0))))
+        lo, hi = lo * sv.min(), hi * sv.max()
+    rho, nR = res["rho"], np.linalg.norm(R)
+    assert lo * nR * (1 - 1e-10) <= rho <= hi * nR * (1 + 1e-10)
+    et = eps * (2 + eps)
+    assert et < 1.0
+    assert rho ** 2 / (1 + et) <= nR ** 2 <= rho ** 2 / (1 - et)
