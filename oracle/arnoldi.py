@@ -70,7 +70,7 @@ def galerkin(A, BT, C1, C2, d: int, tol: float = 0.0, p: int = 1):
 
 def memory_vectors_full(d: int, r: int) -> int:
     """Length-n vectors held by full Arnoldi: both bases, (d+1) r each
-    (the memory table of Section 5, tab_memory; the "Mem" column of the
+    (Table 1, the memory table of Section 5; the "Mem" column of the
     Section 6 tables)."""
     return 2 * (d + 1) * r
 
@@ -83,5 +83,5 @@ def memory_vectors_spkms(rank: int) -> int:
 
 def memory_vectors_tpkms(kA: int, kB: int, r: int) -> int:
     """Length-n vectors of the two truncated windows, k_A r + k_B r, as the
-    t-PKSM table of Example 6.1 (tab2:ex2) counts them."""
+    t-PKSM table of Example 6.1 (Table 3) counts them."""
     return (kA + kB) * r

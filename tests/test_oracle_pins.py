@@ -289,7 +289,7 @@ def test_adjoint_dense_gradient_by_finite_differences():
 
 
 def test_converged_lap32_matches_full_arnoldi_iterations():
-    """Table tab1:ex2's qualitative claim: s-PKSM needs about as many
+    """Table 2's qualitative claim (Example 6.1): s-PKSM needs about as many
     iterations as full Arnoldi (within 5 %) at the same tolerance."""
     P = I.workload("lap32_r1")
     res = SP.spkms(P.A, P.BT, P.C1, P.C2, k=2, s=600, tol=1e-8, maxit=300, p=1, seed=0)
