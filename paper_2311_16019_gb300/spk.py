@@ -212,6 +212,27 @@ class SolveResult:
 def make_opts(*, k=2, k_right=None, s=600, maxit=300, p=1, tol=1e-8, trunc_tol=1e-12, seed=0,
               sketch="srht", precision="fp64", check="every_p", same_sketch=False, fixed_d=0,
               max_newton=100, inject=0, method="sketched") -> Opts:
+    """The spk_opts struct of include/spk.h from keyword options.
+
+    k, k_right: truncation (window) of the left and right Krylov spaces
+        (Eq. (2.4)); k_right defaults to k.
+    s: sketch rows (s >= (maxit + 1) r for the sketched method).
+    maxit, p, tol: Algorithm 1's iteration cap, check period and stopping
+        tolerance on rho / ||beta_1 beta_2^T||_F (Eq. (3.5)).
+    trunc_tol: keep the singular values of Y above trunc_tol * sigma_1.
+    seed: seed of the sketch draws (SplitMix64 streams).
+    sketch: "srht" (Walsh-Hadamard, Section 2.2), "dct" (the paper's
+        experiments, Section 6) or "identity".
+    precision: "fp64", "mixed_fp32" or "mixed_bf16" (basis storage and
+        SpMM; the sketch side stays FP64).
+    check: "every_p" (Algorithm 1) or "adaptive" (spk_next_check).
+    same_sketch: S_V = S_U (square problems only).
+    fixed_d: > 0 runs exactly that many iterations with one check.
+    max_newton: cap on sign-function iterations of the projected solve.
+    inject: SPK_INJECT_* bits (host-side fault injection, tests only).
+    method: "sketched" (Algorithm 1), "truncated" (Algorithm 2) or "full"
+        (full block Arnoldi, Section 2.1).
+    """
     o = Opts()
     load().spk_opts_default(C.byref(o))
     o.k_left = k
@@ -259,9 +280,15 @@ def solve(A, BT, C1, C2, *, device: int = 0, stream=None, raise_on_error: bool =
           keep_raw: bool = False, **opts):
     """s-PKSM solve of A X + X B = C1 C2^T; BT = B^T (CSR, scipy or DeviceCSR).
 
-    Returns SolveResult with X = X1 X2^T.  With keep_raw the library-owned
-    Result struct is returned as well (the caller then frees it with
-    free_raw); used by the adjoint gradients.
+    C1 (n1 x r) and C2 (n2 x r), 1 <= r <= 4, are numpy arrays or torch
+    tensors (moved to the device as float64).  `opts` are the keywords of
+    make_opts.  Runs on `device` and the current torch stream unless
+    `stream` is given.  Returns SolveResult with X = X1 X2^T (device
+    tensors; SPK_ERR_NOT_CONVERGED returns the last check's factors with
+    converged False); any other error status raises SpkError unless
+    raise_on_error is False.  With keep_raw the library-owned Result struct is returned as
+    well (the caller then frees it with free_raw); used by the adjoint
+    gradients.
     """
     return _solve_entry("spk_solve", A, BT, C1, C2, device, stream, raise_on_error, keep_raw,
                         opts)
