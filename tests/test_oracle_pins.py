@@ -421,3 +421,33 @@ def test_P16_sketched_residual_bound_of_appendix_B(s, d):
     et = eps * (2 + eps)
     assert et < 1.0
     assert rho ** 2 / (1 + et) <= nR ** 2 <= rho ** 2 / (1 - et)
+
+
+class _Fp32Operator:
+    """A applied in float32 to a float32-rounded block: what a basis stored
+    in FP32 and an FP32 SpMM give the recurrence."""
+
+    def __init__(self, A):
+        self.A = sp.csr_matrix(A, dtype=np.float32)
+
+    def __matmul__(self, X):
+        return (self.A @ np.asarray(X, dtype=np.float32)).astype(np.float64)
+
+
+def test_fp32_basis_floor_is_inherent_to_the_method():
+    """The mixed form (FP32 basis and SpMM, FP64 sketch side) is not in the
+    paper.  With A applied in FP32 the Arnoldi relation (2.4) holds only to
+    FP32 accuracy: the sketched estimate rho (3.5) still converges (it
+    measures the projected problem), but the true residual stops near
+    u_32-scale.  The oracle with an FP32 operator shows this floor, so the
+    GPU mixed form's residual floor is the method's in that precision."""
+    P = I.workload("cd2d_32_r2")
+    kw = dict(k=4, s=1000, tol=1e-10, maxit=250, p=10, seed=0)
+    ref = SP.spkms(P.A, P.BT, P.C1, P.C2, **kw)
+    mixed = SP.spkms(_Fp32Operator(P.A), _Fp32Operator(P.BT), P.C1, P.C2, **kw)
+    assert ref["converged"] and mixed["converged"]
+    t_ref = M.true_residual(P.A, P.B, P.C1, P.C2, ref["X1"], ref["X2"])
+    t_mix = M.true_residual(P.A, P.B, P.C1, P.C2, mixed["X1"], mixed["X2"])
+    assert t_ref < 1e-10
+    assert mixed["rel_rho"] < 1e-10
+    assert 1e-8 < t_mix < 1e-6
