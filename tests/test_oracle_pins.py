@@ -451,3 +451,26 @@ def test_fp32_basis_floor_is_inherent_to_the_method():
     assert t_ref < 1e-10
     assert mixed["rel_rho"] < 1e-10
     assert 1e-8 < t_mix < 1e-6
+
+
+def test_projected_spectra_leave_the_right_half_plane_past_convergence():
+    """Section 4.1's caveat, measured: the field of values of H~_d can cross
+    the imaginary axis although A's lies in the right half plane.  On the 3-D
+    upwind problem (16^3, r = 2, k = 3, s = 1600) every eigenvalue of H~_d
+    and G~_d has positive real part at d = 60 (rho/||beta1 beta2^T|| 2e-13),
+    while past convergence some do not (d = 200).  This is why the GPU's
+    sign-function solve checks trace(sign) = m and an adaptive schedule that
+    overshoots backs off to an earlier, solvable check."""
+    P = I.workload("cd3d_16_r2")
+    neg = {}
+    for d in (60, 200):
+        res = SP.spkms(P.A, P.BT, P.C1, P.C2, k=3, s=1600, tol=0.0, maxit=d, p=d, seed=0,
+                       recover=False)
+        eh = np.linalg.eigvals(res["Ht"])
+        eg = np.linalg.eigvals(res["Gt"])
+        neg[d] = int(np.sum(eh.real < 0) + np.sum(eg.real < 0))
+        if d == 60:
+            assert res["rel_rho"] < 1e-12
+    A = P.A.toarray()
+    assert np.linalg.eigvalsh((A + A.T) / 2).min() > 0      # W(A) in the right half plane
+    assert neg[60] == 0 and neg[200] > 0
