@@ -474,3 +474,22 @@ def test_projected_spectra_leave_the_right_half_plane_past_convergence():
     A = P.A.toarray()
     assert np.linalg.eigvalsh((A + A.T) / 2).min() > 0      # W(A) in the right half plane
     assert neg[60] == 0 and neg[200] > 0
+
+
+def test_leading_block_of_the_projected_matrix_is_the_earlier_one():
+    """H~_d = T_d H_d T_d^{-1} + T_H h_{d+1,d} tau_d^{-1} E_d^T (Eqs. (2.9)-(2.10))
+    has H~_{d'} as its leading d'r x d'r block for every d' < d: T_d and H_d
+    are upper triangular / Hessenberg with T_{d'}, H_{d'} in their corners,
+    and the correction of H~_{d'} is exactly the (d'+1, d') coupling term of
+    T_d H_d T_d^{-1} restricted to those rows.  The GPU's backtracking after
+    an unsolvable check relies on this: it re-solves on a leading block
+    instead of rebuilding an earlier H~."""
+    P = I.workload("cd2d_24_r2")
+    r, d = P.r, 16
+    full = _run(P, k=3, s=300, maxit=d, p=d)
+    for dp in (5, 11):
+        part = _run(P, k=3, s=300, maxit=dp, p=dp)
+        m = dp * r
+        for key in ("Ht", "Gt"):
+            lead = full[key][:m, :m]
+            assert np.abs(lead - part[key]).max() < 1e-12 * np.abs(part[key]).max(), (key, dp)
