@@ -493,3 +493,19 @@ def test_leading_block_of_the_projected_matrix_is_the_earlier_one():
         for key in ("Ht", "Gt"):
             lead = full[key][:m, :m]
             assert np.abs(lead - part[key]).max() < 1e-12 * np.abs(part[key]).max(), (key, dp)
+
+
+@pytest.mark.parametrize("sketch,k,k_right", [("dct", 2, 2), ("srht", 2, 4), ("dct", 3, 1)])
+def test_P4b_rho_bruteforce_other_sketches_and_windows(sketch, k, k_right):
+    """Eq. (3.5) against ||S_U R S_V^T||_F formed densely, with the DCT sketch
+    of Section 6 (s < n, not orthogonal) and with different truncations for
+    the two spaces (Algorithm 1 takes one k; the spaces are independent)."""
+    P = I.workload("cd2d_24_r2")
+    d = 10
+    res = _run(P, k=k, k_right=k_right, s=150, maxit=d, p=d, sketch=sketch, store_basis=True)
+    X = SP.dense_solution(res)
+    R = P.A @ X + X @ P.B - P.C1 @ P.C2.T
+    brute = np.linalg.norm(res["SU"].dense() @ R @ res["SV"].dense().T)
+    assert abs(brute - res["rho"]) < 1e-9 * brute
+    # and X is the recovered solution of the two-pass step
+    assert np.linalg.norm(res["X1"] @ res["X2"].T - X) < 1e-10 * np.linalg.norm(X)
