@@ -269,6 +269,13 @@ def test_measure_helpers_against_dense():
     R = A @ (X1 @ X2.T) + (X1 @ X2.T) @ B - C1 @ C2.T
     assert M.true_residual(A, B, C1, C2, X1, X2) == pytest.approx(
         np.linalg.norm(R) / np.linalg.norm(C1 @ C2.T), rel=1e-12)
+    # probes: zero for the same product in another gauge, 1/2 for Z = 2X,
+    # and a flipped sign is seen
+    G = np.array([[2.0, 1.0, 0.0], [0.0, 1.0, 0.0], [1.0, 0.0, 3.0]])
+    assert M.probe_errors(X1, X2, X1 @ G, X2 @ np.linalg.inv(G).T) < 1e-13
+    assert M.probe_errors(X1, X2, 2 * X1, X2) == pytest.approx(0.5, rel=1e-12)
+    S1 = rng.standard_normal((50, 3))
+    assert M.probe_errors(S1, S1, S1, -S1) > 1.0
 
 
 def test_adjoint_dense_gradient_by_finite_differences():
