@@ -278,8 +278,8 @@ int32_t spk_next_check(const int32_t* hist_d, const double* hist_rel, int32_t co
 /* spk_profile_enable: turn per-family timing on/off for this handle and reset
  * the counters.  When on, CUDA events are recorded on the launching stream
  * around every group of launches of a kernel family; spk_profile_read
- * returns, for family index 0, 1, ... (SPK_ERR_ARG past the last one, 17
- * in this version), its name, total GPU
+ * returns, for family index 0, 1, ... (18 families, indices 0..17, in
+ * this version; SPK_ERR_ARG past the last), its name, total GPU
  * milliseconds, kernel launches, timed groups, and the ALGORITHMIC bytes and
  * flops of those launches (the minimum the step must move/compute).      */
 int spk_profile_enable(spk_handle* h, int on);
