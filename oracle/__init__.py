@@ -13,7 +13,7 @@ the seeded problem generators of paper_2311_16019_gb300.inputs, which hold
 none of the method's arithmetic.
 
 Modules
-  sketch   - subsampled randomized Hadamard transform from SplitMix64 draws
+  sketch   - subsampled randomized Hadamard and DCT sketches from SplitMix64 draws
   spkms    - Algorithm 1 step by step (plus the Section 5 bordering update)
   tpkms    - Algorithm 2 (truncated Arnoldi, no sketch)
   arnoldi  - full block Arnoldi / Galerkin (Eq. (2.1), Eq. (3.7))
