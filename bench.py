@@ -85,6 +85,10 @@ def parse():
     ap.add_argument("--fixed-d", type=int, default=0,
                     help="run exactly this many iterations (small profiling cases)")
     ap.add_argument("--forms", default="fp64,mixed_fp32")
+    ap.add_argument("--fp64-until", type=float, default=1e-4,
+                    help="mixed forms: FP64 basis until the relative estimate is below this")
+    ap.add_argument("--oracle-sample", default=None,
+                    help=argparse.SUPPRESS)   # internal: one oracle sample in a fresh process
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-iters", type=int, default=40)
@@ -253,13 +257,6 @@ def _lowrank_fro(L, R):
     return float(np.linalg.norm(Ra @ Rb.T))
 
 
-def true_residual(A, B, C1, C2, X1, X2):
-    """||A X + X B - C1 C2^T||_F / ||C1 C2^T||_F for X = X1 X2^T, in factored form."""
-    L = np.hstack([A @ X1, X1, -C1])
-    R = np.hstack([X2, B.T @ X2, C2])
-    return _lowrank_fro(L, R) / _lowrank_fro(C1, C2)
-
-
 # --------------------------------------------------------------------- CPU oracle sample
 def oracle_sample(P, opts, iters: int, hist_d, r: int):
     """Time the oracle (FP64 NumPy/SciPy, as it stands) on a bounded sample of
@@ -319,6 +316,37 @@ def oracle_sample(P, opts, iters: int, hist_d, r: int):
             "t_proj_m1": tproj1, "m1": m1, "fit_a_b": [float(a), float(b)]}
 
 
+def oracle_sample_fresh(workload: str, opts: dict, iters: int, hist_d, r: int) -> dict:
+    """oracle_sample in a fresh Python process with the BLAS thread count
+    pinned to the host's cores, so that the reference arm and the
+    cpu_baseline leg time the same program under the same conditions (in
+    the GPU arm's process, the CUDA runtime and torch's own thread pool
+    share the cores with OpenBLAS)."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[var] = str(cores)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    spec = json.dumps({"workload": workload, "opts": opts, "iters": iters,
+                       "hist": list(hist_d), "r": r})
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", spec],
+                         capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+    line = [ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1]
+    res = json.loads(line)
+    res["cores"] = cores
+    return res
+
+
+def run_oracle_sample(spec_json: str):
+    from paper_2311_16019_gb300 import inputs as I
+    spec = json.loads(spec_json)
+    P = I.workload(spec["workload"])
+    res = oracle_sample(P, spec["opts"], spec["iters"], spec["hist"], spec["r"])
+    print(json.dumps(res), flush=True)
+
+
 # --------------------------------------------------------------------- main arms
 def run_reference(args, rank, world, pg):
     if rank != 0:
@@ -334,8 +362,7 @@ def run_reference(args, rank, world, pg):
     D = hist[-1]
     times = []
     for step in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        res = oracle_sample(P, opts, args.cpu_sample_iters, hist, P.r)
+        res = oracle_sample_fresh(args.workload, opts, args.cpu_sample_iters, hist, P.r)
         if step >= args.warmup:
             times.append(res["solves_per_s"])
     value = statistics.median(times)
@@ -343,10 +370,11 @@ def run_reference(args, rank, world, pg):
             "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
             "config": workload_config(P, opts, 1),
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": res["cores"],
                              "kind": "oracle", "sample": f"{args.cpu_sample_iters} oracle "
                              f"iterations + projected solves at m={res['m0']} and m={res['m1']} "
-                             f"per step, extrapolated to d={D}"},
+                             f"per step, extrapolated to d={D} (fresh process, BLAS threads "
+                             f"= {res['cores']})"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -374,13 +402,17 @@ def run_spk(args, rank, world, local, pg):
     sampler = ClockSampler(local)
     first = None
     for form in forms:
-        last = None
+        fopts = dict(opts)
+        if form != "fp64":
+            fopts["fp64_until"] = args.fp64_until
         for _ in range(args.warmup):
-            last = spk.solve(dA, dB, c1, c2, precision=form, device=local,
-                             raise_on_error=form == forms[0], **opts)
+            spk.solve(dA, dB, c1, c2, precision=form, device=local,
+                      raise_on_error=form == forms[0], **fopts)
         torch.cuda.synchronize()
         barrier(pg)
-        spk.profile_enable(form == forms[0], local)
+        # timed with the library's per-family profiler off (its events would
+        # add to the time); the family table comes from an untimed repeat
+        spk.profile_enable(False, local)
         launches0 = spk.launch_count()
         if form == forms[0]:
             sampler.start()
@@ -392,23 +424,29 @@ def run_spk(args, rank, world, local, pg):
         results = []
         for _ in range(args.steps):
             results.append(spk.solve(dA, dB, c1, c2, precision=form, device=local,
-                                     raise_on_error=form == forms[0], **opts))
+                                     raise_on_error=form == forms[0], **fopts))
         ev1.record()
         torch.cuda.synchronize()
         barrier(pg)
         ms = ev0.elapsed_time(ev1)
         launches = spk.launch_count() - launches0
         clocks = sampler.stop() if form == forms[0] else None
-        prof = spk.profile_read(local) if form == forms[0] else None
-        spk.profile_enable(False, local)
         ms_max = max_over_ranks(pg, ms)
         g = results[-1]
         if g.X1 is None:
             # a later form that stopped with an error (reported, not timed as a solve)
             per_form[form] = dict(status=g.status, ms_per_step=ms_max / args.steps)
             continue
+        prof = None
+        if form == forms[0]:
+            spk.profile_enable(True, local)
+            spk.solve(dA, dB, c1, c2, precision=form, device=local, **fopts)
+            torch.cuda.synchronize()
+            prof = spk.profile_read(local)
+            spk.profile_enable(False, local)
+        tres = g.true_rel_res if g.true_rel_res >= 0 else \
+            spk.true_residual(dA, dB, c1, c2, g, device=local)[2]
         X1, X2 = g.X1.cpu().numpy(), g.X2.cpu().numpy()
-        tres = true_residual(P.A, P.B, P.C1, P.C2, X1, X2)
         per_form[form] = dict(ms_per_step=ms_max / args.steps,
                               solves_per_s=replica_throughput(world, args.steps, ms_max),
                               iters=g.iters, rank=g.rank, converged=g.converged,
@@ -417,6 +455,9 @@ def run_spk(args, rank, world, local, pg):
                                              recover=g.ms_recover),
                               gpu_launches=launches, clocks=clocks, prof=prof, X=(X1, X2),
                               status=g.status)
+        if form != "fp64":
+            per_form[form]["fp64_until"] = args.fp64_until
+            per_form[form]["switch_d"] = g.switch_d
         if first is None:
             first = form
     base = per_form[first]
@@ -465,12 +506,13 @@ def run_spk(args, rank, world, local, pg):
                                f"TFLOP/s (live FMA probe {fp64:.4f})")
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
-        s = oracle_sample(P, opts, args.cpu_sample_iters, base["checks"], P.r)
-        cpu = {"value": s["solves_per_s"], "unit": "solves/s", "cores": os.cpu_count(),
+        s = oracle_sample_fresh(args.workload, opts, args.cpu_sample_iters, base["checks"], P.r)
+        cpu = {"value": s["solves_per_s"], "unit": "solves/s", "cores": s["cores"],
                "kind": "oracle",
                "sample": (f"{s['iters_sampled']} oracle iterations + one projected solve at "
                           f"m={s['m0']} + Bartels-Stewart at m={s['m1']} "
-                          f"({s['sample_seconds']:.1f} s), extrapolated to d={s['extrapolated_to_d']} "
+                          f"({s['sample_seconds']:.1f} s, fresh process, BLAS threads = "
+                          f"{s['cores']}), extrapolated to d={s['extrapolated_to_d']} "
                           f"with the GPU run's {s['checks']} checks (a + b d per iteration, "
                           f"m^3 per check)")}
     if rank == 0:
@@ -589,6 +631,9 @@ def run_batched(args):
 
 def main():
     args = parse()
+    if args.oracle_sample:
+        run_oracle_sample(args.oracle_sample)
+        return
     if args.kernel_case:
         run_kernel_case(args)
         return

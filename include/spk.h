@@ -107,7 +107,18 @@ typedef struct spk_opts {
     double trunc_tol;        /* keep singular values of Y above trunc_tol*s_1  */
     uint64_t seed;           /* sketch draws (SplitMix64 streams)              */
     int32_t method;          /* SPK_METHOD_*                                   */
-    int32_t reserved[7];
+    int32_t verify;          /* true-residual check of the returned factors
+                                (spk_true_residual) after the solve: 0 = for
+                                the mixed forms only (default), 1 = always,
+                                -1 = never.  When it runs and the relative
+                                true residual exceeds tol, the status is
+                                SPK_ERR_NOT_CONVERGED (factors still returned) */
+    double fp64_until;       /* mixed forms: the basis recurrence runs in FP64
+                                until a check's rho / ||beta1 beta2^T||_F is
+                                below this value, in the mixed precision after
+                                (the replay switches at the same iteration);
+                                0 = mixed precision from the first iteration   */
+    int32_t reserved[4];
 } spk_opts;
 
 /* Result of a solve.  X1/X2 and the history arrays are library-owned and
@@ -129,7 +140,13 @@ typedef struct spk_result {
     int64_t mem_basis_vectors;    /* length-n vectors of the two windows       */
     int64_t mem_solution_vectors; /* 2 * rank                                  */
     double ms_arnoldi, ms_project, ms_recover;  /* GPU time per phase          */
-    int32_t reserved[8];
+    double true_rel_res;     /* ||A X + X B - C1 C2^T||_F / ||C1 C2^T||_F of the
+                                returned factors when the verification ran
+                                (spk_opts.verify), else -1                     */
+    int32_t switch_d;        /* mixed forms with fp64_until > 0: first
+                                iteration in the mixed precision (0 = from the
+                                start, -1 = the whole run stayed FP64)         */
+    int32_t reserved[5];
 } spk_result;
 
 /* ---- lifetime ---------------------------------------------------------- */
@@ -196,6 +213,23 @@ typedef struct spk_problem {
 int spk_solve_batched(spk_handle* h, int32_t count, const spk_problem* probs,
                       int32_t concurrency, void* stream, spk_result* outs);
 
+/* spk_true_residual: the true residual of factors X = X1 X2^T (res->X1_dev,
+ * res->X2_dev, res->rank columns, as spk_solve returns them) of Eq. (1.1):
+ *     out3_host[0] = ||A X + X B - C1 C2^T||_F,
+ *     out3_host[1] = ||C1 C2^T||_F,   out3_host[2] = their ratio,
+ * computed on the device in the factored form
+ * [A X1, X1, -C1] [X2, B^T X2, C2]^T without forming X: the two factors'
+ * Gram matrices and the trace of their product are accumulated in
+ * double-double arithmetic, so that the cancellation between the three
+ * terms does not limit the result (a plain FP64 Gram would resolve it only
+ * to ~1e-8 of the terms).  Not a step of Algorithm 1, which stops on the
+ * sketched estimate of Eq. (3.5); this is the check that estimate stands
+ * for.  A, BT (= B^T), C1, C2 as for spk_solve.  SPK_ERR_ARG for null
+ * pointers or sizes that differ from the result's.  Synchronises `stream`. */
+int spk_true_residual(spk_handle* h, const spk_csr* A, const spk_csr* BT,
+                      const double* C1_dev, const double* C2_dev, int r,
+                      const spk_result* res, double* out3_host, void* stream);
+
 /* ---- single steps, for parity tests ----------------------------------- */
 /* Sketch draws (Section 2.2; SplitMix64 streams as documented in the
  * library): rows_dev[s] ascending in [0, n'), n' = 2^ceil(log2 n), and
@@ -246,11 +280,14 @@ int spk_sylvester_dense(spk_handle* h, int32_t m, const double* H_dev,
  * Limits: n <= 2^20, 1 <= r <= 4, n' r <= 2^20 (n' = 2^ceil(log2 n)),
  * 1 <= s <= min(n', 32768); beyond them SPK_ERR_ARG and a message in err
  * (errlen bytes, may be NULL).  The first call on a device (that device
- * current) looks up the array's device address; make it before any stream
- * capture.  All calls on a device share the array and leave their data in
+ * current) looks up the array's device address and creates one event.
+ * Every call waits on the host for `stream` (SPK_ERR_TIMEOUT after 600 s),
+ * so it must not be called while `stream` is being captured into a CUDA
+ * graph.  All calls on a device share the array and leave their data in
  * it; calls whose device work overlaps race and must be ordered by the
- * caller.  Waits for `stream` before returning (SPK_ERR_TIMEOUT after
- * 600 s).                                                                 */
+ * caller.  After a SPK_ERR_TIMEOUT the array stays in use until that call's
+ * kernels finish: the next call on the device waits for them (bounded, else
+ * SPK_ERR_TIMEOUT again).                                                 */
 int spk_sketch_apply_static(int64_t n, int32_t s, uint64_t seed, int32_t sketch_id,
                             const double* X_dev, int32_t r, double* SX_dev, void* stream,
                             char* err, size_t errlen);

@@ -250,10 +250,16 @@ int sketch_draws_launch(int64_t n, int32_t s, uint64_t seed, int32_t sketch_id, 
     if (cudaMemsetAsync(cnt, 0, sizeof(int32_t), st) != cudaSuccess) return SPK_ERR_CUDA;
     count_launches(1);
     k_candidates<<<grid_for(npad, 256), 256, 0, st>>>(npad, x0r, thr, (int32_t)cap, cnt, cidx, ckey);
+    // a copy into pageable host memory blocks until the stream's earlier
+    // work is done, without a limit: drain the stream by a bounded wait
+    // first, so that the copy starts at once, then wait for the copy
     int32_t hcnt = 0;
-    if (cudaMemcpyAsync(&hcnt, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-      return SPK_ERR_CUDA;
-    const int w = bounded_stream_wait(st, kHostWaitSeconds);
+    int w = bounded_stream_wait(st, kHostWaitSeconds);
+    if (w == 0) {
+      if (cudaMemcpyAsync(&hcnt, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SPK_ERR_CUDA;
+      w = bounded_stream_wait(st, kHostWaitSeconds);
+    }
     if (w == 1) {
       snprintf(err, errlen, "sketch row selection: device work did not finish");
       return SPK_ERR_TIMEOUT;

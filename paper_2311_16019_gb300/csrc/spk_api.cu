@@ -244,10 +244,22 @@ int wait_stream(spk_handle* h, cudaStream_t st, double budget_s) {
   }
 }
 
+// Device-to-host read into pageable host memory.  Such a copy blocks the
+// calling thread until the work queued before it on the stream has finished,
+// with no limit, so the stream is first drained by the bounded wait; the
+// copy then starts at once, and a second bounded wait covers the copy.
+int d2h(spk_handle* h, void* dst, const void* src, size_t bytes, cudaStream_t st,
+        double budget_s) {
+  TRY(wait_stream(h, st, budget_s));
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+  return wait_stream(h, st, budget_s);
+}
+int d2h(spk_handle* h, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  return d2h(h, dst, src, bytes, st, h->host_wait_s);
+}
+
 int read_flags(spk_handle* h, cudaStream_t st, uint32_t* out) {
-  CK(cudaMemcpyAsync(out, h->flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  TRY(wait_stream(h, st, h->host_wait_s));
-  return SPK_OK;
+  return d2h(h, out, h->flags, sizeof(uint32_t), st);
 }
 
 int flags_to_status(spk_handle* h, uint32_t f) {
@@ -266,6 +278,69 @@ constexpr double kBreakdownFloor = 1e-14;
 int grid_rows(spk_handle* h, int64_t n) {
   int64_t g = (n + 255) / 256;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)h->sm_count * 4));
+}
+
+// Double-double Gram matrix of the virtual matrix P (see k_residual.cu) into
+// the named workspace buffers <tag>hi, <tag>lo (w x w each).
+int gram_dd(spk_handle* h, const GramParts& P, const std::string& tag, double** hi, double** lo,
+            cudaStream_t st) {
+  const int w = P.wtot;
+  const int nt = gram_dd_tiles(w);
+  WS(tiles, int2, (tag + "tiles").c_str(), nt);
+  WS(work, double, "rs_work", gram_dd_work_doubles(P.n, w, h->sm_count));
+  WS(Ghi, double, (tag + "hi").c_str(), (size_t)w * w);
+  WS(Glo, double, (tag + "lo").c_str(), (size_t)w * w);
+  std::vector<int2> ht(nt);
+  gram_dd_tile_list(w, ht.data());
+  CK(cudaMemcpyAsync(tiles, ht.data(), sizeof(int2) * nt, cudaMemcpyHostToDevice, st));
+  gram_dd_launch(P, tiles, h->sm_count, work, Ghi, Glo, st);
+  // the host tile list must outlive the copy
+  TRY(wait_stream(h, st, h->host_wait_s));
+  *hi = Ghi;
+  *lo = Glo;
+  return SPK_OK;
+}
+
+// ||A X + X B - C1 C2^T||_F and ||C1 C2^T||_F for X = X1 X2^T (ell columns;
+// BT = B^T generates the right space), in the factored form
+// [A X1, X1, -C1] [X2, B^T X2, C2]^T with double-double Gram matrices
+// (k_residual.cu).  out3 (host) = {||R||_F, ||C1 C2^T||_F, ratio}.
+int true_residual(spk_handle* h, const spk_csr* A, const spk_csr* BT, const double* C1,
+                  const double* C2, int r, const double* X1, const double* X2, int ell,
+                  cudaStream_t st, double out3[3]) {
+  const int64_t n1 = A->nrows, n2 = BT->nrows;
+  WS(AX1, double, "rs_AX1", (size_t)n1 * std::max(ell, 1));
+  WS(BX2, double, "rs_BX2", (size_t)n2 * std::max(ell, 1));
+  WS(sc, double, "rs_scalars", 8);
+  if (ell > 0) {
+    spmm_wide_launch(A->rowptr_dev, A->col_dev, A->val_dev, n1, ell, X1, AX1, st);
+    spmm_wide_launch(BT->rowptr_dev, BT->col_dev, BT->val_dev, n2, ell, X2, BX2, st);
+  }
+  GramParts L, M, c1, c2;
+  L.n = n1;
+  L.p[0] = AX1; L.w[0] = ell;
+  L.p[1] = X1; L.w[1] = ell;
+  L.p[2] = C1; L.w[2] = r; L.sgn[2] = -1.0;
+  L.wtot = 2 * ell + r;
+  M.n = n2;
+  M.p[0] = X2; M.w[0] = ell;
+  M.p[1] = BX2; M.w[1] = ell;
+  M.p[2] = C2; M.w[2] = r;
+  M.wtot = 2 * ell + r;
+  c1.n = n1; c1.p[0] = C1; c1.w[0] = r; c1.wtot = r;
+  c2.n = n2; c2.p[0] = C2; c2.w[0] = r; c2.wtot = r;
+  double *Lh, *Ll, *Mh, *Ml, *c1h, *c1l, *c2h, *c2l;
+  TRY(gram_dd(h, L, "rs_GL", &Lh, &Ll, st));
+  TRY(gram_dd(h, M, "rs_GM", &Mh, &Ml, st));
+  TRY(gram_dd(h, c1, "rs_GC1", &c1h, &c1l, st));
+  TRY(gram_dd(h, c2, "rs_GC2", &c2h, &c2l, st));
+  const int64_t w = L.wtot;
+  trace_dd_launch(Lh, Ll, Mh, Ml, w * w, sc, st);
+  trace_dd_launch(c1h, c1l, c2h, c2l, (int64_t)r * r, sc + 2, st);
+  residual_finish_launch(sc, sc + 2, sc + 4, st);
+  CK(cudaGetLastError());
+  TRY(d2h(h, out3, sc + 4, 3 * sizeof(double), st));
+  return SPK_OK;
 }
 
 // --------------------------------------------------------------------------
@@ -402,7 +477,7 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
         const double* mats[4] = {Hk, Gk, Hinv, Ginv};
         power_radius_launch(mats, 4, m, m, kPowerSteps, pwork, cs + 4 * m, st);
       }
-      CK(cudaMemcpyAsync(hcs.data(), cs, sizeof(double) * (4 * m + 4), cudaMemcpyDeviceToHost, st));
+      TRY(d2h(h, hcs.data(), cs, sizeof(double) * (4 * m + 4), st));
     }
     TRY(wait_stream(h, st, h->host_wait_s));
     CK(cudaGetLastError());
@@ -453,8 +528,7 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
       sign_combine_launch(Hk, Hinv, m, m, c, part, sgrid, st);
       sign_combine_launch(Gk, Ginv, m, m, c, part + 2 * sgrid, sgrid, st);
     }
-    CK(cudaMemcpyAsync(hpart.data(), part, sizeof(double) * 4 * sgrid, cudaMemcpyDeviceToHost, st));
-    TRY(wait_stream(h, st, h->host_wait_s));
+    TRY(d2h(h, hpart.data(), part, sizeof(double) * 4 * sgrid, st));
     double dH = 0, nH = 0, dG = 0, nG = 0;
     for (int b = 0; b < sgrid; ++b) {
       dH += hpart[2 * b];
@@ -487,8 +561,7 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
   {
     double tr[2] = {0.0, 0.0};
     diag_sums_launch(Hk, m, Gk, m, m, part, st);
-    CK(cudaMemcpyAsync(tr, part, sizeof tr, cudaMemcpyDeviceToHost, st));
-    TRY(wait_stream(h, st, h->host_wait_s));
+    TRY(d2h(h, tr, part, sizeof tr, st));
     const int negH = (int)std::lround((m - tr[0]) / 2.0), negG = (int)std::lround((m - tr[1]) / 2.0);
     if (negH != 0 || negG != 0) {
       h->spectrum_bad = true;
@@ -551,8 +624,7 @@ int jacobi_svd(spk_handle* h, double* A, int64_t lda, int M, int N, double* V, c
     for (int rd = 0; rd < rounds; ++rd)
       jacobi_round_launch(A, lda, M, N, V, N, dpairs + (size_t)rd * npairs * 2, npairs,
                           offs + (size_t)rd * npairs, st);
-    CK(cudaMemcpyAsync(hoffs.data(), offs, sizeof(double) * hoffs.size(), cudaMemcpyDeviceToHost, st));
-    TRY(wait_stream(h, st, h->host_wait_s));
+    TRY(d2h(h, hoffs.data(), offs, sizeof(double) * hoffs.size(), st));
     CK(cudaGetLastError());
     double mx = 0.0;
     for (double v : hoffs) mx = std::max(mx, v);
@@ -594,8 +666,7 @@ int truncate_Y(spk_handle* h, const double* Y, int m, double trunc_tol, uint64_t
       gemm_f64('N', 'N', m, b, k, -1.0, Q, m, C, k, 1.0, Z, m, st);
     }
     col_norms_launch(Z, m, m, b, nrm, st);
-    CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
-    TRY(wait_stream(h, st, h->host_wait_s));
+    TRY(d2h(h, hn.data(), nrm, sizeof(double) * b, st));
     double mx = 0.0;
     for (int j = 0; j < b; ++j) mx = std::max(mx, hn[j]);
     if (blk == 0) scale = mx;
@@ -606,15 +677,13 @@ int truncate_Y(spk_handle* h, const double* Y, int m, double trunc_tol, uint64_t
     // keep directions above 1e-3 * trunc_tol of the scale, normalised
     select_sv_launch(nrm, b, 1e-3 * trunc_tol * scale / std::max(mx, 1e-300), idx, f1, f2, dcount, st);
     int kb = 0;
-    CK(cudaMemcpyAsync(&kb, dcount, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
-    TRY(wait_stream(h, st, h->host_wait_s));
+    TRY(d2h(h, &kb, dcount, sizeof(int), st));
+    TRY(d2h(h, hn.data(), nrm, sizeof(double) * b, st));
     if (kb <= 0) break;
     // 1/sigma factors (f2 holds sigma^{-1/2}: square it on the device side of the gather)
     std::vector<double> hf(kb);
     std::vector<int> hidx(kb);
-    CK(cudaMemcpyAsync(hidx.data(), idx, sizeof(int) * kb, cudaMemcpyDeviceToHost, st));
-    TRY(wait_stream(h, st, h->host_wait_s));
+    TRY(d2h(h, hidx.data(), idx, sizeof(int) * kb, st));
     for (int t = 0; t < kb; ++t) hf[t] = 1.0 / hn[hidx[t]];
     CK(cudaMemcpyAsync(f1, hf.data(), sizeof(double) * kb, cudaMemcpyHostToDevice, st));
     WS(Zn, double, "tr_Zn", (size_t)m * bsz);
@@ -628,8 +697,7 @@ int truncate_Y(spk_handle* h, const double* Y, int m, double trunc_tol, uint64_t
     }
     TRY(jacobi_svd(h, Zn, m, m, kb, nullptr, st));
     col_norms_launch(Zn, m, m, kb, nrm, st);
-    CK(cudaMemcpyAsync(hn.data(), nrm, sizeof(double) * kb, cudaMemcpyDeviceToHost, st));
-    TRY(wait_stream(h, st, h->host_wait_s));
+    TRY(d2h(h, hn.data(), nrm, sizeof(double) * kb, st));
     for (int t = 0; t < kb; ++t) {
       hidx[t] = t;
       hf[t] = hn[t] > 0.0 ? 1.0 / hn[t] : 0.0;
@@ -658,8 +726,7 @@ int truncate_Y(spk_handle* h, const double* Y, int m, double trunc_tol, uint64_t
   col_norms_launch(Bt, m, m, k, sg, st);
   select_sv_launch(sg, k, trunc_tol, idx2, g1, g2, dell2, st);
   int ell = 0;
-  CK(cudaMemcpyAsync(&ell, dell2, sizeof(int), cudaMemcpyDeviceToHost, st));
-  TRY(wait_stream(h, st, h->host_wait_s));
+  TRY(d2h(h, &ell, dell2, sizeof(int), st));
   WS(Y1, double, "tr_Y1", (size_t)m * std::max(ell, 1));
   WS(Y2, double, "tr_Y2", (size_t)m * std::max(ell, 1));
   WS(QV, double, "tr_QV", (size_t)m * k);
@@ -698,9 +765,15 @@ struct Side {
   double* cwork = nullptr;   // DCT sketch: 2 n r doubles of complex work
   double* V = nullptr;       // full method: n x (maxit+1) r column-major basis
   double *wn = nullptr, *wn1 = nullptr;   // full method: n x r column-major work
+  // mixed forms with an FP64 start (spk_opts.fp64_until > 0): FP64 ring and
+  // work block of the iterations before the switch, FP64 sketch scratch
+  double* win64 = nullptr;
+  double* W64 = nullptr;
+  double* sk_scratch64 = nullptr;
   int grid = 1;
 
   TB* block(int j) const { return win + (size_t)(j % (k + 1)) * n * r; }
+  double* block64(int j) const { return win64 + (size_t)(j % (k + 1)) * n * r; }
   double* hcol(int d) const { return hband + (size_t)d * (k + 1) * r * r; }
   double* hslot(int d, int q) const { return hcol(d) + (size_t)q * r * r; }
   double* R1inv(int d) const { return r1inv + (size_t)d * r * r; }
@@ -714,6 +787,15 @@ struct Solver {
   spk_opts o;
   int r = 1;
   Side<TB, TC, TV> S[2];
+  // Precision schedule of the mixed forms: Arnoldi step d (d = 0: the
+  // initial QR of C) runs in FP64 while d < switch_d and in the form's
+  // precision from switch_d on; block U_j is FP64 iff j <= switch_d.
+  // switch_d = 0: the form's precision throughout (also the FP64 form);
+  // kNever: no switch yet (fp64_until > 0 until a check falls below it).
+  static constexpr int kNever = 0x7fffffff;
+  int switch_d = 0;
+  bool two_prec() const { return !std::is_same<TB, double>::value && o.fp64_until > 0.0; }
+  bool hi_step(int d) const { return d < switch_d; }
 
   int alloc_side(int idx, const spk_csr* op, int k, int s_rows, int sketch_id) {
     auto& sd = S[idx];
@@ -740,6 +822,10 @@ struct Solver {
   if (!sd.field) return fail(h, SPK_ERR_ALLOC, "cannot allocate %s%s", p.c_str(), name);
     SWS(win, TB, "win", (size_t)(k + 1) * sd.n * r);
     SWS(W, TC, "W", (size_t)sd.n * r);
+    if (two_prec()) {
+      SWS(win64, double, "win64", (size_t)(k + 1) * sd.n * r);
+      SWS(W64, double, "W64", (size_t)sd.n * r);
+    }
     SWS(hband, double, "hband", (size_t)(o.maxit + 2) * (k + 1) * r * r);
     SWS(r1inv, double, "r1inv", (size_t)(o.maxit + 2) * r * r);
     SWS(r2inv, double, "r2inv", (size_t)(o.maxit + 2) * r * r);
@@ -803,6 +889,9 @@ struct Solver {
           std::max({(size_t)q_update_chunks((int)mmax) * s * r, (size_t)border_chunks((int)mmax) * mmax * r,
                     (size_t)qt_dot_partial_doubles((int)mmax, r)}));
       SWS(sk_scratch, TC, "skscratch", std::max<int64_t>(1, sd.sk.npad * r));
+      if (two_prec()) {
+        SWS(sk_scratch64, double, "skscratch64", std::max<int64_t>(1, sd.sk.npad * r));
+      }
     }
 #undef SWS
     if (sketched && !sd.sk.identity) {
@@ -847,55 +936,85 @@ struct Solver {
   }
 
   int init_side(Side<TB, TC, TV>& sd, const double* C) {
+    if (hi_step(0)) return init_side_t<double, double>(sd, C, sd.win64, sd.W64, sd.sk_scratch64);
+    return init_side_t<TB, TC>(sd, C, sd.win, sd.W, sd.sk_scratch);
+  }
+
+  template <typename XB, typename XC>
+  int init_side_t(Side<TB, TC, TV>& sd, const double* C, XB* ring, XC* W, XC* skscr) {
+    XB* U1 = ring + (size_t)(1 % (sd.k + 1)) * sd.n * r;
     // U_1 = C ell^{-1} by Cholesky QR twice (Algorithm 1, first step)
-    convert_block_launch<TC>(C, sd.W, sd.n * r, st);
+    convert_block_launch<XC>(C, W, sd.n * r, st);
     WindowPtrs none{};
     none.nwin = 0;
-    update_gram_launch<TB, TC>(sd.W, sd.n, r, none, sd.hband, sd.partial, sd.grid, 1, st);
+    update_gram_launch<XB, XC>(W, sd.n, r, none, sd.hband, sd.partial, sd.grid, 1, st);
     chol_small_launch(sd.partial, sd.grid, r, sd.R1, sd.R1inv(0), h->flags, kBreakdownFloor, st);
-    scale_gram_launch<TC>(sd.W, sd.n, r, sd.R1inv(0), sd.partial, sd.grid, st);
+    scale_gram_launch<XC>(W, sd.n, r, sd.R1inv(0), sd.partial, sd.grid, st);
     chol_small_launch(sd.partial, sd.grid, r, sd.R2, sd.R2inv(0), h->flags, 1e-28, st);
     combine_small_launch(sd.R2, sd.R1, sd.ell, r, 0, st);
-    scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(0), sd.block(1), st);
+    scale_store_launch<XB, XC>(W, sd.n, r, sd.R2inv(0), U1, st);
     if (o.method != SPK_METHOD_SKETCHED) {
       // Algorithm 2 and full Arnoldi: C = U_1 beta with beta = ell
       CK(cudaMemcpyAsync(sd.beta, sd.ell, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
       if (o.method == SPK_METHOD_FULL)
-        block_to_cols_launch(reinterpret_cast<const double*>(sd.block(1)), sd.n, r, sd.V, sd.n, st);
+        block_to_cols_launch(reinterpret_cast<const double*>(U1), sd.n, r, sd.V, sd.n, st);
       return SPK_OK;
     }
     // T_1 = R factor of S U_1 (reading of Algorithm 1's first step), beta = T_1 ell
-    sketch_apply_launch<TB, TC>(sd.sk, sd.block(1), r, sd.w, sd.sk_scratch, st);
+    sketch_apply_launch<XB, XC>(sd.sk, U1, r, sd.w, skscr, st);
     sketch_qr(sd, 0);
     t_write_launch(sd.T, sd.ldT, 0, r, nullptr, nullptr, sd.tau, st);
     combine_small_launch(sd.tau, sd.ell, sd.beta, r, 0, st);
     return SPK_OK;
   }
 
-  WindowPtrs window(const Side<TB, TC, TV>& sd, int d, int* first) const {
+  template <typename XB>
+  WindowPtrs window_in(const Side<TB, TC, TV>& sd, XB* ring, int d, int* first) const {
     const int i0 = std::max(1, d - sd.k + 1);
     WindowPtrs w{};
     w.nwin = d - i0 + 1;
-    for (int q = 0; q < w.nwin; ++q) w.blk[q] = sd.block(i0 + q);
+    for (int q = 0; q < w.nwin; ++q) w.blk[q] = ring + (size_t)((i0 + q) % (sd.k + 1)) * sd.n * r;
     *first = i0;
     return w;
+  }
+  WindowPtrs window(const Side<TB, TC, TV>& sd, int d, int* first) const {
+    return window_in(sd, sd.win, d, first);
+  }
+
+  // First step in the form's precision after FP64 steps: the window blocks
+  // it reads (U_{d-k+1} .. U_d, all FP64) are rounded into the mixed ring.
+  void convert_window(Side<TB, TC, TV>& sd, int d) {
+    for (int j = std::max(1, d - sd.k + 1); j <= d; ++j)
+      convert_block_launch<TB>(sd.block64(j), sd.block(j), sd.n * r, st);
   }
 
   // Arnoldi step d for one side, up to and including U_{d+1} (no sketch).
   void arnoldi_basis(Side<TB, TC, TV>& sd, int d, bool replay) {
+    if (hi_step(d)) {
+      arnoldi_basis_t<double, double, double>(sd, d, replay, sd.win64, sd.W64, sd.op->val_dev);
+      return;
+    }
+    if (d == switch_d && switch_d > 0) convert_window(sd, d);
+    arnoldi_basis_t<TB, TC, TV>(sd, d, replay, sd.win, sd.W, sd.vals);
+  }
+
+  template <typename XB, typename XC, typename XV>
+  void arnoldi_basis_t(Side<TB, TC, TV>& sd, int d, bool replay, XB* ring, XC* W,
+                       const XV* vals) {
+    auto blk = [&](int j) { return ring + (size_t)(j % (sd.k + 1)) * sd.n * r; };
     int i0 = 0;
-    WindowPtrs win = window(sd, d, &i0);
+    WindowPtrs win = window_in(sd, ring, d, &i0);
     const int slot0 = i0 - (d - sd.k + 1);
     double* hs = sd.hslot(d, slot0);
     const spk_csr* op = sd.op;
-    const double nr = (double)sd.n * r, bB = sizeof(TB), bC = sizeof(TC), bV = sizeof(TV);
+    const double nr = (double)sd.n * r, bB = sizeof(XB), bC = sizeof(XC), bV = sizeof(XV);
     const double csr_bytes = (double)op->nnz * (bV + 4) + (double)(sd.n + 1) * 4;
     if (!replay) {
       {
         ProfScope ps(h, F_SPMM, st,
                      csr_bytes + nr * (bB + bC) + win.nwin * nr * bB,
                      2.0 * op->nnz * r + 2.0 * win.nwin * nr * r);
-        spmm_dots_launch<TB, TC, TV>(op->rowptr_dev, op->col_dev, sd.vals, sd.n, r, sd.block(d), sd.W,
+        spmm_dots_launch<XB, XC, XV>(op->rowptr_dev, op->col_dev, vals, sd.n, r, blk(d), W,
                                      win, sd.partial, sd.grid, st);
         for (int g = 0; g < win.nwin; g += 4) {
           const int nq = std::min(4, win.nwin - g);
@@ -906,29 +1025,29 @@ struct Solver {
       {
         ProfScope ps(h, F_UPDATE, st, 2 * nr * bC + win.nwin * nr * bB,
                      2.0 * win.nwin * nr * r + 2.0 * nr * r);
-        update_gram_launch<TB, TC>(sd.W, sd.n, r, win, hs, sd.partial, sd.grid, 1, st);
+        update_gram_launch<XB, XC>(W, sd.n, r, win, hs, sd.partial, sd.grid, 1, st);
         chol_small_launch(sd.partial, sd.grid, r, sd.R1, sd.R1inv(d), h->flags, kBreakdownFloor, st);
       }
       ProfScope ps(h, F_SCALE, st, 3 * nr * bC + nr * bB, 4.0 * nr * r);
-      scale_gram_launch<TC>(sd.W, sd.n, r, sd.R1inv(d), sd.partial, sd.grid, st);
+      scale_gram_launch<XC>(W, sd.n, r, sd.R1inv(d), sd.partial, sd.grid, st);
       chol_small_launch(sd.partial, sd.grid, r, sd.R2, sd.R2inv(d), h->flags, 1e-28, st);
       combine_small_launch(sd.R2, sd.R1, sd.hslot(d, sd.k), r, 0, st);
-      scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(d), sd.block(d + 1), st);
+      scale_store_launch<XB, XC>(W, sd.n, r, sd.R2inv(d), blk(d + 1), st);
     } else {
       WindowPtrs none{};
       none.nwin = 0;
       {
         ProfScope ps(h, F_SPMM, st, csr_bytes + nr * (bB + bC), 2.0 * op->nnz * r);
-        spmm_dots_launch<TB, TC, TV>(op->rowptr_dev, op->col_dev, sd.vals, sd.n, r, sd.block(d),
-                                     sd.W, none, sd.partial, sd.grid, st);
+        spmm_dots_launch<XB, XC, XV>(op->rowptr_dev, op->col_dev, vals, sd.n, r, blk(d), W, none,
+                                     sd.partial, sd.grid, st);
       }
       {
         ProfScope ps(h, F_UPDATE, st, 2 * nr * bC + win.nwin * nr * bB, 2.0 * win.nwin * nr * r);
-        update_gram_launch<TB, TC>(sd.W, sd.n, r, win, hs, sd.partial, sd.grid, 0, st);
+        update_gram_launch<XB, XC>(W, sd.n, r, win, hs, sd.partial, sd.grid, 0, st);
       }
       ProfScope ps(h, F_SCALE, st, 3 * nr * bC + nr * bB, 2.0 * nr * r);
-      scale_gram_launch<TC>(sd.W, sd.n, r, sd.R1inv(d), sd.partial, sd.grid, st);
-      scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(d), sd.block(d + 1), st);
+      scale_gram_launch<XC>(W, sd.n, r, sd.R1inv(d), sd.partial, sd.grid, st);
+      scale_store_launch<XB, XC>(W, sd.n, r, sd.R2inv(d), blk(d + 1), st);
     }
   }
 
@@ -1000,7 +1119,10 @@ struct Solver {
       ProfScope ps(h, F_SKETCH, st,
                    (double)sd.n * r * sizeof(TB) + (double)sd.n + sr8,
                    sd.sk.identity ? 0.0 : (double)sd.sk.npad * r * sd.sk.log2n2 + (double)s * sd.sk.n1 * r);
-      sketch_apply_launch<TB, TC>(sd.sk, sd.block(d + 1), r, sd.w, sd.sk_scratch, st);
+      if (hi_step(d))
+        sketch_apply_launch<double, double>(sd.sk, sd.block64(d + 1), r, sd.w, sd.sk_scratch64, st);
+      else
+        sketch_apply_launch<TB, TC>(sd.sk, sd.block(d + 1), r, sd.w, sd.sk_scratch, st);
     }
     const int nch = q_update_chunks(m);
     {
@@ -1090,8 +1212,8 @@ struct Solver {
                  S[1].ldT, hU, hV, S[0].beta, S[1].beta, o.method == SPK_METHOD_TRUNCATED, out3,
                  st);
     }
-    CK(cudaMemcpyAsync(rho3, out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    TRY(wait_stream(h, st, (o.inject & SPK_INJECT_TIMEOUT) ? 0.0 : h->host_wait_s));
+    TRY(d2h(h, rho3, out3, 3 * sizeof(double), st,
+            (o.inject & SPK_INJECT_TIMEOUT) ? 0.0 : h->host_wait_s));
     CK(cudaGetLastError());
     return SPK_OK;
   }
@@ -1134,14 +1256,21 @@ struct Solver {
       // second sweep: U_1 from C, then U_{j+1} from the stored coefficients
       int last = 0;
       for (int j = 1; j <= d; ++j) {
-        if (j - last == std::min(sd.k, kXMaxBlocks) || j == d) {
+        // chunks never straddle the precision switch: U_j is FP64 iff j <= switch_d
+        if (j - last == std::min(sd.k, kXMaxBlocks) || j == d || j == switch_d) {
           WindowPtrs blocks{};
           blocks.nwin = j - last;
-          for (int q = 0; q < blocks.nwin; ++q) blocks.blk[q] = sd.block(last + 1 + q);
+          const bool hi = last + 1 <= switch_d;
+          for (int q = 0; q < blocks.nwin; ++q)
+            blocks.blk[q] = hi ? static_cast<const void*>(sd.block64(last + 1 + q))
+                               : static_cast<const void*>(sd.block(last + 1 + q));
           ProfScope ps(h, F_XACC, st,
-                       (double)sd.n * (2.0 * 8 * ell + blocks.nwin * r * sizeof(TB)),
+                       (double)sd.n * (2.0 * 8 * ell + blocks.nwin * r * (hi ? 8 : sizeof(TB))),
                        2.0 * sd.n * ell * r * blocks.nwin);
-          x_accumulate_launch<TB>(X, sd.n, ell, r, blocks, Wf[side] + (size_t)last * r, m, st);
+          if (hi)
+            x_accumulate_launch<double>(X, sd.n, ell, r, blocks, Wf[side] + (size_t)last * r, m, st);
+          else
+            x_accumulate_launch<TB>(X, sd.n, ell, r, blocks, Wf[side] + (size_t)last * r, m, st);
           last = j;
         }
         if (j == d) break;
@@ -1152,6 +1281,12 @@ struct Solver {
   }
 
   int replay_start(Side<TB, TC, TV>& sd, const double* C) {
+    if (hi_step(0)) {
+      convert_block_launch<double>(C, sd.W64, sd.n * r, st);
+      scale_gram_launch<double>(sd.W64, sd.n, r, sd.R1inv(0), sd.partial, sd.grid, st);
+      scale_store_launch<double, double>(sd.W64, sd.n, r, sd.R2inv(0), sd.block64(1), st);
+      return SPK_OK;
+    }
     convert_block_launch<TC>(C, sd.W, sd.n * r, st);
     scale_gram_launch<TC>(sd.W, sd.n, r, sd.R1inv(0), sd.partial, sd.grid, st);
     scale_store_launch<TB, TC>(sd.W, sd.n, r, sd.R2inv(0), sd.block(1), st);
@@ -1198,6 +1333,7 @@ struct Solver {
       TRY(wait_stream(h, st, h->host_wait_s));
       C1use = c1c;
     }
+    switch_d = two_prec() ? kNever : 0;
     const int s_req = o.s;
     TRY(alloc_side(0, A, o.k_left, s_req, 0));
     TRY(alloc_side(1, BT, o.k_right, s_req, o.same_sketch ? 0 : 1));
@@ -1215,113 +1351,162 @@ struct Solver {
     int d = 0;
     bool converged = false;
     int last_good = 0;
-    double ms_proj = 0.0;
-    int next_check = o.fixed_d > 0 ? o.fixed_d : (o.check_schedule == SPK_CHECK_ADAPTIVE ? o.p : o.p);
+    double ms_proj = 0.0, ms_loop = 0.0, ms_rec = 0.0;
+    int next_check = o.fixed_d > 0 ? o.fixed_d : o.p;
     const int dmax = o.fixed_d > 0 ? std::min(o.fixed_d, o.maxit) : o.maxit;
-    for (d = 1; d <= dmax; ++d) {
-      for (int side = 0; side < 2; ++side) {
-        if (o.method == SPK_METHOD_FULL) {
-          cur = &S[side];
-          arnoldi_full(S[side], d);
-          continue;
-        }
-        arnoldi_basis(S[side], d, false);
-        if (o.method == SPK_METHOD_SKETCHED) whiten_and_border(S[side], d);
-      }
-      const bool last = d == dmax;
-      bool do_check = last;
-      if (o.fixed_d <= 0) {
-        if (o.check_schedule == SPK_CHECK_EVERY_P) do_check = do_check || (d % o.p == 0);
-        else do_check = do_check || d >= next_check;
-      }
-      if (!do_check) continue;
-      TRY(read_flags(h, st, &f));
-      CK(cudaGetLastError());
-      TRY(flags_to_status(h, f));
-      cudaEventRecord(ec0, st);
-      h->spectrum_bad = false;
-      int crc = check(d, rho3, &newton);
-      if (crc == SPK_ERR_SINGULAR_PROJECTED && h->spectrum_bad && o.fixed_d <= 0) {
-        // Eigenvalues of H~ or G~ off the open right half plane.  Past
-        // convergence the truncated basis degrades and such eigenvalues
-        // appear; the leading block of H~_d is H~_d' for every d' < d, so
-        // bisect between the last good check and d for a check that solves.
-        int lo = last_good, hi = d, found = -1;
-        while (hi - lo > 1) {
-          const int mid = lo + (hi - lo) / 2;
-          double r3[3] = {0, 0, 0};
-          h->spectrum_bad = false;
-          const int rc2 = check(mid, r3, &newton);
-          if (rc2 == SPK_OK) {
-            hd.push_back(mid);
-            hrel.push_back(r3[1]);
-            if (!std::isfinite(r3[1])) return fail(h, SPK_ERR_NONFINITE, "non-finite residual estimate at d=%d", mid);
-            if (r3[1] < o.tol) {
-              found = mid;
-              for (int e = 0; e < 3; ++e) rho3[e] = r3[e];
-              break;
-            }
-            lo = mid;
-          } else if (rc2 == SPK_ERR_SINGULAR_PROJECTED && h->spectrum_bad) {
-            hi = mid;
-          } else {
-            return rc2;
+    // The sketched estimate rho (Eq. (3.5)) measures the projected problem;
+    // with a basis recurrence in reduced precision the Arnoldi relation
+    // (Eq. (2.4)) holds only to that precision, which rho cannot see.  The
+    // mixed forms therefore check the returned factors' true residual; when
+    // it is above tol while rho is below, the iteration resumes (the replay
+    // leaves the window as the first pass left it) with a lower target for
+    // rho, at most kVerifyResumes times.
+    const bool verify = o.verify > 0 || (o.verify == 0 && o.precision != SPK_PREC_FP64);
+    constexpr int kVerifyResumes = 3;
+    double target = o.tol;
+    double true_rel = -1.0;
+    int d_start = 1;
+    for (int attempt = 0;; ++attempt) {
+      for (d = d_start; d <= dmax; ++d) {
+        for (int side = 0; side < 2; ++side) {
+          if (o.method == SPK_METHOD_FULL) {
+            cur = &S[side];
+            arnoldi_full(S[side], d);
+            continue;
           }
+          arnoldi_basis(S[side], d, false);
+          if (o.method == SPK_METHOD_SKETCHED) whiten_and_border(S[side], d);
         }
-        if (found < 0 && lo == 0) return crc;  // no solvable check at all (message kept)
-        if (found < 0) {
-          // not converged: the factors of the last solvable check
-          TRY(check(lo, rho3, &newton));
-          d = lo;
-        } else {
-          d = found;
-          converged = true;
+        const bool last = d == dmax;
+        bool do_check = last;
+        if (o.fixed_d <= 0) {
+          if (o.check_schedule == SPK_CHECK_EVERY_P) do_check = do_check || (d % o.p == 0);
+          else do_check = do_check || d >= next_check;
         }
+        if (!do_check) continue;
+        TRY(read_flags(h, st, &f));
+        CK(cudaGetLastError());
+        TRY(flags_to_status(h, f));
+        cudaEventRecord(ec0, st);
+        h->spectrum_bad = false;
+        int crc = check(d, rho3, &newton);
+        if (crc == SPK_ERR_SINGULAR_PROJECTED && h->spectrum_bad && o.fixed_d <= 0) {
+          // Eigenvalues of H~ or G~ off the open right half plane.  Past
+          // convergence the truncated basis degrades and such eigenvalues
+          // appear; the leading block of H~_d is H~_d' for every d' < d, so
+          // bisect between the last good check and d for a check that solves.
+          int lo = last_good, hi = d, found = -1;
+          while (hi - lo > 1) {
+            const int mid = lo + (hi - lo) / 2;
+            double r3[3] = {0, 0, 0};
+            h->spectrum_bad = false;
+            const int rc2 = check(mid, r3, &newton);
+            if (rc2 == SPK_OK) {
+              hd.push_back(mid);
+              hrel.push_back(r3[1]);
+              if (!std::isfinite(r3[1])) return fail(h, SPK_ERR_NONFINITE, "non-finite residual estimate at d=%d", mid);
+              if (r3[1] < target) {
+                found = mid;
+                for (int e = 0; e < 3; ++e) rho3[e] = r3[e];
+                break;
+              }
+              lo = mid;
+            } else if (rc2 == SPK_ERR_SINGULAR_PROJECTED && h->spectrum_bad) {
+              hi = mid;
+            } else {
+              return rc2;
+            }
+          }
+          if (found < 0 && lo == 0) return crc;  // no solvable check at all (message kept)
+          if (found < 0) {
+            // not converged: the factors of the last solvable check
+            TRY(check(lo, rho3, &newton));
+            d = lo;
+          } else {
+            d = found;
+            converged = true;
+          }
+          cudaEventRecord(ec1, st);
+          TRY(wait_stream(h, st, h->host_wait_s));
+          float msb = 0.f;
+          cudaEventElapsedTime(&msb, ec0, ec1);
+          ms_proj += msb;
+          // no resumption after a backtrack: the window is past d
+          attempt = kVerifyResumes;
+          break;
+        }
+        TRY(crc);
         cudaEventRecord(ec1, st);
         TRY(wait_stream(h, st, h->host_wait_s));
-        float msb = 0.f;
-        cudaEventElapsedTime(&msb, ec0, ec1);
-        ms_proj += msb;
-        break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ec0, ec1);
+        ms_proj += ms;
+        hd.push_back(d);
+        hrel.push_back(rho3[1]);
+        if (!std::isfinite(rho3[1])) return fail(h, SPK_ERR_NONFINITE, "non-finite residual estimate at d=%d", d);
+        if (o.fixed_d <= 0 && rho3[1] < target) {
+          converged = true;
+          break;
+        }
+        last_good = d;
+        // mixed forms with an FP64 start: the basis recurrence turns to the
+        // form's precision once the estimate is below fp64_until
+        if (two_prec() && switch_d == kNever && rho3[1] < o.fp64_until) switch_d = d + 1;
+        if (o.check_schedule == SPK_CHECK_ADAPTIVE && o.fixed_d <= 0)
+          next_check = next_check_adaptive(hd.data(), hrel.data(), (int)hd.size(), target, o.p, dmax);
       }
-      TRY(crc);
-      cudaEventRecord(ec1, st);
+      if (d > dmax) d = dmax;
+      cudaEventRecord(e1, st);
+      TRY(read_flags(h, st, &f));
+      TRY(flags_to_status(h, f));
+      {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_loop += ms;
+      }
+      // Y of the last check is in pj_F
+      double* Y = static_cast<double*>(h->bufs["pj_F"].p);
+      cudaEventRecord(er0, st);
+      if (o.method != SPK_METHOD_FULL) {
+        TRY(replay_start(S[0], C1use));
+        TRY(replay_start(S[1], C2));
+      }
+      TRY(recover(d, Y, out));
+      cudaEventRecord(er1, st);
       TRY(wait_stream(h, st, h->host_wait_s));
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ec0, ec1);
-      ms_proj += ms;
-      hd.push_back(d);
-      hrel.push_back(rho3[1]);
-      if (!std::isfinite(rho3[1])) return fail(h, SPK_ERR_NONFINITE, "non-finite residual estimate at d=%d", d);
-      if (o.fixed_d <= 0 && rho3[1] < o.tol) {
-        converged = true;
-        break;
+      CK(cudaGetLastError());
+      TRY(read_flags(h, st, &f));
+      TRY(flags_to_status(h, f));
+      {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, er0, er1);
+        ms_rec += ms;
       }
+      if (!verify) break;
+      double t3[3] = {0.0, 0.0, 0.0};
+      TRY(true_residual(h, A, BT, C1use, C2, r, out->X1_dev, out->X2_dev, out->rank, st, t3));
+      true_rel = t3[2];
+      if (o.fixed_d > 0 || true_rel < o.tol) break;
+      const bool can_resume = converged && d < dmax && attempt < kVerifyResumes;
+      converged = false;
+      if (!can_resume) break;
+      // resume: drop these factors, regenerate U_{d+1} and V_{d+1} (the
+      // replay stops at U_d) from the stored coefficients, and aim rho lower
+      cudaFree(out->X1_dev);
+      cudaFree(out->X2_dev);
+      out->X1_dev = out->X2_dev = nullptr;
+      out->rank = 0;
+      if (o.method != SPK_METHOD_FULL)
+        for (int side = 0; side < 2; ++side) arnoldi_basis(S[side], d, true);
+      target = std::min(target, rho3[1]) * std::max(0.1, 0.5 * o.tol / true_rel);
+      d_start = d + 1;
       last_good = d;
-      if (o.check_schedule == SPK_CHECK_ADAPTIVE && o.fixed_d <= 0)
-        next_check = next_check_adaptive(hd.data(), hrel.data(), (int)hd.size(), o.tol, o.p, dmax);
+      next_check = o.check_schedule == SPK_CHECK_ADAPTIVE
+                       ? next_check_adaptive(hd.data(), hrel.data(), (int)hd.size(), target, o.p, dmax)
+                       : d + 1;
+      cudaEventRecord(e0, st);
     }
-    if (d > dmax) d = dmax;
-    cudaEventRecord(e1, st);
-    TRY(read_flags(h, st, &f));
-    TRY(flags_to_status(h, f));
-    // Y of the last check is in pj_F
-    double* Y = static_cast<double*>(h->bufs["pj_F"].p);
-    cudaEventRecord(er0, st);
-    if (o.method != SPK_METHOD_FULL) {
-      TRY(replay_start(S[0], C1use));
-      TRY(replay_start(S[1], C2));
-    }
-    TRY(recover(d, Y, out));
-    cudaEventRecord(er1, st);
-    TRY(wait_stream(h, st, h->host_wait_s));
-    CK(cudaGetLastError());
-    TRY(read_flags(h, st, &f));
-    TRY(flags_to_status(h, f));
     h->prof.resolve();
-    float ms_loop = 0.f, ms_rec = 0.f;
-    cudaEventElapsedTime(&ms_loop, e0, e1);
-    cudaEventElapsedTime(&ms_rec, er0, er1);
     out->iters = d;
     out->converged = converged ? 1 : 0;
     out->rel_rho = rho3[1];
@@ -1338,8 +1523,10 @@ struct Solver {
                                  ? (int64_t)2 * (d + 1) * r
                                  : (int64_t)(o.k_left + 1 + o.k_right + 1) * r;
     out->ms_project = ms_proj;
-    out->ms_arnoldi = std::max(0.0, (double)ms_loop - ms_proj);
+    out->ms_arnoldi = std::max(0.0, ms_loop - ms_proj);
     out->ms_recover = ms_rec;
+    out->true_rel_res = true_rel;
+    out->switch_d = two_prec() ? (switch_d == kNever ? -1 : switch_d) : 0;
     out->status = (converged || o.fixed_d > 0) ? SPK_OK : SPK_ERR_NOT_CONVERGED;
     return out->status;
   }
@@ -1629,11 +1816,28 @@ int spk_adjoint_gradients(spk_handle* h, const spk_result* X, const spk_result* 
       trace_product_launch(M1, M2, ll, lx, sc + 1, st);
     }
     double hv[2] = {0.0, 0.0};
-    CK(cudaMemcpyAsync(hv, sc, sizeof hv, cudaMemcpyDeviceToHost, st));
-    TRY(wait_stream(h, st, h->host_wait_s));
+    TRY(d2h(h, hv, sc, sizeof hv, st));
     *dtheta = -(hv[0] + hv[1]);
   }
   TRY(wait_stream(h, st, h->host_wait_s));
+  CK(cudaGetLastError());
+  return SPK_OK;
+}
+
+int spk_true_residual(spk_handle* h, const spk_csr* A, const spk_csr* BT, const double* C1,
+                      const double* C2, int r, const spk_result* res, double* out3,
+                      void* stream) {
+  if (!h) return SPK_ERR_ARG;
+  if (!A || !BT || !C1 || !C2 || !res || !out3 || r < 1)
+    return fail(h, SPK_ERR_ARG, "spk_true_residual: null argument or r < 1");
+  if (A->nrows != res->n1 || BT->nrows != res->n2 || A->nrows != A->ncols ||
+      BT->nrows != BT->ncols)
+    return fail(h, SPK_ERR_ARG, "spk_true_residual: operator sizes differ from the result's");
+  if (res->rank < 0 || (res->rank > 0 && (!res->X1_dev || !res->X2_dev)))
+    return fail(h, SPK_ERR_ARG, "spk_true_residual: result holds no factors");
+  if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, SPK_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  TRY(true_residual(h, A, BT, C1, C2, r, res->X1_dev, res->X2_dev, res->rank, st, out3));
   CK(cudaGetLastError());
   return SPK_OK;
 }

@@ -347,6 +347,31 @@ void power_radius_launch(const double* const* M, int nmat, int m, int64_t ld, in
 // out2_dev = {trace(A), trace(B)}, A and B m x m column-major.
 void diag_sums_launch(const double* A, int64_t lda, const double* B, int64_t ldb, int m,
                       double* out2_dev, cudaStream_t st);
+// ---------------------------------------------------------------- true residual
+// Columns of a virtual n x wtot matrix P = [sgn0 P0, sgn1 P1, sgn2 P2], each
+// part row-major n x w[q] (w[q] may be 0).
+struct GramParts {
+  const double* p[3] = {nullptr, nullptr, nullptr};
+  int w[3] = {0, 0, 0};
+  double sgn[3] = {1.0, 1.0, 1.0};
+  int64_t n = 0;
+  int wtot = 0;
+};
+// G = P^T P (wtot x wtot, column-major, both triangles) in double-double:
+// G = Ghi + Glo.  tiles_dev: gram_dd_tiles(w) int2 from gram_dd_tile_list;
+// work: gram_dd_work_doubles(n, w, sm_count) doubles.
+int gram_dd_tiles(int w);
+size_t gram_dd_work_doubles(int64_t n, int w, int sm_count);
+void gram_dd_tile_list(int w, int2* host_tiles);
+void gram_dd_launch(const GramParts& P, const int2* tiles_dev, int sm_count, double* work,
+                    double* Ghi, double* Glo, cudaStream_t st);
+// out2 = double-double sum_e (Ghi + Glo)_e (Hhi + Hlo)_e over count entries.
+void trace_dd_launch(const double* Ghi, const double* Glo, const double* Hhi, const double* Hlo,
+                     int64_t count, double* out2, cudaStream_t st);
+// out3 = {sqrt(num), sqrt(den), sqrt(num / den)} of double-double squares.
+void residual_finish_launch(const double* num2, const double* den2, double* out3,
+                            cudaStream_t st);
+
 // Measured FP64 FMA rate of the device in TFLOP/s (dependent-chain probe).
 double fp64_fma_probe(int sm_count, double* scratch, cudaStream_t st);
 // out_dev[0] = trace(A B), A p x q and B q x p column-major (ld p and q).

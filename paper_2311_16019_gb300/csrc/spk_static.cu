@@ -18,14 +18,21 @@
 //
 // Set-up: the first call on a device, with that device current, resolves
 // the array's device address with cudaGetSymbolAddress (a host-side name of
-// a __device__ variable is not a device address); later calls on that
-// device reuse it.  Make that first call before any stream capture.
+// a __device__ variable is not a device address) and creates one event;
+// later calls on that device reuse both.  Every call waits on the host for
+// its stream (the row selection reads a count back, and the call returns
+// only when S X is written), so no call may be made while its stream is
+// being captured into a CUDA graph.
 //
 // Sharing: every call on a device uses the same array and leaves its
 // contents behind.  The selection counter is cleared by each call; every
 // other byte a call reads it has written earlier in the same call.  Calls
 // whose device work overlaps (different streams, or different host threads
 // without ordering) race on the array and give wrong results: order them.
+// A call that returns SPK_ERR_TIMEOUT may leave kernels queued that still
+// write the array; the event recorded at the end of each call's device work
+// makes the next call on that device wait for them first (bounded: that
+// call returns SPK_ERR_TIMEOUT too while they have not finished).
 #include "spk_internal.cuh"
 
 #include <cstdio>
@@ -48,6 +55,8 @@ static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
+// recorded after each call's last kernel: the array is free once it completes
+cudaEvent_t g_done[kMaxDevices] = {nullptr};
 
 int64_t next_pow2(int64_t n) {
   int64_t p = 1;
@@ -92,6 +101,7 @@ extern "C" int spk_sketch_apply_static(int64_t n, int32_t s, uint64_t seed, int3
     return SPK_ERR_CUDA;
   }
   unsigned char* base = nullptr;
+  cudaEvent_t done = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_scratch_addr[dev]) {
@@ -106,7 +116,31 @@ extern "C" int spk_sketch_apply_static(int64_t n, int32_t s, uint64_t seed, int3
       }
       g_scratch_addr[dev] = static_cast<unsigned char*>(p);
     }
+    if (!g_done[dev]) {
+      cudaError_t e = cudaEventCreateWithFlags(&g_done[dev], cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_done[dev] = nullptr;
+        set_err(err, errlen, "spk_sketch_apply_static: cudaEventCreate failed");
+        return SPK_ERR_CUDA;
+      }
+    }
     base = g_scratch_addr[dev];
+    done = g_done[dev];
+  }
+  // kernels of an earlier call that timed out may still use the array
+  {
+    const int w0 = spk::bounded_event_wait(done, spk::kHostWaitSeconds);
+    if (w0 == 1) {
+      set_err(err, errlen, "spk_sketch_apply_static: an earlier call's device work is still "
+                           "running on the shared array");
+      return SPK_ERR_TIMEOUT;
+    }
+    if (w0 != 0) {
+      cudaGetLastError();
+      set_err(err, errlen, "spk_sketch_apply_static: earlier device work failed");
+      return SPK_ERR_CUDA;
+    }
   }
   double* transform = reinterpret_cast<double*>(base);
   int32_t* rows = reinterpret_cast<int32_t*>(base + kTransformBytes);
@@ -117,6 +151,9 @@ extern "C" int spk_sketch_apply_static(int64_t n, int32_t s, uint64_t seed, int3
   int rc = spk::sketch_draws_launch(n, s, seed, sketch_id, rows, signs, draw, kDrawBytes, st,
                                     derr, sizeof derr);
   if (rc != SPK_OK) {
+    // the draws may have queued kernels before failing: mark their end
+    cudaEventRecord(done, st);
+    cudaGetLastError();
     set_err(err, errlen, derr);
     return rc;
   }
@@ -125,6 +162,11 @@ extern "C" int spk_sketch_apply_static(int64_t n, int32_t s, uint64_t seed, int3
   sk.rows = rows;
   sk.signs = signs;
   spk::sketch_apply_launch<double, double>(sk, X_dev, r, SX_dev, transform, st);
+  if (cudaEventRecord(done, st) != cudaSuccess) {
+    cudaGetLastError();
+    set_err(err, errlen, "spk_sketch_apply_static: cudaEventRecord failed");
+    return SPK_ERR_CUDA;
+  }
   const int w = spk::bounded_stream_wait(st, spk::kHostWaitSeconds);
   if (w == 1) {
     set_err(err, errlen, "spk_sketch_apply_static: device work did not finish");

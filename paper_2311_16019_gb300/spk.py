@@ -46,7 +46,8 @@ class Opts(C.Structure):
                 ("precision", C.c_int32), ("check_schedule", C.c_int32),
                 ("same_sketch", C.c_int32), ("fixed_d", C.c_int32), ("max_newton", C.c_int32),
                 ("inject", C.c_uint32), ("tol", C.c_double), ("trunc_tol", C.c_double),
-                ("seed", C.c_uint64), ("method", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("seed", C.c_uint64), ("method", C.c_int32), ("verify", C.c_int32),
+                ("fp64_until", C.c_double), ("reserved", C.c_int32 * 4)]
 
 
 class Result(C.Structure):
@@ -58,7 +59,7 @@ class Result(C.Structure):
                 ("hist_d_host", C.POINTER(C.c_int32)), ("hist_rel_host", C.POINTER(C.c_double)),
                 ("mem_basis_vectors", C.c_int64), ("mem_solution_vectors", C.c_int64),
                 ("ms_arnoldi", C.c_double), ("ms_project", C.c_double), ("ms_recover", C.c_double),
-                ("reserved", C.c_int32 * 8)]
+                ("true_rel_res", C.c_double), ("switch_d", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class Problem(C.Structure):
@@ -91,6 +92,7 @@ def load() -> C.CDLL:
         "spk_adjoint_gradients": (i32, [vp, P(Result), P(Result), vp, vp, C.c_int, P(Csr), P(Csr),
                                         vp, vp, P(dbl), vp]),
         "spk_result_free": (None, [P(Result)]),
+        "spk_true_residual": (i32, [vp, P(Csr), P(Csr), vp, vp, C.c_int, P(Result), P(dbl), vp]),
         "spk_sketch_draws": (i32, [vp, i64, i32, u64, i32, vp, vp, vp]),
         "spk_sketch_apply": (i32, [vp, i64, i32, u64, i32, vp, i32, vp, vp]),
         "spk_spmm": (i32, [vp, P(Csr), vp, i32, vp, vp]),
@@ -207,11 +209,14 @@ class SolveResult:
     ms_arnoldi: float
     ms_project: float
     ms_recover: float
+    true_rel_res: float = -1.0   # relative true residual when verified, else -1
+    switch_d: int = 0            # mixed forms: first iteration in mixed precision
 
 
 def make_opts(*, k=2, k_right=None, s=600, maxit=300, p=1, tol=1e-8, trunc_tol=1e-12, seed=0,
               sketch="srht", precision="fp64", check="every_p", same_sketch=False, fixed_d=0,
-              max_newton=100, inject=0, method="sketched") -> Opts:
+              max_newton=100, inject=0, method="sketched", verify=0,
+              fp64_until=0.0) -> Opts:
     """The spk_opts struct of include/spk.h from keyword options.
 
     k, k_right: truncation (window) of the left and right Krylov spaces
@@ -232,6 +237,11 @@ def make_opts(*, k=2, k_right=None, s=600, maxit=300, p=1, tol=1e-8, trunc_tol=1
     inject: SPK_INJECT_* bits (host-side fault injection, tests only).
     method: "sketched" (Algorithm 1), "truncated" (Algorithm 2) or "full"
         (full block Arnoldi, Section 2.1).
+    verify: true-residual check of the returned factors: 0 for the mixed
+        forms only, 1 always, -1 never (status NOT_CONVERGED above tol).
+    fp64_until: mixed forms: FP64 basis recurrence until a check's relative
+        estimate is below this value, the mixed precision after (0: mixed
+        from the start).
     """
     o = Opts()
     load().spk_opts_default(C.byref(o))
@@ -251,6 +261,8 @@ def make_opts(*, k=2, k_right=None, s=600, maxit=300, p=1, tol=1e-8, trunc_tol=1
     o.max_newton = max_newton
     o.inject = inject
     o.method = METHOD[method]
+    o.verify = int(verify)
+    o.fp64_until = float(fp64_until)
     return o
 
 
@@ -264,7 +276,8 @@ def _result_to_py(lib, res: Result, keep_status=(SPK_OK, SPK_ERR_NOT_CONVERGED))
     hr = [res.hist_rel_host[i] for i in range(res.n_hist)] if res.hist_rel_host else []
     return SolveResult(res.status, res.iters, res.rank, bool(res.converged), res.rel_rho, res.rho,
                        X1, X2, hd, hr, res.newton_iters, res.mem_basis_vectors,
-                       res.mem_solution_vectors, res.ms_arnoldi, res.ms_project, res.ms_recover)
+                       res.mem_solution_vectors, res.ms_arnoldi, res.ms_project, res.ms_recover,
+                       res.true_rel_res, res.switch_d)
 
 
 def _block(C_, device="cuda"):
@@ -426,6 +439,23 @@ def result_view(sol: "SolveResult") -> Result:
     res.X1_dev = sol.X1.data_ptr() if sol.X1 is not None else None
     res.X2_dev = sol.X2.data_ptr() if sol.X2 is not None else None
     return res
+
+
+def true_residual(A, BT, C1, C2, sol: "SolveResult", device: int = 0):
+    """(||A X + X B - C1 C2^T||_F, ||C1 C2^T||_F, ratio) for X = sol.X1 sol.X2^T,
+    computed on the device by spk_true_residual (BT = B^T)."""
+    h = handle(device)
+    dA = A if isinstance(A, DeviceCSR) else DeviceCSR(A)
+    dB = BT if isinstance(BT, DeviceCSR) else DeviceCSR(BT)
+    c1, c2 = _block(C1), _block(C2)
+    res = result_view(sol)
+    out = (C.c_double * 3)()
+    rc = h.lib.spk_true_residual(h.h, C.byref(dA.c), C.byref(dB.c), C.c_void_p(c1.data_ptr()),
+                                 C.c_void_p(c2.data_ptr()), c1.shape[1], C.byref(res), out,
+                                 _stream_ptr())
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+    return out[0], out[1], out[2]
 
 
 def free_raw(res: Result, device: int = 0):

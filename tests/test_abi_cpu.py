@@ -39,9 +39,11 @@ def test_struct_layout_matches_binding(lib):
 #include <stddef.h>
 #include "spk.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(spk_csr), sizeof(spk_opts), sizeof(spk_result),
-         offsetof(spk_opts, tol), offsetof(spk_result, X1_dev), offsetof(spk_result, ms_recover),
-         sizeof(spk_problem), offsetof(spk_problem, opts));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(spk_csr), sizeof(spk_opts),
+         sizeof(spk_result), offsetof(spk_opts, tol), offsetof(spk_result, X1_dev),
+         offsetof(spk_result, ms_recover), sizeof(spk_problem), offsetof(spk_problem, opts),
+         offsetof(spk_opts, verify), offsetof(spk_opts, fp64_until),
+         offsetof(spk_result, true_rel_res), offsetof(spk_result, switch_d));
   return 0;
 }
 '''
@@ -53,7 +55,9 @@ int main(void) {
         got = [int(x) for x in subprocess.check_output([exe]).split()]
     want = [ctypes.sizeof(spk.Csr), ctypes.sizeof(spk.Opts), ctypes.sizeof(spk.Result),
             spk.Opts.tol.offset, spk.Result.X1_dev.offset, spk.Result.ms_recover.offset,
-            ctypes.sizeof(spk.Problem), spk.Problem.opts.offset]
+            ctypes.sizeof(spk.Problem), spk.Problem.opts.offset, spk.Opts.verify.offset,
+            spk.Opts.fp64_until.offset, spk.Result.true_rel_res.offset,
+            spk.Result.switch_d.offset]
     assert got == want
 
 

@@ -257,6 +257,31 @@ def test_P12_memory_tables(golden_dir):
             assert AR.memory_vectors_tpkms(int(t[2]), int(t[3]), int(t[1])) == int(t[4])
 
 
+def test_true_residual_measure_resolves_cancellation():
+    """The oracle's true residual (Householder QR of both factors) against a
+    closed form in which the terms cancel to 1e-10 of their size: integer
+    operator and factors make A X1 and B^T X2 exact, and with
+    C1 = [A X1, X1, eps e1], C2 = [X2, B^T X2, e2] the residual of
+    X = X1 X2^T is exactly -eps e1 e2^T.  A Gram-trace expansion would
+    return noise of order 1e-8 of the terms here."""
+    P = I.workload("cd2d_32_r2")
+    A, BT = P.A.tocsr().copy(), P.BT.tocsr().copy()
+    A.data, BT.data = np.round(A.data), np.round(BT.data)     # integer stencils
+    rng = np.random.default_rng(3)
+    n = A.shape[0]
+    X1 = rng.integers(-50, 50, size=(n, 3)).astype(np.float64)
+    X2 = rng.integers(-50, 50, size=(n, 3)).astype(np.float64)
+    e1 = rng.integers(-3, 4, size=(n, 1)).astype(np.float64)
+    e2 = rng.integers(-3, 4, size=(n, 1)).astype(np.float64)
+    C1n, C2n = np.hstack([A @ X1, X1]), np.hstack([X2, BT @ X2])
+    big = np.linalg.norm(C1n @ C2n.T)
+    eps = 1e-10 * big / (np.linalg.norm(e1) * np.linalg.norm(e2))
+    C1, C2 = np.hstack([C1n, eps * e1]), np.hstack([C2n, e2])
+    exact = eps * np.linalg.norm(e1) * np.linalg.norm(e2) / np.linalg.norm(C1 @ C2.T)
+    got = M.true_residual(A, BT.T, C1, C2, X1, X2)
+    assert got == pytest.approx(exact, rel=1e-4)
+
+
 def test_measure_helpers_against_dense():
     rng = np.random.default_rng(0)
     X1, X2 = rng.standard_normal((50, 3)), rng.standard_normal((40, 3))
