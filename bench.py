@@ -612,6 +612,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     conv = sum(1 for g in outs if g.converged)
+    not_conv = [i for i, g in enumerate(outs) if not g.converged]
     failed = {}
     for g in outs:
         if g.X1 is None:
@@ -624,6 +625,7 @@ def run_batched(args):
                                    "tol=1e-8, p=20 adaptive", "form": form,
                        "concurrency": args.concurrency},
             "seconds_per_batch": secs / args.steps, "converged": conv, "failed": failed,
+            "not_converged": not_conv,
             "iters": [g.iters if g.X1 is not None else g.status for g in outs],
             "first_error": spk.handle().error() if failed else ""}
     print(json.dumps(line), flush=True)

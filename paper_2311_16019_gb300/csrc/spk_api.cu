@@ -135,6 +135,11 @@ struct spk_handle {
   // set by the sign iteration when it fails because of the spectrum (an
   // eigenvalue off the open right half plane, or no convergence)
   bool spectrum_bad = false;
+  // set with spectrum_bad when the iteration converged and the traces of
+  // sign(H), sign(G) counted neg_h, neg_g eigenvalues with negative real
+  // part (the iterates then hold sign(H) and sign(G))
+  bool trace_fail = false;
+  int neg_h = 0, neg_g = 0;
   // batched form: worker handles, each with its own stream and workspace
   struct Worker {
     spk_handle* h = nullptr;
@@ -565,6 +570,9 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
     const int negH = (int)std::lround((m - tr[0]) / 2.0), negG = (int)std::lround((m - tr[1]) / 2.0);
     if (negH != 0 || negG != 0) {
       h->spectrum_bad = true;
+      h->trace_fail = true;
+      h->neg_h = negH;
+      h->neg_g = negG;
       return fail(h, SPK_ERR_SINGULAR_PROJECTED,
                   "projected matrices have %d and %d eigenvalues off the open right half plane "
                   "(m=%d): the sign iteration does not apply",
@@ -578,6 +586,166 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
   } else {
     scale_matrix_launch(F, m, m, m, 0.5, st);
   }
+  return SPK_OK;
+}
+
+int jacobi_svd(spk_handle* h, double* A, int64_t lda, int M, int N, double* V, cudaStream_t st);
+
+int max_col_abs_sum(spk_handle* h, const double* A, int64_t lda, int m, cudaStream_t st,
+                    double* out) {
+  WS(cs, double, "sp_colsum", m);
+  col_abs_sums_launch(A, lda, m, m, cs, st);
+  std::vector<double> hc(m);
+  TRY(d2h(h, hc.data(), cs, sizeof(double) * m, st));
+  double mx = 0.0;
+  for (double v : hc) mx = std::max(mx, v);
+  *out = mx;
+  return SPK_OK;
+}
+
+// The part of the solution of A X + X B^T = R0 that lies in the invariant
+// subspace of A's kA eigenvalues with negative real part: X = P_A- X with
+// A X + X B^T = P_A- R0, P_A- = (I - S_A)/2 the spectral projector from
+// S_A = sign(A).  With W an orthonormal basis of range(P_A-) (range finder
+// on P_A- and one-sided Jacobi), A W = W L with L = W^T A W (kA x kA), and
+// X = W Z where L Z + Z B^T = V^T R0, V^T = W^T P_A-.  The small equation is
+// solved through the complex Schur form L = U T U^H: row i of Zt = U^H Z
+// (from the last) solves (B + t_ii I) z^T = (Rt_i - sum_{j>i} t_ij Zt_j)^T,
+// a real 2m x 2m system inverted by Gauss-Jordan; Z = Re(U Zt).  Adds X (or
+// X^T when transpose) to out (m x m, column-major).
+int minus_block(spk_handle* h, int m, const double* A, int64_t lda, const double* B, int64_t ldb,
+                const double* SA, int64_t lds, int kA, const double* R0, bool transpose,
+                double* out, uint64_t seed, cudaStream_t st) {
+  const int q = std::min(m, kA + 4);
+  WS(Om, double, "sp_Om", (size_t)m * q);
+  WS(Z0, double, "sp_Z0", (size_t)m * q);
+  WS(nrm, double, "sp_nrm", q);
+  WS(idx, int, "sp_idx", q);
+  WS(fac, double, "sp_fac", q);
+  WS(W, double, "sp_W", (size_t)m * kA);
+  WS(AW, double, "sp_AW", (size_t)m * kA);
+  WS(L, double, "sp_L", (size_t)kA * kA);
+  WS(Vt, double, "sp_Vt", (size_t)m * kA);
+  WS(R, double, "sp_R", (size_t)kA * m);
+  WS(U, double2, "sp_U", (size_t)kA * kA);
+  WS(T, double2, "sp_T", (size_t)kA * kA);
+  WS(Rt, double2, "sp_Rt", (size_t)kA * m);
+  WS(Zt, double2, "sp_Zt", (size_t)kA * m);
+  WS(Z, double, "sp_Zr", (size_t)kA * m);
+  WS(rhs, double, "sp_rhs", 2 * (size_t)m);
+  WS(x, double, "sp_x", 2 * (size_t)m);
+  const int m2 = 2 * m;
+  WS(M, double, "sp_M", (size_t)m2 * m2);
+  WS(ipiv, int32_t, "sp_ipiv", m2);
+  WS(cvec, double, "sp_cvec", 2 * (size_t)m2);
+  WS(scal, double, "sp_scal", 8);
+  WS(gpanel, double, "sp_panel", (size_t)m2 * gje_panel_width());
+  WS(gbsave, double, "sp_bsave", (size_t)m2 * gje_panel_width());
+  // range of P_A-: Z0 = (Om - S_A Om) / 2, orthogonal columns by Jacobi
+  gaussian_fill_launch(Om, (int64_t)m * q, seed, st);
+  copy_matrix_launch(Om, m, Z0, m, m, q, st);
+  gemm_f64('N', 'N', m, q, m, -0.5, SA, lds, Om, m, 0.5, Z0, m, st);
+  TRY(jacobi_svd(h, Z0, m, m, q, nullptr, st));
+  col_norms_launch(Z0, m, m, q, nrm, st);
+  std::vector<double> hn(q);
+  TRY(d2h(h, hn.data(), nrm, sizeof(double) * q, st));
+  std::vector<int> order(q);
+  for (int j = 0; j < q; ++j) order[j] = j;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return hn[a] > hn[b]; });
+  // the projector has rank kA: a clear gap after the kA-th singular value
+  if (!(hn[order[kA - 1]] > 0.0) || (q > kA && hn[order[kA]] > 1e-6 * hn[order[kA - 1]]))
+    return fail(h, SPK_ERR_SINGULAR_PROJECTED,
+                "split solve: the spectral projector's numerical rank is not %d", kA);
+  std::vector<int> hidx(kA);
+  std::vector<double> hf(kA);
+  for (int t = 0; t < kA; ++t) {
+    hidx[t] = order[t];
+    hf[t] = 1.0 / hn[order[t]];
+  }
+  CK(cudaMemcpyAsync(idx, hidx.data(), sizeof(int) * kA, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(fac, hf.data(), sizeof(double) * kA, cudaMemcpyHostToDevice, st));
+  gather_cols_launch(Z0, m, m, idx, fac, kA, W, m, st);
+  // L = W^T A W, V = P_A-^T W = (W - S_A^T W) / 2, R = V^T R0
+  gemm_f64('N', 'N', m, kA, m, 1.0, A, lda, W, m, 0.0, AW, m, st);
+  gemm_f64('T', 'N', kA, kA, m, 1.0, W, m, AW, m, 0.0, L, kA, st);
+  copy_matrix_launch(W, m, Vt, m, m, kA, st);
+  gemm_f64('T', 'N', m, kA, m, -0.5, SA, lds, W, m, 0.5, Vt, m, st);
+  gemm_f64('T', 'N', kA, m, m, 1.0, Vt, m, R0, m, 0.0, R, kA, st);
+  small_schur_launch(L, kA, kA, U, T, h->flags, st);
+  uh_times_launch(U, kA, R, kA, m, Rt, st);
+  // host copies kept alive until the stream is drained below
+  TRY(wait_stream(h, st, h->host_wait_s));
+  GjeState gs{ipiv, cvec, scal, h->flags, gpanel, gbsave};
+  for (int i = kA - 1; i >= 0; --i) {
+    row_rhs_launch(Rt, T, kA, i, Zt, m, rhs, st);
+    realify_shift_launch(B, ldb, m, T, kA, i, M, st);
+    gje_invert(M, m2, m2, gs, st);
+    gemm_f64('N', 'N', m2, 1, m2, 1.0, M, m2, rhs, m2, 0.0, x, m2, st);
+    store_row_launch(x, m, kA, i, Zt, st);
+  }
+  u_times_real_launch(U, kA, Zt, m, Z, st);
+  if (!transpose)
+    gemm_f64('N', 'N', m, m, kA, 1.0, W, m, Z, kA, 1.0, out, m, st);
+  else
+    gemm_f64('T', 'T', m, m, kA, 1.0, Z, kA, W, m, 1.0, out, m, st);
+  uint32_t f = 0;
+  TRY(read_flags(h, st, &f));
+  if (f & kFlagZeroPivot)
+    return fail(h, SPK_ERR_SINGULAR_PROJECTED,
+                "split solve: a shifted system is singular or the small Schur form did not converge");
+  return SPK_OK;
+}
+
+// H Y + Y G^T = F (m x m, column-major, ld m) when H and/or G have eigenvalues
+// off the open right half plane (Eq. (3.4) with a sketched projection whose
+// field of values left the half plane): the sign iteration alone does not
+// apply, but its iterates converged to S_H = sign(H), S_G = sign(G) with
+// kH, kG eigenvalues of negative real part (kH, kG <= kSplitMaxK).  With the
+// spectral projectors P_H+- = (I +- S_H)/2 and P_G+- likewise,
+//   Y = P_H+ Y P_G+^T + P_H+ Y P_G-^T + P_H- Y.
+// The first part solves H' Y + Y G'^T = P_H+ F P_G+^T with H' = H + c_H P_H-,
+// G' = G + c_G P_G- (c = twice the largest column sum, so that every
+// eigenvalue is moved into the right half plane; H' and H agree on the range
+// of P_H+), by the sign iteration.  The last part is minus_block on (H, G),
+// the middle one minus_block on the transposed equation (G, H).  Y to Yout.
+int split_solve(spk_handle* h, int m, const double* H, const double* G, const double* SH,
+                const double* SG, int kH, int kG, const double* F, double* Yout, int max_newton,
+                uint64_t seed, cudaStream_t st, int* iters_out) {
+  if (kH > kSplitMaxK || kG > kSplitMaxK || kH < 0 || kG < 0 || kH + kG == 0)
+    return fail(h, SPK_ERR_SINGULAR_PROJECTED,
+                "projected matrices have %d and %d eigenvalues off the open right half plane "
+                "(m=%d): more than the split solve handles (%d)", kH, kG, m, kSplitMaxK);
+  WS(H1, double, "sp_H1", (size_t)m * m);
+  WS(G1, double, "sp_G1", (size_t)m * m);
+  WS(P, double, "sp_P", (size_t)m * m);
+  WS(F1, double, "sp_F1", (size_t)m * m);
+  WS(T1, double, "sp_T1", (size_t)m * m);
+  double cH = 0.0, cG = 0.0;
+  TRY(max_col_abs_sum(h, H, m, m, st, &cH));
+  TRY(max_col_abs_sum(h, G, m, m, st, &cG));
+  cH *= 2.0;
+  cG *= 2.0;
+  // F1 = P_H+ F P_G+^T; T1 = P_H+ F (kept for the middle part)
+  sign_affine_launch(nullptr, m, 0.0, SH, m, 0.5, 1.0, m, P, m, st);
+  gemm_f64('N', 'N', m, m, m, 1.0, P, m, F, m, 0.0, T1, m, st);
+  sign_affine_launch(nullptr, m, 0.0, SG, m, 0.5, 1.0, m, P, m, st);
+  gemm_f64('N', 'T', m, m, m, 1.0, T1, m, P, m, 0.0, F1, m, st);
+  // H' = H + c_H (I - S_H)/2, G' = G + c_G (I - S_G)/2
+  sign_affine_launch(H, m, 1.0, SH, m, 0.5 * cH, -1.0, m, H1, m, st);
+  sign_affine_launch(G, m, 1.0, SG, m, 0.5 * cG, -1.0, m, G1, m, st);
+  copy_matrix_launch(F1, m, Yout, m, m, m, st);
+  h->trace_fail = false;
+  TRY(sign_solve(h, m, H1, G1, Yout, max_newton, st, iters_out));
+  if (kH > 0) TRY(minus_block(h, m, H, m, G, m, SH, m, kH, F, false, Yout, seed + 17, st));
+  if (kG > 0) {
+    // the transposed equation G X + X H^T = (P_H+ F)^T for X = (P_H+ Y P_G-^T)^T
+    WS(T1t, double, "sp_T1t", (size_t)m * m);
+    sign_affine_launch(nullptr, m, 0.0, SH, m, 0.5, 1.0, m, P, m, st);
+    gemm_f64('T', 'T', m, m, m, 1.0, F, m, P, m, 0.0, T1t, m, st);
+    TRY(minus_block(h, m, G, m, H, m, SG, m, kG, T1t, true, Yout, seed + 29, st));
+  }
+  TRY(wait_stream(h, st, h->host_wait_s));
+  CK(cudaGetLastError());
   return SPK_OK;
 }
 
@@ -1194,7 +1362,36 @@ struct Solver {
     fill_factor_launch(Rf, m, r, S[1].beta, st);
     if (o.inject & SPK_INJECT_SINGULAR)
       return fail(h, SPK_ERR_SINGULAR_PROJECTED, "injected: singular projected equation");
-    TRY(sign_solve(h, m, Hk, Gk, F, o.max_newton, st, newton_iters, Lf, Rf, r, qcap));
+    h->trace_fail = false;
+    int src = sign_solve(h, m, Hk, Gk, F, o.max_newton, st, newton_iters, Lf, Rf, r, qcap);
+    if (src == SPK_ERR_SINGULAR_PROJECTED && h->trace_fail) {
+      // eigenvalues off the open right half plane: Hk and Gk now hold sign(H~)
+      // and sign(G~); solve by spectral splitting on the original matrices
+      const int kH = h->neg_h, kG = h->neg_g;
+      WS(H0, double, "pj_H0", (size_t)m * m);
+      WS(G0, double, "pj_G0", (size_t)m * m);
+      WS(Fd, double, "pj_Fd", (size_t)m * m);
+      if (sketched || full) {
+        copy_matrix_launch(S[0].Ht, S[0].ldH, H0, m, m, m, st);
+        copy_matrix_launch(S[1].Ht, S[1].ldH, G0, m, m, m, st);
+      } else {
+        set_zero_launch(H0, (int64_t)m * m, st);
+        set_zero_launch(G0, (int64_t)m * m, st);
+        band_to_dense_launch(S[0].hband, S[0].k, r, d, H0, m, st);
+        band_to_dense_launch(S[1].hband, S[1].k, r, d, G0, m, st);
+      }
+      set_zero_launch(Lf, (int64_t)m * r, st);
+      set_zero_launch(Rf, (int64_t)m * r, st);
+      fill_factor_launch(Lf, m, r, S[0].beta, st);
+      fill_factor_launch(Rf, m, r, S[1].beta, st);
+      gemm_f64('N', 'T', m, m, r, 1.0, Lf, m, Rf, m, 0.0, Fd, m, st);
+      h->spectrum_bad = false;
+      src = split_solve(h, m, H0, G0, Hk, Gk, kH, kG, Fd, F, o.max_newton, o.seed, st,
+                        newton_iters);
+      // unsolved: let the caller fall back to an earlier check
+      if (src != SPK_OK) h->spectrum_bad = true;
+    }
+    TRY(src);
     {
       ProfScope ps(h, F_RHO, st, 16.0 * m * r, 8.0 * m * r * r);
       // the newest subdiagonal blocks: h_{d+1,d} (hband slot, or the Cholesky
@@ -1950,7 +2147,16 @@ int spk_sylvester_dense(spk_handle* h, int32_t m, const double* H, const double*
   CK(cudaMemcpyAsync(Y, F, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
   CK(cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), st));
   int it = 0;
+  h->trace_fail = false;
   int rc = sign_solve(h, m, Hk, Gk, Y, 100, st, &it);
+  if (rc == SPK_ERR_SINGULAR_PROJECTED && h->trace_fail) {
+    // eigenvalues off the open right half plane: spectral splitting (Hk, Gk
+    // hold sign(H), sign(G); the right-hand side is copied again)
+    CK(cudaMemcpyAsync(Y, F, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
+    WS(Fd, double, "sd_F", (size_t)m * m);
+    CK(cudaMemcpyAsync(Fd, F, sizeof(double) * m * m, cudaMemcpyDeviceToDevice, st));
+    rc = split_solve(h, m, H, G, Hk, Gk, h->neg_h, h->neg_g, Fd, Y, 100, 12345, st, &it);
+  }
   if (newton_iters) *newton_iters = it;
   if (rc != SPK_OK) return rc;
   TRY(wait_stream(h, st, h->host_wait_s));

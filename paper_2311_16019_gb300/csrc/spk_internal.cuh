@@ -372,6 +372,27 @@ void trace_dd_launch(const double* Ghi, const double* Glo, const double* Hhi, co
 void residual_finish_launch(const double* num2, const double* den2, double* out3,
                             cudaStream_t st);
 
+// ---------------------------------------------------------------- split solve
+// Largest number of eigenvalues off the open right half plane that the split
+// solve of the projected equation handles (k_split.cu).
+constexpr int kSplitMaxK = 16;
+// out = alpha A + beta (I + gamma S) for m x m column-major A (may be null), S
+void sign_affine_launch(const double* A, int64_t lda, double alpha, const double* S, int64_t lds,
+                        double beta, double gamma, int m, double* out, int64_t ldo,
+                        cudaStream_t st);
+// complex Schur form A = U T U^H of a real k x k matrix (k <= kSplitMaxK)
+void small_schur_launch(const double* A, int64_t lda, int k, double2* U, double2* T,
+                        uint32_t* flags, cudaStream_t st);
+void uh_times_launch(const double2* U, int k, const double* R, int64_t ldr, int64_t n,
+                     double2* Rt, cudaStream_t st);
+void row_rhs_launch(const double2* Rt, const double2* T, int k, int i, const double2* Zt,
+                    int64_t n, double* rhs, cudaStream_t st);
+void realify_shift_launch(const double* G, int64_t ldg, int n, const double2* T, int k, int i,
+                          double* M, cudaStream_t st);
+void store_row_launch(const double* x, int64_t n, int k, int i, double2* Zt, cudaStream_t st);
+void u_times_real_launch(const double2* U, int k, const double2* Zt, int64_t n, double* Z,
+                         cudaStream_t st);
+
 // Measured FP64 FMA rate of the device in TFLOP/s (dependent-chain probe).
 double fp64_fma_probe(int sm_count, double* scratch, cudaStream_t st);
 // out_dev[0] = trace(A B), A p x q and B q x p column-major (ld p and q).

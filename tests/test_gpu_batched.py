@@ -69,18 +69,46 @@ def test_batched_invalid_instance_fails_alone():
     assert outs[0].X1 is not None and outs[2].X1 is not None
 
 
-def test_projected_spectrum_off_right_half_plane_is_reported():
+def test_projected_spectrum_off_right_half_plane_parity():
     """With s = 2 d r this instance's sketched projection has an eigenvalue
-    with negative real part (the oracle's H~ has min Re = -41.6), where the
-    sign-function solve does not apply: the solver must say so, not return
-    a wrong X."""
+    with negative real part (the oracle's H~ has min Re = -41.6, G~'s
+    smallest real part is 78: no shift of Eq. (3.4) puts both in the right
+    half plane).  The spectral split solves it as the oracle's
+    Bartels-Stewart does: X within 1e-10."""
     from paper_2311_16019_gb300 import spk
+    from oracle import spkms as SP, measure as M
     P = I.batched_instances(count=4, seed=10, nmin=12, nmax=24)[2]
-    with pytest.raises(spk.SpkError) as e:
-        spk.solve(P.A, P.BT, P.C1, P.C2, k=4, s=48, maxit=12, p=12, tol=0.0, seed=11,
-                  fixed_d=12)
-    assert e.value.code == spk.SPK_ERR_SINGULAR_PROJECTED
-    assert "right half plane" in str(e.value)
+    kw = dict(k=4, s=48, maxit=12, p=12, tol=0.0, seed=11)
+    g = spk.solve(P.A, P.BT, P.C1, P.C2, fixed_d=12, **kw)
+    o = SP.spkms(P.A, P.BT, P.C1, P.C2, **kw)
+    assert np.linalg.eigvals(o["Ht"]).real.min() < 0
+    err = M.rel_error(g.X1.cpu().numpy(), g.X2.cpu().numpy(), o["X1"], o["X2"])
+    assert err < 1e-10, err
+    assert g.rho == pytest.approx(o["rho"], rel=1e-8)
+
+
+def test_spectrum_crossing_before_convergence_converges_as_oracle():
+    """Instance 38 of the 64-instance batch (n = 112^2, r = 1, s = 4000):
+    from d = 294 on one eigenvalue of H~ lies far in the left half plane
+    (-1.03e3 at d = 300) before the estimate reaches 1e-8.  Checking every
+    20 iterations, the oracle (Bartels-Stewart) converges at d = 300; the
+    device solve must too, with the true residual at tol.  The basis is
+    numerically degenerate at that d (the spurious eigenvalue is its mark),
+    so the projected solution is ill-conditioned: both X solve the equation
+    to the same residual and agree to 1e-6, not 1e-10."""
+    from paper_2311_16019_gb300 import spk
+    from oracle import spkms as SP, measure as M
+    P = I.batched_instances(count=64, seed=4)[38]
+    kw = dict(k=4, s=4000, maxit=2000, p=20, tol=1e-8, seed=4)
+    g = spk.solve(P.A, P.BT, P.C1, P.C2, **kw)
+    o = SP.spkms(P.A, P.BT, P.C1, P.C2, **kw)
+    assert o["converged"] and g.converged and g.iters == o["d"] == 300
+    err = M.rel_error(g.X1.cpu().numpy(), g.X2.cpu().numpy(), o["X1"], o["X2"])
+    tres = M.true_residual(P.A, P.B, P.C1, P.C2, g.X1.cpu().numpy(), g.X2.cpu().numpy())
+    ores = M.true_residual(P.A, P.B, P.C1, P.C2, o["X1"], o["X2"])
+    print(f"instance 38: d={g.iters}, X vs oracle {err:.2e}, true residual {tres:.2e} "
+          f"(oracle {ores:.2e})")
+    assert err < 1e-6 and tres < 2e-8 and ores < 2e-8
 
 
 def test_autotuned_concurrency_is_a_candidate_and_results_do_not_depend_on_it():

@@ -92,6 +92,48 @@ def test_sylvester_dense_against_bartels_stewart(m):
     assert it < 60
 
 
+def _spectrum_matrix(m, seed, neg):
+    """Q (T) Q^T with T block upper triangular: eigenvalues uniform in
+    [20, 200] except the given ones off the right half plane (a complex
+    c contributes the 2 x 2 block of the pair c, conj(c))."""
+    rng = np.random.default_rng(seed)
+    T = np.diag(rng.uniform(20.0, 200.0, m)) + 0.2 * np.triu(rng.standard_normal((m, m)), 2)
+    i = 0
+    for c in neg:
+        if np.iscomplex(c):
+            T[i:i + 2, i:i + 2] = [[c.real, c.imag], [-c.imag, c.real]]
+            i += 2
+        else:
+            T[i, i] = c
+            i += 1
+    Qm, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    return Qm @ T @ Qm.T
+
+
+@pytest.mark.parametrize("m,negH,negG", [(40, [-41.6], []), (120, [-5.0 + 3.0j], [-7.0]),
+                                        (300, [-13.0, -2.0 + 1.0j], [-9.0 + 4.0j, -15.0])])
+def test_sylvester_dense_off_right_half_plane(m, negH, negG):
+    """Spectra of H and G partly in the left half plane (the projected
+    matrices of a sketched basis can have that; the equation stays solvable
+    while no lambda_i + mu_j vanishes).  The sign iteration alone cannot
+    solve it; the spectral split (sign iteration on the right-half-plane
+    part, complex Schur form and shifted solves on the rest) must match
+    Bartels-Stewart.  m = 300 takes the blocked Gauss-Jordan for the 2m x 2m
+    shifted systems."""
+    H = _spectrum_matrix(m, 1, negH)
+    G = _spectrum_matrix(m, 2, negG)
+    lh, lg = np.linalg.eigvals(H), np.linalg.eigvals(G)
+    assert np.sum(lh.real < 0) == sum(2 if np.iscomplex(c) else 1 for c in negH)
+    assert np.abs(lh[:, None] + lg[None, :]).min() > 1.0
+    F = np.zeros((m, m))
+    F[:, :2] = np.random.default_rng(3).standard_normal((m, 2))
+    Y, it = spk().sylvester_dense(H, G, F)
+    Yref = sl.solve_sylvester(H, G.T, F)
+    err = np.linalg.norm(Y - Yref) / np.linalg.norm(Yref)
+    print(f"m={m}: relative difference from Bartels-Stewart {err:.2e}")
+    assert err <= 1e-10, err
+
+
 def _two_eigenvalue_matrix(m, seed, a, b):
     rng = np.random.default_rng(seed)
     Qm, _ = np.linalg.qr(rng.standard_normal((m, m)))
