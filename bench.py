@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--fixed-d", type=int, default=0,
                     help="run exactly this many iterations (small profiling cases)")
     ap.add_argument("--forms", default="fp64,mixed_fp32")
+    ap.add_argument("--engine", default="tensor", choices=["tensor", "fp64"],
+                    help="dense products of the projected solve: tensor cores (error-free "
+                         "splitting) or FP64 CUDA cores")
     ap.add_argument("--fp64-until", type=float, default=1e-4,
                     help="mixed forms: FP64 basis until the relative estimate is below this")
     ap.add_argument("--oracle-sample", default=None,
@@ -390,6 +393,7 @@ def run_spk(args, rank, world, local, pg):
         build.build()
     barrier(pg)
     spk.load()
+    spk.set_tensor_gemm(args.engine == "tensor", local)
     P = I.workload(args.workload)
     opts = solver_opts(args)
     dA, dB = spk.DeviceCSR(P.A), spk.DeviceCSR(P.BT)
@@ -549,20 +553,28 @@ def run_kernel_case(args):
     H, G = rhp(), rhp()
     F = np.zeros((m, m))
     F[:4, :4] = rng.standard_normal((4, 4))
-    spk.sylvester_dense(H, G, F)        # warm-up (workspace, first launches)
-    torch.cuda.synchronize()
-    spk.profile_enable(True)
-    t0 = time.perf_counter()
-    Y, it = spk.sylvester_dense(H, G, F)
-    torch.cuda.synchronize()
-    secs = time.perf_counter() - t0
-    prof = spk.profile_read()
-    spk.profile_enable(False)
-    fams = {k: {"ms": round(v["ms"], 2), "launches": v["launches"],
-                "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4)}
-            for k, v in prof.items() if v["ms"] > 0}
-    print(json.dumps({"kernel_case": args.kernel_case, "m": m, "newton_iters": it,
-                      "seconds": secs, "families": fams}), flush=True)
+    out = {"kernel_case": args.kernel_case, "m": m}
+    Ys = {}
+    for engine in ("fp64", "tensor"):
+        spk.set_tensor_gemm(engine == "tensor")
+        spk.sylvester_dense(H, G, F)        # warm-up (workspace, first launches)
+        torch.cuda.synchronize()
+        spk.profile_enable(True)
+        t0 = time.perf_counter()
+        Y, it = spk.sylvester_dense(H, G, F)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        prof = spk.profile_read()
+        spk.profile_enable(False)
+        Ys[engine] = Y
+        fams = {k: {"ms": round(v["ms"], 2), "launches": v["launches"],
+                    "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4)}
+                for k, v in prof.items() if v["ms"] > 0}
+        out[engine] = {"newton_iters": it, "seconds": secs, "families": fams}
+    out["tensor_vs_fp64_rel_diff"] = float(np.linalg.norm(Ys["tensor"] - Ys["fp64"]) /
+                                           np.linalg.norm(Ys["fp64"]))
+    spk.set_tensor_gemm(args.engine == "tensor")
+    print(json.dumps(out), flush=True)
 
 
 def batched_opts(P, form, maxit=2000):

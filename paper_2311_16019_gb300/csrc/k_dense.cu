@@ -739,6 +739,12 @@ void gje_update_launch(double* A, int64_t lda, int m, int k0, int nb, GjeState g
   count_launches(1);
   k_gje_prep<<<grid_for(m, 128), 128, 0, st>>>(A, lda, m, k0, nb, gs.ipiv, gs.bsave);
   copy_matrix_launch(A + (int64_t)k0 * lda, lda, gs.panel, m, m, nb, st);
+  if (gs.oz_work && ozaki_enabled(m, m, nb)) {
+    // the rank-nb update on the tensor cores (FP64 accuracy by splitting)
+    ozaki_gemm('N', 'N', m, m, nb, 1.0, gs.panel, m, gs.bsave, nb, 1.0, A, lda, gs.oz_work,
+               gs.flags, st);
+    return;
+  }
   // unused dynamic shared memory caps the GEMM at three CTAs per SM, which
   // leaves registers for the other matrix's pivot sweeps running alongside
   gemm_f64('N', 'N', m, m, nb, 1.0, gs.panel, m, gs.bsave, nb, 1.0, A, lda, st, kGemmReserve);

@@ -1,0 +1,326 @@
+// FP64 matrix product on the tcgen05 tensor cores by error-free splitting
+// (Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59 (2012); here with BF16 slices and the
+// FP32 accumulators of the tensor cores).
+//
+//   C = alpha op(A) op(B) + beta C,   op(A): M x K,  op(B): K x N,  FP64.
+//
+// Splitting.  Row i of op(A) is scaled by 2^-eA_i (eA_i: the exponent of its
+// largest magnitude, so that every scaled entry lies in (-1, 1)) and written
+// as a sum of kOzS slices, v = sum_p n_p 2^(-7 p), each n_p an integer with
+// |n_p| <= 128 (rounded to nearest, so the remainder after slice p is at most
+// 2^(-7 p - 1)); likewise column j of op(B) with eB_j.  The integers are
+// exact in BF16.  After 8 slices the remainder is below 2^-57 of the row's
+// largest entry: the splitting is exact to more than FP64's 53 bits.
+//
+// Products.  A K-chunk of 64: the product of slices p and q sums 64 products
+// of integers of at most 2^14 each, and the (at most 8) slice pairs of one
+// level L = p + q share one FP32 accumulator in tensor memory: at most 2^23
+// in magnitude, so every level sum is EXACT in FP32.  Levels 2 .. 9 (the 36
+// pairs with p + q <= 9; the pairs left out are below 2^-58 of |row| |col|
+// per product) live side by side in the 512 columns of tensor memory.  The
+// epilogue adds 2^(-7 L) D_L to FP64 accumulators held in registers, chunk
+// after chunk, and finally scales by alpha 2^(eA_i + eB_j).
+//
+// Kernels: k_oz_rowexp (the exponents), k_oz_split (slices, written in the
+// tensor cores' shared-memory operand layout: 8-row x 16-byte core matrices,
+// K-major, no swizzle), k_oz_mma (one CTA per 128 x 64 tile of C; one thread
+// issues the bulk copies of the chunk's slices and the tcgen05.mma
+// instructions, all four warps read tensor memory for the FP64 epilogue).
+#include "spk_internal.cuh"
+
+#include <algorithm>
+
+namespace spk {
+
+namespace {
+
+constexpr int kOzS = 8;          // slices per operand
+constexpr int kOzBits = 7;       // bits per slice
+constexpr int kOzTM = 128;       // tile rows (M of the MMA)
+constexpr int kOzTN = 64;        // tile columns (N of the MMA)
+constexpr int kOzKC = 64;        // K per chunk (4 MMAs of K = 16)
+constexpr int kOzLevels = 8;     // levels L = 2 .. 9
+constexpr int kOzATile = kOzTM * kOzKC * 2;   // bytes of one A slice tile (16 KB)
+constexpr int kOzBTile = kOzTN * kOzKC * 2;   // bytes of one B slice tile (8 KB)
+constexpr int kOzSmem = kOzS * (kOzATile + kOzBTile);   // 192 KB
+constexpr uint32_t kOzSbo = (kOzKC / 8) * 128;          // next 8-row group of core matrices
+constexpr uint32_t kOzLbo = 128;                        // next 8-element K group
+constexpr long kOzSpin = 1l << 26;                      // bounded mbarrier waits
+
+// Byte offset of element (i, k) inside a slice tile (K-major core matrices).
+__host__ __device__ __forceinline__ uint32_t oz_offset(int i, int k) {
+  return (uint32_t)((i >> 3) * kOzSbo + (k >> 3) * kOzLbo + (i & 7) * 16 + (k & 7) * 2);
+}
+
+// Element (i, k) of a strided view: P[i * rs + k * ks].
+struct View {
+  const double* p;
+  int64_t rs, ks;
+};
+
+// Exponent of the largest magnitude of each row of the view (rows x K):
+// 2^e > max |row|, e = 0 for a zero row.  One thread per row (rs == 1) or
+// one warp per row (ks == 1).
+__global__ void k_oz_rowexp(View v, int rows, int K, int rows_pad, int* __restrict__ e) {
+  if (v.rs == 1) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows_pad; i += gridDim.x * blockDim.x) {
+      double mx = 0.0;
+      if (i < rows)
+        for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(v.p[i + k * v.ks]));
+      int ex = 0;
+      if (mx > 0.0) frexp(mx, &ex);
+      e[i] = ex;
+    }
+  } else {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows_pad; i += warps) {
+      double mx = 0.0;
+      if (i < rows)
+        for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(v.p[i * v.rs + (int64_t)k * v.ks]));
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      int ex = 0;
+      if (mx > 0.0) frexp(mx, &ex);
+      if (lane == 0) e[i] = ex;
+    }
+  }
+}
+
+// Slices of the view: out[((p * RT + rt) * KT + kt) * tile + oz_offset(i % TR, k % KC)]
+// = n_p(i, k) for the tiles of TR rows and kOzKC columns; padding is zero.
+template <int TR>
+__global__ void k_oz_split(View v, int rows, int K, const int* __restrict__ e, int RT, int KT,
+                           __nv_bfloat16* __restrict__ out) {
+  const int64_t rows_pad = (int64_t)RT * TR, cols_pad = (int64_t)KT * kOzKC;
+  const int64_t total = rows_pad * cols_pad;
+  const int64_t tile = (int64_t)TR * kOzKC;
+  const int64_t slice = (int64_t)RT * KT * tile;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    // the view's unit-stride index runs fastest across threads
+    int64_t i, k;
+    if (v.ks == 1) {
+      i = t / cols_pad;
+      k = t - i * cols_pad;
+    } else {
+      k = t / rows_pad;
+      i = t - k * rows_pad;
+    }
+    double x = 0.0;
+    if (i < rows && k < K) x = ldexp(v.p[i * v.rs + k * v.ks], -e[i]);
+    const int rt = (int)(i / TR), kt = (int)(k / kOzKC);
+    __nv_bfloat16* o = out + ((int64_t)rt * KT + kt) * tile + oz_offset((int)(i % TR), (int)(k % kOzKC)) / 2;
+#pragma unroll
+    for (int p = 0; p < kOzS; ++p) {
+      const double t7 = x * 128.0;
+      const double n = rint(t7);
+      x = t7 - n;
+      o[p * slice] = __double2bfloat16(n);
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t oz_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(kOzLbo >> 4) << 16;
+  d |= (uint64_t)(kOzSbo >> 4) << 32;
+  d |= (uint64_t)1 << 46;     // descriptor version of tcgen05; no swizzle
+  return d;
+}
+
+__device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long it = 0; it < kOzSpin && !done; ++it) {
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  }
+  return done != 0;
+}
+
+// One CTA per 128 x 64 tile of C; 128 threads.
+__global__ void __launch_bounds__(128, 1) k_oz_mma(const uint8_t* __restrict__ As,
+                                                   const uint8_t* __restrict__ Bs,
+                                                   const int* __restrict__ eA,
+                                                   const int* __restrict__ eB, int M, int N,
+                                                   int MT, int NT, int KT, double alpha,
+                                                   double beta, double* __restrict__ C,
+                                                   int64_t ldc, uint32_t* __restrict__ flags) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + kOzS * kOzATile;
+  __shared__ __align__(8) uint64_t bar_load, bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mt = blockIdx.x, nt = blockIdx.y;
+  if (tid == 0) failed = 0;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base)), "r"(kOzLevels * kOzTN) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar_load)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar_mma)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzTN >> 3) << 17) |
+                         ((uint32_t)(kOzTM >> 4) << 24);
+  double acc[kOzTN];
+#pragma unroll
+  for (int j = 0; j < kOzTN; ++j) acc[j] = 0.0;
+  for (int kt = 0; kt < KT; ++kt) {
+    const uint32_t parity = kt & 1;
+    if (tid == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                   :: "r"(smem_u32(&bar_load)), "r"((uint32_t)kOzSmem) : "memory");
+      for (int p = 0; p < kOzS; ++p) {
+        const uint8_t* src = As + (((int64_t)p * MT + mt) * KT + kt) * kOzATile;
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(smem_u32(sA + p * kOzATile)), "l"(src), "r"((uint32_t)kOzATile),
+                        "r"(smem_u32(&bar_load)) : "memory");
+      }
+      for (int q = 0; q < kOzS; ++q) {
+        const uint8_t* src = Bs + (((int64_t)q * NT + nt) * KT + kt) * kOzBTile;
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(smem_u32(sB + q * kOzBTile)), "l"(src), "r"((uint32_t)kOzBTile),
+                        "r"(smem_u32(&bar_load)) : "memory");
+      }
+      if (!oz_wait(smem_u32(&bar_load), parity)) {
+        failed = 1;
+      } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int p = 0; p < kOzS; ++p) {
+          for (int q = 0; p + q < kOzLevels; ++q) {
+            const uint32_t d = tmem + (uint32_t)((p + q) * kOzTN);
+#pragma unroll
+            for (int ks = 0; ks < kOzKC / 16; ++ks) {
+              const uint64_t da = oz_desc(smem_u32(sA + p * kOzATile) + ks * 2 * kOzLbo);
+              const uint64_t db = oz_desc(smem_u32(sB + q * kOzBTile) + ks * 2 * kOzLbo);
+              const uint32_t accum = (p > 0 || ks > 0) ? 1u : 0u;
+              asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                           "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                           :: "r"(d), "l"(da), "l"(db), "r"(idesc), "r"(accum) : "memory");
+            }
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(smem_u32(&bar_mma)) : "memory");
+      }
+    }
+    __syncthreads();
+    if (failed) break;
+    if (!oz_wait(smem_u32(&bar_mma), parity)) {
+      if (lane == 0) failed = 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (failed) break;
+    // FP64 epilogue: row 32 warp + lane of the tile, 64 columns per level
+#pragma unroll 1
+    for (int lv = 0; lv < kOzLevels; ++lv) {
+      const double scale = ldexp(1.0, -kOzBits * (lv + 2));
+#pragma unroll
+      for (int c0 = 0; c0 < kOzTN; c0 += 16) {
+        uint32_t r[16];
+        const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(lv * kOzTN + c0);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                       "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                       "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                     : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          acc[c0 + j] = fma((double)__uint_as_float(r[j]), scale, acc[c0 + j]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (failed) {
+    if (tid == 0) atomicOr(flags, kFlagNonfinite);
+  } else {
+    const int row = mt * kOzTM + 32 * warp + lane;
+    if (row < M) {
+      const int ea = eA[row];
+#pragma unroll
+      for (int j = 0; j < kOzTN; ++j) {
+        const int col = nt * kOzTN + j;
+        if (col < N) {
+          double* c = C + (int64_t)col * ldc + row;
+          const double v = alpha * ldexp(acc[j], ea + eB[col]);
+          *c = beta == 0.0 ? v : fma(beta, *c, v);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                 :: "r"(tmem), "r"(kOzLevels * kOzTN) : "memory");
+}
+
+int oz_grid(int64_t work, int block) {
+  int64_t g = (work + block - 1) / block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+}
+
+}  // namespace
+
+size_t ozaki_work_bytes(int M, int N, int K) {
+  const int64_t MT = (M + kOzTM - 1) / kOzTM, NT = (N + kOzTN - 1) / kOzTN;
+  const int64_t KT = (K + kOzKC - 1) / kOzKC;
+  return (size_t)(kOzS * MT * KT * kOzATile + kOzS * NT * KT * kOzBTile) +
+         sizeof(int) * (size_t)(MT * kOzTM + NT * kOzTN) + 1024;
+}
+
+bool ozaki_enabled(int M, int N, int K) {
+  // below these sizes the FP64 GEMM's few CTAs finish sooner than the splitting
+  return M >= 256 && N >= 256 && K >= 64;
+}
+
+void ozaki_gemm(char ta, char tb, int M, int N, int K, double alpha, const double* A, int64_t lda,
+                const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work,
+                uint32_t* flags, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
+    attr = true;
+  }
+  const int MT = (M + kOzTM - 1) / kOzTM, NT = (N + kOzTN - 1) / kOzTN;
+  const int KT = (K + kOzKC - 1) / kOzKC;
+  uint8_t* base = static_cast<uint8_t*>(work);
+  uint8_t* As = base;
+  uint8_t* Bs = As + (size_t)kOzS * MT * KT * kOzATile;
+  int* eA = reinterpret_cast<int*>(Bs + (size_t)kOzS * NT * KT * kOzBTile);
+  int* eB = eA + (size_t)MT * kOzTM;
+  // op(A)(i, k) and B^T(j, k) = op(B)(k, j) as strided views
+  const View va = ta == 'N' ? View{A, 1, lda} : View{A, lda, 1};
+  const View vb = tb == 'N' ? View{B, ldb, 1} : View{B, 1, ldb};
+  count_launches(5);
+  k_oz_rowexp<<<oz_grid((int64_t)MT * kOzTM * (va.rs == 1 ? 1 : 32), 256), 256, 0, st>>>(
+      va, M, K, MT * kOzTM, eA);
+  k_oz_rowexp<<<oz_grid((int64_t)NT * kOzTN * (vb.rs == 1 ? 1 : 32), 256), 256, 0, st>>>(
+      vb, N, K, NT * kOzTN, eB);
+  k_oz_split<kOzTM><<<oz_grid((int64_t)MT * kOzTM * KT * kOzKC, 256), 256, 0, st>>>(
+      va, M, K, eA, MT, KT, reinterpret_cast<__nv_bfloat16*>(As));
+  k_oz_split<kOzTN><<<oz_grid((int64_t)NT * kOzTN * KT * kOzKC, 256), 256, 0, st>>>(
+      vb, N, K, eB, NT, KT, reinterpret_cast<__nv_bfloat16*>(Bs));
+  k_oz_mma<<<dim3((unsigned)MT, (unsigned)NT), 128, kOzSmem, st>>>(As, Bs, eA, eB, M, N, MT, NT,
+                                                                    KT, alpha, beta, C, ldc, flags);
+}
+
+}  // namespace spk

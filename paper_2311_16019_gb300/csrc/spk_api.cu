@@ -140,6 +140,9 @@ struct spk_handle {
   // part (the iterates then hold sign(H) and sign(G))
   bool trace_fail = false;
   int neg_h = 0, neg_g = 0;
+  // dense products of the projected solve on the tensor cores (error-free
+  // BF16 splitting) where the sizes pay; off: the FP64 CUDA-core GEMM
+  bool tensor_gemm = true;
   // batched form: worker handles, each with its own stream and workspace
   struct Worker {
     spk_handle* h = nullptr;
@@ -428,6 +431,24 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
   WS(gbsaveG, double, "sg_bsaveG", (size_t)m * gje_panel_width());
   const int sgrid = sign_combine_grid(m);
   WS(part, double, "sg_part", 4 * (size_t)sgrid);
+  // tensor-core products (error-free BF16 splitting): the two inversions'
+  // trailing updates and the right-hand side updates
+  const bool oz = h->tensor_gemm && ozaki_enabled(m, m, gje_panel_width());
+  void *ozH = nullptr, *ozG = nullptr, *ozF = nullptr;
+  if (oz) {
+    ozH = ws_get(h, "sg_ozH", ozaki_work_bytes(m, m, gje_panel_width()));
+    ozG = ws_get(h, "sg_ozG", ozaki_work_bytes(m, m, gje_panel_width()));
+    ozF = ws_get(h, "sg_ozF", ozaki_work_bytes(m, m, m));
+    if (!ozH || !ozG || !ozF) return fail(h, SPK_ERR_ALLOC, "cannot allocate tensor-core GEMM work");
+  }
+  auto gemm = [&](char ta, char tb, int M, int N, int K, double alpha, const double* A, int64_t lda,
+                  const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                  cudaStream_t s_) {
+    if (oz && ozaki_enabled(M, N, K))
+      ozaki_gemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, ozF, h->flags, s_);
+    else
+      gemm_f64(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s_);
+  };
   std::vector<double> hpart(4 * (size_t)sgrid), hcs(4 * (size_t)m + 4);
   double delta_prev = 1e300;
   bool converged = false;
@@ -438,8 +459,8 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
     {
       const double mm2 = (double)m * m;
       ProfScope ps(h, F_GJE, st, 2 * 16.0 * mm2, 2 * 2.0 * mm2 * m);
-      GjeState gh{ipiv, cvec, scalH, h->flags, gpanel, gbsave};
-      GjeState gg{ipivG, cvecG, scalG, h->flags, gpanelG, gbsaveG};
+      GjeState gh{ipiv, cvec, scalH, h->flags, gpanel, gbsave, ozH};
+      GjeState gg{ipivG, cvecG, scalG, h->flags, gpanelG, gbsaveG, ozG};
       CK(cudaEventRecord(h->ev_fork, st));
       CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
       if (gje_blocked(m, gh)) {
@@ -508,15 +529,15 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
       // the factors would outgrow their capacity: F = L R^T from here on
       const double mm2 = (double)m * m;
       ProfScope ps(h, F_GEMM, st, 8.0 * (mm2 + 2.0 * m * q), 2.0 * mm2 * q);
-      gemm_f64('N', 'T', m, m, q, 1.0, Lf, m, Rf, m, 0.0, F, m, st);
+      gemm('N', 'T', m, m, q, 1.0, Lf, m, Rf, m, 0.0, F, m, st);
       fact = false;
     }
     if (fact) {
       const double mm2 = (double)m * m;
       ProfScope ps(h, F_GEMM, st, 2 * 8.0 * (mm2 + 3.0 * m * q), 2 * 2.0 * mm2 * q);
       const double a_new = 1.0 / std::sqrt(2.0 * c), a_old = std::sqrt(0.5 * c);
-      gemm_f64('N', 'N', m, q, m, a_new, Hinv, m, Lf, m, 0.0, Lf + (size_t)q * m, m, st);
-      gemm_f64('N', 'N', m, q, m, a_new, Ginv, m, Rf, m, 0.0, Rf + (size_t)q * m, m, st);
+      gemm('N', 'N', m, q, m, a_new, Hinv, m, Lf, m, 0.0, Lf + (size_t)q * m, m, st);
+      gemm('N', 'N', m, q, m, a_new, Ginv, m, Rf, m, 0.0, Rf + (size_t)q * m, m, st);
       scale_matrix_launch(Lf, m, m, q, a_old, st);
       scale_matrix_launch(Rf, m, m, q, a_old, st);
       q *= 2;
@@ -524,8 +545,8 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
       // F <- (c/2) F + (1/(2c)) (H^{-1} F) G^{-T}
       const double mm2 = (double)m * m;
       ProfScope ps(h, F_GEMM, st, 7 * 8.0 * mm2, 4.0 * mm2 * m);
-      gemm_f64('N', 'N', m, m, m, 1.0, Hinv, m, F, m, 0.0, P, m, st);
-      gemm_f64('N', 'T', m, m, m, 0.5 / c, P, m, Ginv, m, 0.5 * c, F, m, st);
+      gemm('N', 'N', m, m, m, 1.0, Hinv, m, F, m, 0.0, P, m, st);
+      gemm('N', 'T', m, m, m, 0.5 / c, P, m, Ginv, m, 0.5 * c, F, m, st);
     }
     {
       const double mm2 = (double)m * m;
@@ -582,7 +603,7 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
   if (fact) {
     const double mm2 = (double)m * m;
     ProfScope ps(h, F_GEMM, st, 8.0 * (mm2 + 2.0 * m * q), 2.0 * mm2 * q);
-    gemm_f64('N', 'T', m, m, q, 0.5, Lf, m, Rf, m, 0.0, F, m, st);
+    gemm('N', 'T', m, m, q, 0.5, Lf, m, Rf, m, 0.0, F, m, st);
   } else {
     scale_matrix_launch(F, m, m, m, 0.5, st);
   }
@@ -1923,6 +1944,7 @@ int spk_solve_batched(spk_handle* h, int32_t count, const spk_problem* probs,
       return fail(h, SPK_ERR_CUDA, "cannot create batched worker stream");
     }
     w.h->host_wait_s = h->host_wait_s;
+    w.h->tensor_gemm = h->tensor_gemm;
     h->workers.push_back(w);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -2133,6 +2155,39 @@ int spk_spmm(spk_handle* h, const spk_csr* A, const double* X, int32_t r, double
   }
   TRY(wait_stream(h, st, h->host_wait_s));
   CK(cudaGetLastError());
+  return SPK_OK;
+}
+
+int spk_set_tensor_gemm(spk_handle* h, int32_t on) {
+  if (!h) return SPK_ERR_ARG;
+  h->tensor_gemm = on != 0;
+  for (auto& w : h->workers) w.h->tensor_gemm = h->tensor_gemm;
+  return SPK_OK;
+}
+
+int spk_dense_gemm(spk_handle* h, int32_t engine, char ta, char tb, int32_t M, int32_t N,
+                   int32_t K, double alpha, const double* A, int64_t lda, const double* B,
+                   int64_t ldb, double beta, double* C, int64_t ldc, void* stream) {
+  if (!h) return SPK_ERR_ARG;
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || (ta != 'N' && ta != 'T') ||
+      (tb != 'N' && tb != 'T') || (engine != 0 && engine != 1))
+    return fail(h, SPK_ERR_ARG, "spk_dense_gemm: bad argument");
+  if (lda < (ta == 'N' ? M : K) || ldb < (tb == 'N' ? K : N) || ldc < M)
+    return fail(h, SPK_ERR_ARG, "spk_dense_gemm: leading dimension too small");
+  if (cudaSetDevice(h->device) != cudaSuccess) return fail(h, SPK_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(h->flags, 0, sizeof(uint32_t), st));
+  if (engine == 0) {
+    gemm_f64(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+  } else {
+    WS(work, uint8_t, "oz_work", ozaki_work_bytes(M, N, K));
+    ozaki_gemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, work, h->flags, st);
+  }
+  TRY(wait_stream(h, st, h->host_wait_s));
+  CK(cudaGetLastError());
+  uint32_t f = 0;
+  TRY(read_flags(h, st, &f));
+  if (f) return fail(h, SPK_ERR_TIMEOUT, "spk_dense_gemm: a bounded wait in the tensor-core GEMM expired");
   return SPK_OK;
 }
 

@@ -306,6 +306,7 @@ struct GjeState {
   uint32_t* flags;
   double* panel = nullptr;   // m x 64 scratch (blocked path)
   double* bsave = nullptr;   // 64 x m scratch (blocked path)
+  void* oz_work = nullptr;   // ozaki_work_bytes(m, m, nb): trailing updates on the tensor cores
 };
 void gje_invert(double* A, int64_t lda, int m, GjeState gs, cudaStream_t st);
 // The blocked inversion's pieces (m > 256 with panel/bsave scratch): for
@@ -371,6 +372,17 @@ void trace_dd_launch(const double* Ghi, const double* Glo, const double* Hhi, co
 // out3 = {sqrt(num), sqrt(den), sqrt(num / den)} of double-double squares.
 void residual_finish_launch(const double* num2, const double* den2, double* out3,
                             cudaStream_t st);
+
+// ---------------------------------------------------------------- tensor-core FP64 GEMM
+// C = alpha op(A) op(B) + beta C (column-major FP64) on the tcgen05 tensor
+// cores by error-free splitting into BF16 slices (k_ozaki.cu).  work:
+// ozaki_work_bytes(M, N, K) bytes (16-byte aligned); a failed bounded wait
+// sets kFlagNonfinite in flags.  ozaki_enabled: sizes where it pays.
+size_t ozaki_work_bytes(int M, int N, int K);
+bool ozaki_enabled(int M, int N, int K);
+void ozaki_gemm(char ta, char tb, int M, int N, int K, double alpha, const double* A, int64_t lda,
+                const double* B, int64_t ldb, double beta, double* C, int64_t ldc, void* work,
+                uint32_t* flags, cudaStream_t st);
 
 // ---------------------------------------------------------------- split solve
 // Largest number of eigenvalues off the open right half plane that the split

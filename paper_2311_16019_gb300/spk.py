@@ -93,6 +93,9 @@ def load() -> C.CDLL:
                                         vp, vp, P(dbl), vp]),
         "spk_result_free": (None, [P(Result)]),
         "spk_true_residual": (i32, [vp, P(Csr), P(Csr), vp, vp, C.c_int, P(Result), P(dbl), vp]),
+        "spk_set_tensor_gemm": (i32, [vp, i32]),
+        "spk_dense_gemm": (i32, [vp, i32, C.c_char, C.c_char, i32, i32, i32, dbl, vp, i64, vp,
+                                 i64, dbl, vp, i64, vp]),
         "spk_sketch_draws": (i32, [vp, i64, i32, u64, i32, vp, vp, vp]),
         "spk_sketch_apply": (i32, [vp, i64, i32, u64, i32, vp, i32, vp, vp]),
         "spk_spmm": (i32, [vp, P(Csr), vp, i32, vp, vp]),
@@ -541,6 +544,39 @@ def sylvester_dense(H, G, F, device: int = 0):
     if rc != SPK_OK:
         raise SpkError(rc, h.error())
     return Y.t().cpu().numpy(), it.value
+
+
+def set_tensor_gemm(on: bool, device: int = 0):
+    """Projected-solve products on the tensor cores (True) or FP64 CUDA cores."""
+    h = handle(device)
+    rc = h.lib.spk_set_tensor_gemm(h.h, 1 if on else 0)
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+
+
+def dense_gemm(A, B, *, ta="N", tb="N", alpha=1.0, beta=0.0, Cin=None, engine="tensor",
+               device: int = 0):
+    """C = alpha op(A) op(B) + beta Cin in FP64 on the device (spk_dense_gemm):
+    engine "fp64" (CUDA cores) or "tensor" (tcgen05, error-free BF16 splitting).
+    A, B, Cin are numpy arrays (copied in column-major order); returns C."""
+    torch = _torch()
+    h = handle(device)
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    M, K = (A.shape if ta == "N" else A.shape[::-1])
+    K2, N = (B.shape if tb == "N" else B.shape[::-1])
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    cm = lambda X: torch.as_tensor(np.asarray(X, dtype=np.float64).T.copy(), device="cuda")
+    Ad, Bd = cm(A), cm(B)
+    Cd = cm(Cin) if Cin is not None else torch.zeros((N, M), dtype=torch.float64, device="cuda")
+    rc = h.lib.spk_dense_gemm(h.h, 0 if engine == "fp64" else 1, ta.encode(), tb.encode(), M, N,
+                              K, alpha, C.c_void_p(Ad.data_ptr()), A.shape[0],
+                              C.c_void_p(Bd.data_ptr()), B.shape[0], beta,
+                              C.c_void_p(Cd.data_ptr()), M, _stream_ptr())
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+    return Cd.t().cpu().numpy()
 
 
 def inspect(name: str, device: int = 0) -> np.ndarray:
