@@ -259,6 +259,170 @@ __global__ void __launch_bounds__(kGjePanelThreads) k_gje_panel_step(double* A, 
   if (threadIdx.x == 0) gje_record_pivot(gs, j + 1, sp, col[sp]);
 }
 
+// The whole panel [k0, k0 + nb) in one launch: CTA b owns column k0 + b for
+// all nb pivot steps, its m entries held in registers (thread t holds rows
+// t, t + 256, ...; kGjePersistRows per thread, so m <= 256 kGjePersistRows).
+// Step j needs the pivot row p_j, the pivot value and the raw pivot column
+// (column j before the row exchange); the CTA that owns column j publishes
+// them during step j - 1, right after its own update of that column: it
+// writes them to cstore / pstore / ipiv, fences, and releases ready[j - k0]
+// (= gen, a number unique to this launch).  Every other CTA acquires that
+// flag before step j, so the steps proceed with no launch in between.  The
+// arithmetic and its order are those of k_gje_first + k_gje_panel_step, so
+// the result is the same to the bit.  Each wait is bounded: on expiry the
+// CTA sets kFlagTimeout and stops (the host then reports SPK_ERR_TIMEOUT).
+// The CTAs wait on one another, so every CTA of the launch must be able to
+// run at the same time; they use little memory (no shared-memory column),
+// which leaves room beside a tensor-core GEMM CTA on every SM.
+constexpr int kGjePersistThreads = 256;
+constexpr int kGjePersistRows = 24;      // m <= 6144
+constexpr uint64_t kGjeWaitNs = 20ull * 1000000000ull;   // 20 s per wait at most
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+template <int U>
+__global__ void __launch_bounds__(kGjePersistThreads) k_gje_panel_persist(
+    double* A, int64_t ld, int m, int k0, int nb, GjeState gs, uint32_t gen) {
+  __shared__ double s_aj, s_ap, s_piv, s_cp;
+  __shared__ int s_abort;
+  __shared__ int sp;
+  __shared__ double sv;
+  const int tid = threadIdx.x;
+  const int l = k0 + blockIdx.x;
+  double* __restrict__ col = A + (int64_t)l * ld;
+  double v[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int i = tid + u * kGjePersistThreads;
+    v[u] = i < m ? col[i] : 0.0;
+  }
+  if (tid == 0) s_abort = 0;
+  // publish the pivot of column `jj` (rows jj .. m-1 searched) from v
+  auto publish = [&](int jj) {
+    double best = -1.0;
+    int bidx = m;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = tid + u * kGjePersistThreads;
+      if (i >= jj && i < m) {
+        const double a = fabs(v[u]);
+        if (a > best || (a == best && i < bidx)) { best = a; bidx = i; }
+      }
+    }
+    block_argmax_reduce(best, bidx, &sp, &sv);
+    const int p = sp;
+    double* __restrict__ cs = gs.cstore + (int64_t)(jj - k0) * m;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = tid + u * kGjePersistThreads;
+      if (i < m) __stcg(cs + i, v[u]);
+      if (i == p) s_piv = v[u];
+      if (i == jj) s_cp = v[u];
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      // the step's record: pivot row, pivot value (= raw column at p) and the
+      // raw column at jj, read by the other CTAs in one round trip
+      const double piv = s_piv;
+      double* rec = gs.pstore + 4 * (jj - k0);
+      __stcg(rec, (double)p);
+      __stcg(rec + 1, piv);
+      __stcg(rec + 2, s_cp);
+      __stcg(gs.ipiv + jj, p);
+      if (!(fabs(piv) > 1e-300) || !isfinite(piv)) atomicOr(gs.flags, kFlagZeroPivot);
+      const double ld0 = __ldcg(gs.scal);
+      __stcg(gs.scal, (jj == 0 ? 0.0 : ld0) + log(fabs(piv)));
+      __threadfence();
+      st_release_u32(gs.ready + (jj - k0), gen);
+    }
+  };
+  __syncthreads();
+  if (l == k0) publish(k0);
+  for (int j = k0; j < k0 + nb; ++j) {
+    const int q = j - k0;
+    if (tid == 0) {
+      long it = 0;
+      uint64_t t0 = 0;
+      while (ld_acquire_u32(gs.ready + q) != gen) {
+        if (++it == 64) t0 = globaltimer_ns();
+        if (it > 64) {
+          __nanosleep(64);
+          if ((it & 1023) == 0 && globaltimer_ns() - t0 > kGjeWaitNs) {
+            s_abort = 1;
+            atomicOr(gs.flags, kFlagTimeout);
+            break;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (s_abort) return;
+    const double* rec = gs.pstore + 4 * q;
+    const int p = (int)__ldcg(rec);
+    const double piv = __ldcg(rec + 1);
+    const double cp = __ldcg(rec + 2);
+    const double cj = piv;              // the raw pivot column at row p
+    const double rpiv = 1.0 / piv;
+    const double* __restrict__ c = gs.cstore + (int64_t)q * m;
+    double cv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = tid + u * kGjePersistThreads;
+      cv[u] = i < m ? __ldcg(c + i) : 0.0;
+    }
+    // rows j and p of this column (after the exchange: row j holds old row p)
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = tid + u * kGjePersistThreads;
+      if (i == p) s_aj = v[u];
+      if (i == j) s_ap = v[u];
+    }
+    __syncthreads();
+    const double aj = s_aj, ap = s_ap;
+    if (l == j) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = tid + u * kGjePersistThreads;
+        if (i < m) {
+          const double ce = (i == j) ? cj : (i == p ? cp : cv[u]);
+          v[u] = (i == j) ? rpiv : -ce * rpiv;
+        }
+      }
+    } else {
+      const double f = aj * rpiv;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = tid + u * kGjePersistThreads;
+        if (i < m) {
+          const double ce = (i == j) ? cj : (i == p ? cp : cv[u]);
+          v[u] = (i == j) ? f : fma(-ce, f, (i == p) ? ap : v[u]);
+        }
+      }
+    }
+    if (l == j + 1 && j + 1 < k0 + nb) publish(j + 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int i = tid + u * kGjePersistThreads;
+    if (i < m) col[i] = v[u];
+  }
+}
+
 // After a panel: for every column outside it, apply the panel's row
 // exchanges in order, save the pivot rows to Bsave (nb x m, column-major)
 // and zero them; panel columns get zero columns in Bsave.
@@ -282,6 +446,82 @@ __global__ void k_gje_prep(double* A, int64_t ld, int m, int k0, int nb,
     for (int q = 0; q < nb; ++q) {
       b[q] = col[k0 + q];
       col[k0 + q] = 0.0;
+    }
+  }
+}
+
+// The panel's row exchanges (rows k0 + q <-> ipiv[k0 + q], q = 0 .. nb-1, in
+// order) as one permutation: new row r = old row sp[r].  One CTA; the index
+// array lives in shared memory (m <= kGjePermMax).  Output: the rows to
+// write (the nb panel rows first, then every moved row below the panel) and
+// their source rows, *cnt of them (at most 2 nb).
+constexpr int kGjePermMax = 8192;
+
+__global__ void k_gje_perm(int m, int k0, int nb, const int32_t* __restrict__ ipiv,
+                           int32_t* __restrict__ dst, int32_t* __restrict__ src,
+                           int32_t* __restrict__ cnt) {
+  extern __shared__ int32_t sp[];
+  __shared__ int n_extra;
+  for (int r = threadIdx.x; r < m; r += blockDim.x) sp[r] = r;
+  if (threadIdx.x == 0) n_extra = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < nb; ++q) {
+      const int j = k0 + q, p = ipiv[j];
+      const int t = sp[j];
+      sp[j] = sp[p];
+      sp[p] = t;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+    dst[q] = k0 + q;
+    src[q] = sp[k0 + q];
+  }
+  for (int r = k0 + nb + threadIdx.x; r < m; r += blockDim.x) {
+    if (sp[r] != r) {
+      const int t = atomicAdd(&n_extra, 1);
+      dst[nb + t] = r;
+      src[nb + t] = sp[r];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *cnt = nb + n_extra;
+}
+
+// Every column outside the panel (one CTA per column): the permutation as a
+// gather (all loads before any store), the pivot rows to Bsave (nb x m,
+// column-major) and zeroed; panel columns get zero columns in Bsave.
+__global__ void __launch_bounds__(256) k_gje_prep_perm(double* A, int64_t ld, int m, int k0, int nb,
+                                                       const int32_t* __restrict__ dst,
+                                                       const int32_t* __restrict__ src,
+                                                       const int32_t* __restrict__ cnt,
+                                                       double* __restrict__ Bsave) {
+  const int l = blockIdx.x;
+  double* col = A + (int64_t)l * ld;
+  double* b = Bsave + (int64_t)l * nb;
+  if (l >= k0 && l < k0 + nb) {
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) b[q] = 0.0;
+    return;
+  }
+  const int n = *cnt;
+  double v[2];
+  int r[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int t = threadIdx.x + u * 256;
+    r[u] = t < n ? dst[t] : -1;
+    v[u] = t < n ? col[src[t]] : 0.0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    if (r[u] < 0) continue;
+    if (r[u] < k0 + nb) {
+      b[r[u] - k0] = v[u];
+      col[r[u]] = 0.0;
+    } else {
+      col[r[u]] = v[u];
     }
   }
 }
@@ -725,7 +965,24 @@ bool gje_blocked(int m, const GjeState& gs) {
 
 int gje_panel_width() { return kGjeNb; }
 
+bool gje_persistent_ok(int m) { return m <= kGjePersistThreads * kGjePersistRows; }
+
 void gje_panel_launch(double* A, int64_t lda, int m, int k0, int nb, GjeState gs, cudaStream_t st) {
+  if (gs.cstore && gs.pstore && gs.ready && gje_persistent_ok(m)) {
+    static std::atomic<uint32_t> gen{0};
+    const uint32_t g = gen.fetch_add(1) + 1;
+    count_launches(1);
+    const int rows = (m + kGjePersistThreads - 1) / kGjePersistThreads;
+    if (rows <= 4)
+      k_gje_panel_persist<4><<<nb, kGjePersistThreads, 0, st>>>(A, lda, m, k0, nb, gs, g);
+    else if (rows <= 8)
+      k_gje_panel_persist<8><<<nb, kGjePersistThreads, 0, st>>>(A, lda, m, k0, nb, gs, g);
+    else if (rows <= 16)
+      k_gje_panel_persist<16><<<nb, kGjePersistThreads, 0, st>>>(A, lda, m, k0, nb, gs, g);
+    else
+      k_gje_panel_persist<24><<<nb, kGjePersistThreads, 0, st>>>(A, lda, m, k0, nb, gs, g);
+    return;
+  }
   count_launches(1);
   k_gje_first<<<1, kGjeThreads, 0, st>>>(A, lda, m, k0, gs);
   count_launches(nb);
@@ -736,8 +993,16 @@ void gje_panel_launch(double* A, int64_t lda, int m, int k0, int nb, GjeState gs
 void gje_update_launch(double* A, int64_t lda, int m, int k0, int nb, GjeState gs, cudaStream_t st) {
   // every column outside the panel: the panel's row exchanges, its pivot rows
   // saved to Bsave and zeroed; then A[:, R] += Panel * Bsave[:, R]
-  count_launches(1);
-  k_gje_prep<<<grid_for(m, 128), 128, 0, st>>>(A, lda, m, k0, nb, gs.ipiv, gs.bsave);
+  if (gs.perm && m <= kGjePermMax && nb <= 256) {
+    count_launches(2);
+    k_gje_perm<<<1, 256, sizeof(int32_t) * m, st>>>(m, k0, nb, gs.ipiv, gs.perm, gs.perm + 2 * nb,
+                                                    gs.perm + 4 * nb);
+    k_gje_prep_perm<<<m, 256, 0, st>>>(A, lda, m, k0, nb, gs.perm, gs.perm + 2 * nb,
+                                       gs.perm + 4 * nb, gs.bsave);
+  } else {
+    count_launches(1);
+    k_gje_prep<<<grid_for(m, 128), 128, 0, st>>>(A, lda, m, k0, nb, gs.ipiv, gs.bsave);
+  }
   copy_matrix_launch(A + (int64_t)k0 * lda, lda, gs.panel, m, m, nb, st);
   if (gs.oz_work && ozaki_enabled(m, m, nb)) {
     // the rank-nb update on the tensor cores (FP64 accuracy by splitting)

@@ -14,14 +14,17 @@
 // exact in BF16.  After 8 slices the remainder is below 2^-57 of the row's
 // largest entry: the splitting is exact to more than FP64's 53 bits.
 //
-// Products.  A K-chunk of 64: the product of slices p and q sums 64 products
-// of integers of at most 2^14 each, and the (at most 8) slice pairs of one
-// level L = p + q share one FP32 accumulator in tensor memory: at most 2^23
-// in magnitude, so every level sum is EXACT in FP32.  Levels 2 .. 9 (the 36
+// Products.  The (at most 8) slice pairs of one level L = p + q share one
+// FP32 accumulator in tensor memory over K-ranges of 256 (four chunks of 64
+// staged through shared memory): |n_1| <= 128 and |n_p| <= 64 for p >= 2,
+// so a level sum is at most 256 (2 2^13 + 6 2^12) < 2^24 in magnitude (2^22
+// for L = 2) and every level sum is EXACT in FP32.  Levels 2 .. 9 (the 36
 // pairs with p + q <= 9; the pairs left out are below 2^-58 of |row| |col|
 // per product) live side by side in the 512 columns of tensor memory.  The
-// epilogue adds 2^(-7 L) D_L to FP64 accumulators held in registers, chunk
-// after chunk, and finally scales by alpha 2^(eA_i + eB_j).
+// epilogue adds 2^(-7 L) D_L to FP64 accumulators held in registers, range
+// after range, converting the FP32 integers to FP64 by bit operations on the
+// integer pipe (one FP64 addition per level and element), and finally
+// scales by alpha 2^(eA_i + eB_j).
 //
 // Kernels: k_oz_rowexp (the exponents), k_oz_split (slices, written in the
 // tensor cores' shared-memory operand layout: 8-row x 16-byte core matrices,
@@ -41,6 +44,7 @@ constexpr int kOzBits = 7;       // bits per slice
 constexpr int kOzTM = 128;       // tile rows (M of the MMA)
 constexpr int kOzTN = 64;        // tile columns (N of the MMA)
 constexpr int kOzKC = 64;        // K per chunk (4 MMAs of K = 16)
+constexpr int kOzEpi = 4;        // chunks accumulated in tensor memory between epilogues
 constexpr int kOzLevels = 8;     // levels L = 2 .. 9
 constexpr int kOzATile = kOzTM * kOzKC * 2;   // bytes of one A slice tile (16 KB)
 constexpr int kOzBTile = kOzTN * kOzKC * 2;   // bytes of one B slice tile (8 KB)
@@ -134,6 +138,17 @@ __device__ __forceinline__ uint64_t oz_desc(uint32_t saddr) {
   return d;
 }
 
+// x 2^sh for the FP32 bit pattern f of an integer with |x| < 2^24, built on
+// the integer pipe: FP32 exponent rebiased to FP64 (+896) and shifted by sh,
+// mantissa moved to the top of the FP64 fraction.  Exact.
+__device__ __forceinline__ double oz_f32_int_to_f64(uint32_t f, int sh) {
+  if ((f & 0x7fffffffu) == 0u) return 0.0;
+  const uint32_t e = ((f >> 23) & 0xffu) + 896u + (uint32_t)sh;
+  const uint32_t mant = f & 0x7fffffu;
+  const uint32_t hi = (f & 0x80000000u) | (e << 20) | (mant >> 3);
+  return __hiloint2double((int)hi, (int)(mant << 29));
+}
+
 __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity) {
   uint32_t done = 0;
   for (long it = 0; it < kOzSpin && !done; ++it) {
@@ -201,6 +216,7 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const uint8_t* __restrict__ A
         failed = 1;
       } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const bool range_start = (kt % kOzEpi) == 0;
         for (int p = 0; p < kOzS; ++p) {
           for (int q = 0; p + q < kOzLevels; ++q) {
             const uint32_t d = tmem + (uint32_t)((p + q) * kOzTN);
@@ -208,7 +224,7 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const uint8_t* __restrict__ A
             for (int ks = 0; ks < kOzKC / 16; ++ks) {
               const uint64_t da = oz_desc(smem_u32(sA + p * kOzATile) + ks * 2 * kOzLbo);
               const uint64_t db = oz_desc(smem_u32(sB + q * kOzBTile) + ks * 2 * kOzLbo);
-              const uint32_t accum = (p > 0 || ks > 0) ? 1u : 0u;
+              const uint32_t accum = (p > 0 || ks > 0 || !range_start) ? 1u : 0u;
               asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
                            :: "r"(d), "l"(da), "l"(db), "r"(idesc), "r"(accum) : "memory");
@@ -227,10 +243,12 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const uint8_t* __restrict__ A
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (failed) break;
+    // the level sums stay in tensor memory until the end of a 256-wide range
+    if ((kt % kOzEpi) != kOzEpi - 1 && kt != KT - 1) continue;
     // FP64 epilogue: row 32 warp + lane of the tile, 64 columns per level
 #pragma unroll 1
     for (int lv = 0; lv < kOzLevels; ++lv) {
-      const double scale = ldexp(1.0, -kOzBits * (lv + 2));
+      const int sh = -kOzBits * (lv + 2);
 #pragma unroll
       for (int c0 = 0; c0 < kOzTN; c0 += 16) {
         uint32_t r[16];
@@ -242,15 +260,14 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const uint8_t* __restrict__ A
                      : "r"(ta));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          acc[c0 + j] = fma((double)__uint_as_float(r[j]), scale, acc[c0 + j]);
+        for (int j = 0; j < 16; ++j) acc[c0 + j] += oz_f32_int_to_f64(r[j], sh);
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
   }
   if (failed) {
-    if (tid == 0) atomicOr(flags, kFlagNonfinite);
+    if (tid == 0) atomicOr(flags, kFlagTimeout);
   } else {
     const int row = mt * kOzTM + 32 * warp + lane;
     if (row < M) {

@@ -271,6 +271,8 @@ int read_flags(spk_handle* h, cudaStream_t st, uint32_t* out) {
 }
 
 int flags_to_status(spk_handle* h, uint32_t f) {
+  if (f & kFlagTimeout)
+    return fail(h, SPK_ERR_TIMEOUT, "a bounded device-side wait expired (a kernel gave up)");
   if (f & kFlagNonfinite) return fail(h, SPK_ERR_NONFINITE, "non-finite value in a reduction");
   if (f & kFlagBreakdown)
     return fail(h, SPK_ERR_BREAKDOWN, "rank-deficient block in a Cholesky QR (Gram pivot <= 1e-14 trace)");
@@ -441,6 +443,25 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
     ozF = ws_get(h, "sg_ozF", ozaki_work_bytes(m, m, m));
     if (!ozH || !ozG || !ozF) return fail(h, SPK_ERR_ALLOC, "cannot allocate tensor-core GEMM work");
   }
+  // one launch per Gauss-Jordan panel: published pivot columns, pivot values
+  // and ready flags for each of the two concurrent inversions
+  const int nbw = gje_panel_width();
+  double *cstH = nullptr, *cstG = nullptr, *pstH = nullptr, *pstG = nullptr;
+  uint32_t *rdyH = nullptr, *rdyG = nullptr;
+  if (gje_persistent_ok(m)) {
+    cstH = static_cast<double*>(ws_get(h, "sg_cstH", sizeof(double) * (size_t)m * nbw));
+    cstG = static_cast<double*>(ws_get(h, "sg_cstG", sizeof(double) * (size_t)m * nbw));
+    pstH = static_cast<double*>(ws_get(h, "sg_pstH", sizeof(double) * 4 * nbw));
+    pstG = static_cast<double*>(ws_get(h, "sg_pstG", sizeof(double) * 4 * nbw));
+    rdyH = static_cast<uint32_t*>(ws_get(h, "sg_rdyH", sizeof(uint32_t) * nbw));
+    rdyG = static_cast<uint32_t*>(ws_get(h, "sg_rdyG", sizeof(uint32_t) * nbw));
+    if (!cstH || !cstG || !pstH || !pstG || !rdyH || !rdyG)
+      return fail(h, SPK_ERR_ALLOC, "cannot allocate Gauss-Jordan panel work");
+    CK(cudaMemsetAsync(rdyH, 0, sizeof(uint32_t) * nbw, st));
+    CK(cudaMemsetAsync(rdyG, 0, sizeof(uint32_t) * nbw, st));
+  }
+  WS(permH, int32_t, "sg_permH", 4 * (size_t)nbw + 1);
+  WS(permG, int32_t, "sg_permG", 4 * (size_t)nbw + 1);
   auto gemm = [&](char ta, char tb, int M, int N, int K, double alpha, const double* A, int64_t lda,
                   const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
                   cudaStream_t s_) {
@@ -459,8 +480,8 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
     {
       const double mm2 = (double)m * m;
       ProfScope ps(h, F_GJE, st, 2 * 16.0 * mm2, 2 * 2.0 * mm2 * m);
-      GjeState gh{ipiv, cvec, scalH, h->flags, gpanel, gbsave, ozH};
-      GjeState gg{ipivG, cvecG, scalG, h->flags, gpanelG, gbsaveG, ozG};
+      GjeState gh{ipiv, cvec, scalH, h->flags, gpanel, gbsave, ozH, cstH, pstH, rdyH, permH};
+      GjeState gg{ipivG, cvecG, scalG, h->flags, gpanelG, gbsaveG, ozG, cstG, pstG, rdyG, permG};
       CK(cudaEventRecord(h->ev_fork, st));
       CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
       if (gje_blocked(m, gh)) {
@@ -509,6 +530,11 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
     CK(cudaGetLastError());
     uint32_t f = 0;
     TRY(read_flags(h, st, &f));
+    if (f & kFlagTimeout) {
+      *iters_out = it;
+      return fail(h, SPK_ERR_TIMEOUT, "a bounded device-side wait expired in sign iteration %d "
+                  "(m=%d)", it, m);
+    }
     if (f & kFlagZeroPivot) {
       *iters_out = it;
       return fail(h, SPK_ERR_SINGULAR_PROJECTED, "zero pivot in sign iteration %d (m=%d)", it, m);

@@ -24,6 +24,7 @@ enum : uint32_t {
   kFlagBreakdown = 1u << 0,
   kFlagNonfinite = 1u << 1,
   kFlagZeroPivot = 1u << 2,
+  kFlagTimeout = 1u << 3,     // a bounded device-side wait gave up
 };
 
 // Number of kernel launches issued by the library since it was loaded.
@@ -307,7 +308,17 @@ struct GjeState {
   double* panel = nullptr;   // m x 64 scratch (blocked path)
   double* bsave = nullptr;   // 64 x m scratch (blocked path)
   void* oz_work = nullptr;   // ozaki_work_bytes(m, m, nb): trailing updates on the tensor cores
+  // one launch per panel (gje_persistent_ok): the published pivot columns
+  // (nb x m), per-step records (4 nb: pivot row, pivot value, raw column at
+  // the step's row) and ready flags (nb, zeroed once)
+  double* cstore = nullptr;
+  double* pstore = nullptr;
+  uint32_t* ready = nullptr;
+  // the panel's row exchanges as one gather: 4 nb + 1 ints (destination rows,
+  // source rows, count)
+  int32_t* perm = nullptr;
 };
+bool gje_persistent_ok(int m);
 void gje_invert(double* A, int64_t lda, int m, GjeState gs, cudaStream_t st);
 // The blocked inversion's pieces (m > 256 with panel/bsave scratch): for
 // k0 = 0, nb, 2 nb, ...: gje_panel_launch (pivot sweeps of columns
@@ -377,7 +388,7 @@ void residual_finish_launch(const double* num2, const double* den2, double* out3
 // C = alpha op(A) op(B) + beta C (column-major FP64) on the tcgen05 tensor
 // cores by error-free splitting into BF16 slices (k_ozaki.cu).  work:
 // ozaki_work_bytes(M, N, K) bytes (16-byte aligned); a failed bounded wait
-// sets kFlagNonfinite in flags.  ozaki_enabled: sizes where it pays.
+// sets kFlagTimeout in flags.  ozaki_enabled: sizes where it pays.
 size_t ozaki_work_bytes(int M, int N, int K);
 bool ozaki_enabled(int M, int N, int K);
 void ozaki_gemm(char ta, char tb, int M, int N, int K, double alpha, const double* A, int64_t lda,
