@@ -382,6 +382,49 @@ __global__ void k_cols_to_block(const double* __restrict__ V, int64_t ldv, int64
 
 }  // namespace
 
+// P[i + (c0 + a) * ldp] = U[i * r + a]: block columns into an FP64 panel
+template <typename TB>
+__global__ void k_block_to_panel(const TB* __restrict__ U, int64_t n, int r,
+                                 double* __restrict__ P, int64_t ldp) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * r;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / n, i = e - a * n;
+    P[i + a * ldp] = (double)Store<TB>::ld(U + i * r + a);
+  }
+}
+
+template <typename TB>
+void block_to_panel_launch(const TB* U, int64_t n, int r, double* P, int64_t ldp, cudaStream_t st) {
+  count_launches(1);
+  k_block_to_panel<TB><<<default_grid(n * r), 256, 0, st>>>(U, n, r, P, ldp);
+}
+
+// X (n x ell row-major) = Xcm (n x ell column-major), through 32 x 32 tiles
+__global__ void k_cols_to_rows(const double* __restrict__ Xcm, int64_t n, int ell,
+                               double* __restrict__ X) {
+  __shared__ double tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int cc = ty; cc < 32; cc += 8) {
+    const int c = c0 + cc;
+    const int64_t i = i0 + tx;
+    tile[cc][tx] = (c < ell && i < n) ? Xcm[(int64_t)c * n + i] : 0.0;
+  }
+  __syncthreads();
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int64_t i = i0 + ii;
+    const int c = c0 + tx;
+    if (i < n && c < ell) X[i * ell + c] = tile[tx][ii];
+  }
+}
+
+void cols_to_rows_launch(const double* Xcm, int64_t n, int ell, double* X, cudaStream_t st) {
+  count_launches(1);
+  k_cols_to_rows<<<dim3((unsigned)((n + 31) / 32), (unsigned)((ell + 31) / 32)), 256, 0, st>>>(
+      Xcm, n, ell, X);
+}
+
 void block_to_cols_launch(const double* B, int64_t n, int r, double* V, int64_t ldv,
                           cudaStream_t st) {
   count_launches(1);
@@ -519,7 +562,8 @@ void combine_small_launch(const double* A, const double* B, double* C, int r, in
                                            cudaStream_t);                                       \
   template void x_accumulate_launch<TB>(double*, int64_t, int, int, WindowPtrs, const double*,  \
                                         int64_t, cudaStream_t);                                 \
-  template void convert_block_launch<TB>(const double*, TB*, int64_t, cudaStream_t);
+  template void convert_block_launch<TB>(const double*, TB*, int64_t, cudaStream_t);         \
+  template void block_to_panel_launch<TB>(const TB*, int64_t, int, double*, int64_t, cudaStream_t);
 SPK_INST(double, double, double)
 SPK_INST(float, float, float)
 SPK_INST(__nv_bfloat16, float, float)

@@ -94,34 +94,51 @@ __global__ void k_oz_rowexp(View v, int rows, int K, int rows_pad, int* __restri
 
 // Slices of the view: out[((p * RT + rt) * KT + kt) * tile + oz_offset(i % TR, k % KC)]
 // = n_p(i, k) for the tiles of TR rows and kOzKC columns; padding is zero.
+// One thread per row and group of 8 consecutive k (one 16-byte row of a
+// core matrix): 8 loads, and one 16-byte store per slice.
 template <int TR>
 __global__ void k_oz_split(View v, int rows, int K, const int* __restrict__ e, int RT, int KT,
                            __nv_bfloat16* __restrict__ out) {
-  const int64_t rows_pad = (int64_t)RT * TR, cols_pad = (int64_t)KT * kOzKC;
-  const int64_t total = rows_pad * cols_pad;
+  const int64_t rows_pad = (int64_t)RT * TR, groups = (int64_t)KT * (kOzKC / 8);
+  const int64_t total = rows_pad * groups;
   const int64_t tile = (int64_t)TR * kOzKC;
   const int64_t slice = (int64_t)RT * KT * tile;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    // the view's unit-stride index runs fastest across threads
-    int64_t i, k;
+    // consecutive threads take consecutive rows (coalesced when the view's
+    // rows are unit-stride) or consecutive groups of a row (when k is)
+    int64_t i, g;
     if (v.ks == 1) {
-      i = t / cols_pad;
-      k = t - i * cols_pad;
+      i = t / groups;
+      g = t - i * groups;
     } else {
-      k = t / rows_pad;
-      i = t - k * rows_pad;
+      g = t / rows_pad;
+      i = t - g * rows_pad;
     }
-    double x = 0.0;
-    if (i < rows && k < K) x = ldexp(v.p[i * v.rs + k * v.ks], -e[i]);
-    const int rt = (int)(i / TR), kt = (int)(k / kOzKC);
-    __nv_bfloat16* o = out + ((int64_t)rt * KT + kt) * tile + oz_offset((int)(i % TR), (int)(k % kOzKC)) / 2;
+    const int64_t k0 = g * 8;
+    double x[8];
+    const int ei = i < rows ? e[i] : 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t k = k0 + u;
+      x[u] = (i < rows && k < K) ? ldexp(v.p[i * v.rs + k * v.ks], -ei) : 0.0;
+    }
+    const int rt = (int)(i / TR), kt = (int)(k0 / kOzKC);
+    uint4* o = reinterpret_cast<uint4*>(out + ((int64_t)rt * KT + kt) * tile +
+                                        oz_offset((int)(i % TR), (int)(k0 % kOzKC)) / 2);
 #pragma unroll
     for (int p = 0; p < kOzS; ++p) {
-      const double t7 = x * 128.0;
-      const double n = rint(t7);
-      x = t7 - n;
-      o[p * slice] = __double2bfloat16(n);
+      uint32_t w[4];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        const double t0 = x[u] * 128.0, t1 = x[u + 1] * 128.0;
+        const double n0 = rint(t0), n1 = rint(t1);
+        x[u] = t0 - n0;
+        x[u + 1] = t1 - n1;
+        const __nv_bfloat162 b = __floats2bfloat162_rn((float)n0, (float)n1);
+        w[u / 2] = *reinterpret_cast<const uint32_t*>(&b);
+      }
+      o[p * (slice / 8)] = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }

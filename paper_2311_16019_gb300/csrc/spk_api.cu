@@ -1496,6 +1496,39 @@ struct Solver {
         gemm_f64('T', 'T', ell, (int)sd.n, m, 1.0, Wf[side], m, sd.V, sd.n, 0.0, X, ell, st);
         continue;
       }
+      if (h->tensor_gemm && sd.n >= 4096 && ell >= 8) {
+        // second sweep on the tensor cores: the regenerated blocks fill a
+        // panel of kXPanelCols FP64 columns; each full panel adds
+        // P W[rows] to a column-major accumulator (tcgen05, error-free
+        // splitting), transposed into X at the end
+        const int bpp = std::max(1, kXPanelCols / r);
+        const int pc = bpp * r;
+        WS(Pn, double, "x_panel", (size_t)sd.n * pc);
+        WS(Xcm, double, "x_colmajor", (size_t)sd.n * ell);
+        WS(ozw, uint8_t, "x_ozaki", ozaki_work_bytes((int)sd.n, ell, pc));
+        CK(cudaMemsetAsync(Xcm, 0, sizeof(double) * sd.n * ell, st));
+        int j0 = 1;
+        for (int j = 1; j <= d; ++j) {
+          const int slot = j - j0;
+          if (j <= switch_d)
+            block_to_panel_launch<double>(sd.block64(j), sd.n, r, Pn + (size_t)slot * r * sd.n,
+                                          sd.n, st);
+          else
+            block_to_panel_launch<TB>(sd.block(j), sd.n, r, Pn + (size_t)slot * r * sd.n, sd.n, st);
+          if (slot + 1 == bpp || j == d) {
+            const int cols = (slot + 1) * r;
+            ProfScope ps(h, F_XACC, st, (double)sd.n * (2.0 * 8 * ell + 8.0 * cols),
+                         2.0 * sd.n * ell * cols);
+            ozaki_gemm('N', 'N', (int)sd.n, ell, cols, 1.0, Pn, sd.n,
+                       Wf[side] + (size_t)(j0 - 1) * r, m, 1.0, Xcm, sd.n, ozw, h->flags, st);
+            j0 = j + 1;
+          }
+          if (j == d) break;
+          arnoldi_basis(sd, j, true);
+        }
+        cols_to_rows_launch(Xcm, sd.n, ell, X, st);
+        continue;
+      }
       CK(cudaMemsetAsync(X, 0, sizeof(double) * sd.n * ell, st));
       // second sweep: U_1 from C, then U_{j+1} from the stored coefficients
       int last = 0;

@@ -18,6 +18,7 @@ namespace spk {
 constexpr int kMaxR = 4;      // block width r supported by the fused kernels
 constexpr int kMaxWin = 16;   // largest truncation window k
 constexpr int kXMaxBlocks = 8; // blocks per factor-accumulation launch
+constexpr int kXPanelCols = 64; // basis columns per tensor-core accumulation
 
 // Device-side status word bits (written by kernels, read by the host).
 enum : uint32_t {
@@ -243,6 +244,11 @@ void spmm_wide_launch(const int32_t* rowptr, const int32_t* col, const double* v
                       int w, const double* X, double* Y, cudaStream_t st);
 template <typename TV>
 void convert_values_launch(const double* src, TV* dst, int64_t count, cudaStream_t st);
+// r columns of a row-major n x r block into an FP64 column-major panel (ld ldp)
+template <typename TB>
+void block_to_panel_launch(const TB* U, int64_t n, int r, double* P, int64_t ldp, cudaStream_t st);
+// X (n x ell, row-major) from Xcm (n x ell, column-major)
+void cols_to_rows_launch(const double* Xcm, int64_t n, int ell, double* X, cudaStream_t st);
 template <typename TB>
 void convert_block_launch(const double* src, TB* dst, int64_t count, cudaStream_t st);
 void combine_small_launch(const double* A, const double* B, double* C, int r, int mode,

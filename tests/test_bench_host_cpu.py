@@ -41,6 +41,10 @@ def test_roofline_picks_the_dominant_family_and_its_bound(bench):
     assert roof["achieved"] == pytest.approx(400.0) and roof["unit"] == "GB/s"
     assert roof["frac"] == pytest.approx(400.0 / 5000.0)
     assert bench.pick_roofline({}, 5000.0, 1.0) == (None, {})
+    # a composite wall-time family (two concurrent inversions) is never chosen
+    prof["gje_invert"] = {"ms": 5000.0, "groups": 1, "launches": 10, "bytes": 1e9, "flops": 1e13}
+    roof, table = bench.pick_roofline(prof, hbm_gbs=5000.0, fp64_tflops=1.0)
+    assert roof["kernel"] == "stream" and "gje_invert" in table
 
 
 def test_fp64_alu_peak_from_units_and_clock(bench):
