@@ -722,12 +722,41 @@ int minus_block(spk_handle* h, int m, const double* A, int64_t lda, const double
   uh_times_launch(U, kA, R, kA, m, Rt, st);
   // host copies kept alive until the stream is drained below
   TRY(wait_stream(h, st, h->host_wait_s));
+  // the shifts t_ii: a real one (the usual case: a real eigenvalue off the
+  // half plane) needs only the m x m inverse of B + t I, applied to the real
+  // and imaginary parts of the right-hand side alike
+  std::vector<double2> tdiag(kA);
+  for (int i = 0; i < kA; ++i)
+    TRY(d2h(h, &tdiag[i], T + (size_t)i * kA + i, sizeof(double2), st));
+  // the inversions' trailing updates on the tensor cores, one launch per panel
+  const int nbw = gje_panel_width();
   GjeState gs{ipiv, cvec, scal, h->flags, gpanel, gbsave};
+  if (h->tensor_gemm && ozaki_enabled(m, m, nbw)) {
+    gs.oz_work = ws_get(h, "sp_oz", ozaki_work_bytes(m2, m2, nbw));
+    if (!gs.oz_work) return fail(h, SPK_ERR_ALLOC, "cannot allocate split-solve GEMM work");
+  }
+  if (gje_persistent_ok(m2)) {
+    gs.cstore = static_cast<double*>(ws_get(h, "sp_cst", sizeof(double) * (size_t)m2 * nbw));
+    gs.pstore = static_cast<double*>(ws_get(h, "sp_pst", sizeof(double) * 4 * nbw));
+    gs.ready = static_cast<uint32_t*>(ws_get(h, "sp_rdy", sizeof(uint32_t) * nbw));
+    gs.perm = static_cast<int32_t*>(ws_get(h, "sp_perm", sizeof(int32_t) * (4 * nbw + 1)));
+    if (!gs.cstore || !gs.pstore || !gs.ready || !gs.perm)
+      return fail(h, SPK_ERR_ALLOC, "cannot allocate split-solve panel work");
+    CK(cudaMemsetAsync(gs.ready, 0, sizeof(uint32_t) * nbw, st));
+  }
   for (int i = kA - 1; i >= 0; --i) {
     row_rhs_launch(Rt, T, kA, i, Zt, m, rhs, st);
-    realify_shift_launch(B, ldb, m, T, kA, i, M, st);
-    gje_invert(M, m2, m2, gs, st);
-    gemm_f64('N', 'N', m2, 1, m2, 1.0, M, m2, rhs, m2, 0.0, x, m2, st);
+    const double2 t = tdiag[i];
+    if (std::fabs(t.y) <= 1e-13 * std::max(1.0, std::hypot(t.x, t.y))) {
+      // M = B + Re(t) I (m x m); x = M^{-1} [rhs_re, rhs_im]
+      sign_affine_launch(B, ldb, 1.0, B, ldb, t.x, 0.0, m, M, m, st);
+      gje_invert(M, m, m, gs, st);
+      gemm_f64('N', 'N', m, 2, m, 1.0, M, m, rhs, m, 0.0, x, m, st);
+    } else {
+      realify_shift_launch(B, ldb, m, T, kA, i, M, st);
+      gje_invert(M, m2, m2, gs, st);
+      gemm_f64('N', 'N', m2, 1, m2, 1.0, M, m2, rhs, m2, 0.0, x, m2, st);
+    }
     store_row_launch(x, m, kA, i, Zt, st);
   }
   u_times_real_launch(U, kA, Zt, m, Z, st);
