@@ -30,7 +30,7 @@
 // tensor cores' shared-memory operand layout: 8-row x 16-byte core matrices,
 // K-major, no swizzle), k_oz_mma (one CTA per 128 x 64 tile of C; one thread
 // issues the bulk copies of the chunk's slices and the tcgen05.mma
-// instructions, all four warps read tensor memory for the FP64 epilogue).
+// instructions, all eight warps read tensor memory for the FP64 epilogue).
 #include "spk_internal.cuh"
 
 #include <algorithm>
@@ -52,6 +52,7 @@ constexpr int kOzSmem = kOzS * (kOzATile + kOzBTile);   // 192 KB
 constexpr uint32_t kOzSbo = (kOzKC / 8) * 128;          // next 8-row group of core matrices
 constexpr uint32_t kOzLbo = 128;                        // next 8-element K group
 constexpr long kOzSpin = 1l << 26;                      // bounded mbarrier waits
+constexpr int kOzThreads = 256;                         // 8 warps: two per TMEM lane quadrant
 
 // Byte offset of element (i, k) inside a slice tile (K-major core matrices).
 __host__ __device__ __forceinline__ uint32_t oz_offset(int i, int k) {
@@ -176,8 +177,8 @@ __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity) {
   return done != 0;
 }
 
-// One CTA per 128 x 64 tile of C; 128 threads.
-__global__ void __launch_bounds__(128, 1) k_oz_mma(const uint8_t* __restrict__ As,
+// One CTA per 128 x 64 tile of C; 256 threads.
+__global__ void __launch_bounds__(kOzThreads, 1) k_oz_mma(const uint8_t* __restrict__ As,
                                                    const uint8_t* __restrict__ Bs,
                                                    const int* __restrict__ eA,
                                                    const int* __restrict__ eB, int M, int N,
@@ -209,9 +210,13 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const uint8_t* __restrict__ A
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzTN >> 3) << 17) |
                          ((uint32_t)(kOzTM >> 4) << 24);
-  double acc[kOzTN];
+  // warps w and w + 4 share the lane quadrant w of tensor memory (rows
+  // 32 w .. 32 w + 31 of the tile) and take one half of the columns each
+  const int quad = warp & 3, half = warp >> 2;
+  constexpr int kCols = kOzTN / 2;
+  double acc[kCols];
 #pragma unroll
-  for (int j = 0; j < kOzTN; ++j) acc[j] = 0.0;
+  for (int j = 0; j < kCols; ++j) acc[j] = 0.0;
   for (int kt = 0; kt < KT; ++kt) {
     const uint32_t parity = kt & 1;
     if (tid == 0) {
@@ -267,9 +272,10 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const uint8_t* __restrict__ A
     for (int lv = 0; lv < kOzLevels; ++lv) {
       const int sh = -kOzBits * (lv + 2);
 #pragma unroll
-      for (int c0 = 0; c0 < kOzTN; c0 += 16) {
+      for (int c0 = 0; c0 < kCols; c0 += 16) {
         uint32_t r[16];
-        const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(lv * kOzTN + c0);
+        const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) +
+                            (uint32_t)(lv * kOzTN + half * kCols + c0);
         asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
                        "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
@@ -286,12 +292,12 @@ __global__ void __launch_bounds__(128, 1) k_oz_mma(const uint8_t* __restrict__ A
   if (failed) {
     if (tid == 0) atomicOr(flags, kFlagTimeout);
   } else {
-    const int row = mt * kOzTM + 32 * warp + lane;
+    const int row = mt * kOzTM + 32 * quad + lane;
     if (row < M) {
       const int ea = eA[row];
 #pragma unroll
-      for (int j = 0; j < kOzTN; ++j) {
-        const int col = nt * kOzTN + j;
+      for (int j = 0; j < kCols; ++j) {
+        const int col = nt * kOzTN + half * kCols + j;
         if (col < N) {
           double* c = C + (int64_t)col * ldc + row;
           const double v = alpha * ldexp(acc[j], ea + eB[col]);
@@ -353,7 +359,7 @@ void ozaki_gemm(char ta, char tb, int M, int N, int K, double alpha, const doubl
       va, M, K, eA, MT, KT, reinterpret_cast<__nv_bfloat16*>(As));
   k_oz_split<kOzTN><<<oz_grid((int64_t)NT * kOzTN * KT * kOzKC, 256), 256, 0, st>>>(
       vb, N, K, eB, NT, KT, reinterpret_cast<__nv_bfloat16*>(Bs));
-  k_oz_mma<<<dim3((unsigned)MT, (unsigned)NT), 128, kOzSmem, st>>>(As, Bs, eA, eB, M, N, MT, NT,
+  k_oz_mma<<<dim3((unsigned)MT, (unsigned)NT), kOzThreads, kOzSmem, st>>>(As, Bs, eA, eB, M, N, MT, NT,
                                                                     KT, alpha, beta, C, ldc, flags);
 }
 
