@@ -153,29 +153,35 @@ __global__ void __launch_bounds__(512) k_fwht_chunks(const TB* __restrict__ X, i
   for (int t = threadIdx.x; t < n2; t += blockDim.x) Y[((int64_t)t * n1 + chunk) * r + c] = buf[t];
 }
 
-template <typename TC>
-__global__ void k_gather_rows(const TC* __restrict__ Y, int64_t n1, int r, int n2, int log2n2,
+// One warp per selected row; the r column sums end in a reduce-scatter
+// warp sum (6 additions per lane for r = 4 instead of 20).
+template <typename TC, int R>
+__global__ void k_gather_rows(const TC* __restrict__ Y, int64_t n1, int n2, int log2n2,
                               const int32_t* __restrict__ rows, int32_t s, double scale,
                               double* __restrict__ SX) {
+  __shared__ double out[8][R];
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int wl = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= s) return;
   const int32_t rho = rows[warp];
   const int64_t lo = rho & (n2 - 1);
   const int64_t hi = (int64_t)rho >> log2n2;
-  double acc[kMaxR] = {0, 0, 0, 0};
+  double acc[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) acc[k] = 0.0;
   for (int64_t c = lane; c < n1; c += 32) {
     const bool neg = __popcll((unsigned long long)(hi & c)) & 1;
-    const TC* y = Y + (lo * n1 + c) * r;
-    for (int k = 0; k < r; ++k) {
+    const TC* y = Y + (lo * n1 + c) * R;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
       const double v = (double)y[k];
       acc[k] += neg ? -v : v;
     }
   }
-  for (int k = 0; k < r; ++k) {
-    const double v = warp_sum(acc[k]);
-    if (lane == 0) SX[warp + (int64_t)k * s] = v * scale;
-  }
+  warp_sum_store<R>(acc, out[wl]);
+  __syncwarp();
+  if (lane < R) SX[warp + (int64_t)lane * s] = out[wl][lane] * scale;
 }
 
 template <typename TB>
@@ -329,8 +335,24 @@ void sketch_apply_launch(const SketchDev& sk, const TB* X, int r, double* SX, TC
   const int warps_per_block = 8;
   const int blocks = (sk.s + warps_per_block - 1) / warps_per_block;
   count_launches(1);
-  k_gather_rows<TC><<<blocks, warps_per_block * 32, 0, st>>>(scratch, sk.n1, r, sk.n2, sk.log2n2,
-                                                             sk.rows, sk.s, sk.scale, SX);
+  switch (r) {
+    case 1:
+      k_gather_rows<TC, 1><<<blocks, warps_per_block * 32, 0, st>>>(
+          scratch, sk.n1, sk.n2, sk.log2n2, sk.rows, sk.s, sk.scale, SX);
+      break;
+    case 2:
+      k_gather_rows<TC, 2><<<blocks, warps_per_block * 32, 0, st>>>(
+          scratch, sk.n1, sk.n2, sk.log2n2, sk.rows, sk.s, sk.scale, SX);
+      break;
+    case 3:
+      k_gather_rows<TC, 3><<<blocks, warps_per_block * 32, 0, st>>>(
+          scratch, sk.n1, sk.n2, sk.log2n2, sk.rows, sk.s, sk.scale, SX);
+      break;
+    default:
+      k_gather_rows<TC, 4><<<blocks, warps_per_block * 32, 0, st>>>(
+          scratch, sk.n1, sk.n2, sk.log2n2, sk.rows, sk.s, sk.scale, SX);
+      break;
+  }
 }
 
 template void sketch_apply_launch<double, double>(const SketchDev&, const double*, int, double*,

@@ -64,16 +64,17 @@ constexpr int kRowTile = 128;
 constexpr int kColChunk = 256;
 constexpr int kQtMaxChunks = 32;
 
-// partial[(chunk*s + i)*r + c] = sum_{j in chunk} Q[i + j*ldq] * t[j*r + c]
+// partial[(chunk*s + i)*r + c] = sum_{j in chunk} Q[i + j*ldq] * t[j*r + c],
+// chunks of cw <= kColChunk columns
 template <int R>
 __global__ void __launch_bounds__(kRowTile) k_q_times_t(const double* __restrict__ Q, int64_t ldq,
-                                                        int64_t s, int m,
+                                                        int64_t s, int m, int cw,
                                                         const double* __restrict__ t,
                                                         double* __restrict__ partial) {
   __shared__ double ts[kColChunk * R];
   const int chunk = blockIdx.y;
-  const int j0 = chunk * kColChunk;
-  const int j1 = min(m, j0 + kColChunk);
+  const int j0 = chunk * cw;
+  const int j1 = min(m, j0 + cw);
   for (int e = threadIdx.x; e < (j1 - j0) * R; e += blockDim.x) ts[e] = t[(int64_t)j0 * R + e];
   __syncthreads();
   const int64_t i = (int64_t)blockIdx.x * kRowTile + threadIdx.x;
@@ -211,37 +212,48 @@ void q_update_launch(const double* Q, int64_t ldq, int64_t s, int m, const doubl
     cudaMemcpyAsync(w_out, w_in, sizeof(double) * s * r, cudaMemcpyDeviceToDevice, st);
     return;
   }
+  const int cw = (m + nchunk - 1) / nchunk;    // <= kColChunk (q_update_chunks)
   dim3 grid((unsigned)((s + kRowTile - 1) / kRowTile), (unsigned)nchunk);
   const int g2 = grid_for(s, 256);
   switch (r) {
     case 1:
       count_launches(1);
-      k_q_times_t<1><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, t, partial);
+      k_q_times_t<1><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, cw, t, partial);
       count_launches(1);
       k_q_update_finish<1><<<g2, 256, 0, st>>>(w_in, w_out, partial, s, nchunk);
       break;
     case 2:
       count_launches(1);
-      k_q_times_t<2><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, t, partial);
+      k_q_times_t<2><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, cw, t, partial);
       count_launches(1);
       k_q_update_finish<2><<<g2, 256, 0, st>>>(w_in, w_out, partial, s, nchunk);
       break;
     case 3:
       count_launches(1);
-      k_q_times_t<3><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, t, partial);
+      k_q_times_t<3><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, cw, t, partial);
       count_launches(1);
       k_q_update_finish<3><<<g2, 256, 0, st>>>(w_in, w_out, partial, s, nchunk);
       break;
     default:
       count_launches(1);
-      k_q_times_t<4><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, t, partial);
+      k_q_times_t<4><<<grid, kRowTile, 0, st>>>(Q, ldq, s, m, cw, t, partial);
       count_launches(1);
       k_q_update_finish<4><<<g2, 256, 0, st>>>(w_in, w_out, partial, s, nchunk);
       break;
   }
 }
 
-int q_update_chunks(int m) { return std::max(1, (m + kColChunk - 1) / kColChunk); }
+// Column chunks of Q t: at least ceil(m / kColChunk), and more (down to 32
+// columns each) while the row tiles alone would leave the GPU short of about
+// four CTAs per SM.  Non-decreasing in m, so the count at the largest m
+// sizes the partial buffer.
+int q_update_chunks(int m, int64_t s) {
+  const int base = std::max(1, (m + kColChunk - 1) / kColChunk);
+  const int64_t tiles = std::max<int64_t>(1, (s + kRowTile - 1) / kRowTile);
+  const int want = (int)std::min<int64_t>(64, (4 * 152 + tiles - 1) / tiles);
+  const int fine = std::max(1, std::min(want, (m + 31) / 32));
+  return std::max(base, fine);
+}
 
 void ts_gram_launch(const double* w, int64_t s, int r, double* partial, int grid, cudaStream_t st) {
   switch (r) {

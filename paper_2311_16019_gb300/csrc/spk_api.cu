@@ -285,9 +285,12 @@ int flags_to_status(spk_handle* h, uint32_t f) {
 // trace (condition number above ~1e7) is reported as a breakdown.
 constexpr double kBreakdownFloor = 1e-14;
 
+// Row kernels with per-CTA partial sums: two CTAs of 256 threads per SM, so
+// that each thread covers several rows before its block reduction (the
+// reduction's FP64 additions, per row, shrink in proportion).
 int grid_rows(spk_handle* h, int64_t n) {
   int64_t g = (n + 255) / 256;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)h->sm_count * 4));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)h->sm_count * 2));
 }
 
 // Double-double Gram matrix of the virtual matrix P (see k_residual.cu) into
@@ -1083,7 +1086,7 @@ struct Solver {
       SWS(t1, double, "t1", (size_t)mmax * r);
       SWS(t2, double, "t2", (size_t)mmax * r);
       SWS(qpartial, double, "qpartial",
-          std::max((size_t)q_update_chunks((int)mmax) * sd.n * r,
+          std::max((size_t)q_update_chunks((int)mmax, sd.n) * sd.n * r,
                    (size_t)qt_dot_partial_doubles((int)mmax, r)));
       CK(cudaMemsetAsync(sd.Ht, 0, sizeof(double) * sd.ldH * sd.ldH, st));
     }
@@ -1130,7 +1133,7 @@ struct Solver {
         (size_t)std::max(std::max(sd.grid, 2 * h->sm_count), 64) * 4 * r * r * std::max(groups, 1));
     if (sketched) {
       SWS(qpartial, double, "qpartial",
-          std::max({(size_t)q_update_chunks((int)mmax) * s * r, (size_t)border_chunks((int)mmax) * mmax * r,
+          std::max({(size_t)q_update_chunks((int)mmax, s) * s * r, (size_t)border_chunks((int)mmax) * mmax * r,
                     (size_t)qt_dot_partial_doubles((int)mmax, r)}));
       SWS(sk_scratch, TC, "skscratch", std::max<int64_t>(1, sd.sk.npad * r));
       if (two_prec()) {
@@ -1310,7 +1313,7 @@ struct Solver {
                                    sd.W, none, sd.partial, sd.grid, st);
     }
     block_to_cols_launch(reinterpret_cast<const double*>(sd.W), n, r, sd.wn, n, st);
-    const int nch = q_update_chunks(m);
+    const int nch = q_update_chunks(m, n);
     const double nm8 = 8.0 * n * m, nr8 = 8.0 * nr;
     {
       ProfScope ps(h, F_QTDOT, st, nm8 + nr8, 2.0 * n * m * r);
@@ -1368,7 +1371,7 @@ struct Solver {
       else
         sketch_apply_launch<TB, TC>(sd.sk, sd.block(d + 1), r, sd.w, sd.sk_scratch, st);
     }
-    const int nch = q_update_chunks(m);
+    const int nch = q_update_chunks(m, s);
     {
       ProfScope ps(h, F_QTDOT, st, sm8 + sr8 + 8.0 * m * r, 2.0 * s * m * r);
       qt_dot_launch(sd.Q, s, s, m, sd.w, r, sd.t1, sd.qpartial, st);

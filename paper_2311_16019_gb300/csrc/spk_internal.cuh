@@ -266,7 +266,7 @@ void q_update_launch(const double* Q, int64_t ldq, int64_t s, int m, const doubl
 void ts_gram_launch(const double* w, int64_t s, int r, double* partial, int grid, cudaStream_t st);
 void ts_scale_launch(double* w, int64_t s, int r, const double* Rinv, double* out,
                      int64_t ldo, cudaStream_t st);
-int q_update_chunks(int m);
+int q_update_chunks(int m, int64_t s);
 void t_write_launch(double* T, int64_t ldT, int m, int r, const double* t1, const double* t2,
                     const double* tau, cudaStream_t st);
 
