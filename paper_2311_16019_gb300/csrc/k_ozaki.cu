@@ -32,6 +32,7 @@
 // issues the bulk copies of the chunk's slices and the tcgen05.mma
 // instructions, all eight warps read tensor memory for the FP64 epilogue).
 #include "spk_internal.cuh"
+#include "tc_common.cuh"
 
 #include <algorithm>
 
@@ -144,37 +145,14 @@ __global__ void k_oz_split(View v, int rows, int K, const int* __restrict__ e, i
   }
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
+using tc::smem_u32;
 
 __device__ __forceinline__ uint64_t oz_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)(kOzLbo >> 4) << 16;
-  d |= (uint64_t)(kOzSbo >> 4) << 32;
-  d |= (uint64_t)1 << 46;     // descriptor version of tcgen05; no swizzle
-  return d;
-}
-
-// x 2^sh for the FP32 bit pattern f of an integer with |x| < 2^24, built on
-// the integer pipe: FP32 exponent rebiased to FP64 (+896) and shifted by sh,
-// mantissa moved to the top of the FP64 fraction.  Exact.
-__device__ __forceinline__ double oz_f32_int_to_f64(uint32_t f, int sh) {
-  if ((f & 0x7fffffffu) == 0u) return 0.0;
-  const uint32_t e = ((f >> 23) & 0xffu) + 896u + (uint32_t)sh;
-  const uint32_t mant = f & 0x7fffffu;
-  const uint32_t hi = (f & 0x80000000u) | (e << 20) | (mant >> 3);
-  return __hiloint2double((int)hi, (int)(mant << 29));
+  return tc::desc_kmajor(saddr, kOzLbo, kOzSbo);
 }
 
 __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (long it = 0; it < kOzSpin && !done; ++it) {
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-  }
-  return done != 0;
+  return tc::mbar_wait(bar, parity, kOzSpin);
 }
 
 // One CTA per 128 x 64 tile of C; 256 threads.
@@ -208,8 +186,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_mma(const uint8_t* __restr
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzTN >> 3) << 17) |
-                         ((uint32_t)(kOzTM >> 4) << 24);
+  constexpr uint32_t idesc = tc::idesc_bf16(kOzTM, kOzTN);
   // warps w and w + 4 share the lane quadrant w of tensor memory (rows
   // 32 w .. 32 w + 31 of the tile) and take one half of the columns each
   const int quad = warp & 3, half = warp >> 2;
@@ -283,7 +260,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_mma(const uint8_t* __restr
                      : "r"(ta));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[c0 + j] += oz_f32_int_to_f64(r[j], sh);
+        for (int j = 0; j < 16; ++j) acc[c0 + j] += tc::f32_int_to_f64(r[j], sh);
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

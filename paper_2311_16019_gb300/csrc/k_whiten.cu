@@ -205,6 +205,23 @@ void qt_dot_launch(const double* Q, int64_t ldq, int64_t s, int m, const double*
 
 int qt_dot_partial_doubles(int mmax, int r) { return kQtMaxChunks * mmax * r; }
 
+void qt_finish_launch(const double* tpart, int64_t count, int nchunk, double* t, cudaStream_t st) {
+  count_launches(1);
+  k_qt_finish<<<grid_for(count, 256), 256, 0, st>>>(tpart, count, nchunk, t);
+}
+
+void q_update_finish_launch(const double* w_in, double* w_out, const double* partial, int64_t s,
+                            int r, int nchunk, cudaStream_t st) {
+  const int g = grid_for(s, 256);
+  count_launches(1);
+  switch (r) {
+    case 1: k_q_update_finish<1><<<g, 256, 0, st>>>(w_in, w_out, partial, s, nchunk); break;
+    case 2: k_q_update_finish<2><<<g, 256, 0, st>>>(w_in, w_out, partial, s, nchunk); break;
+    case 3: k_q_update_finish<3><<<g, 256, 0, st>>>(w_in, w_out, partial, s, nchunk); break;
+    default: k_q_update_finish<4><<<g, 256, 0, st>>>(w_in, w_out, partial, s, nchunk); break;
+  }
+}
+
 void q_update_launch(const double* Q, int64_t ldq, int64_t s, int m, const double* t, int r,
                      const double* w_in, double* w_out, double* partial, int nchunk,
                      cudaStream_t st) {

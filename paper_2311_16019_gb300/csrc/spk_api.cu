@@ -1001,6 +1001,11 @@ struct Side {
   double* T = nullptr;
   int64_t ldT = 0;
   double* Q = nullptr;       // s x ldT
+  // BF16-sliced copies of Q for the tensor-core whitening products
+  QsGeom qs;
+  uint8_t *QA = nullptr, *QB = nullptr;
+  int* qexp = nullptr;
+  bool qs_on = false;
   double* Ht = nullptr;
   int64_t ldH = 0;
   SketchDev sk;
@@ -1132,9 +1137,18 @@ struct Solver {
     SWS(partial, double, "partial",
         (size_t)std::max(std::max(sd.grid, 2 * h->sm_count), 64) * 4 * r * r * std::max(groups, 1));
     if (sketched) {
-      SWS(qpartial, double, "qpartial",
-          std::max({(size_t)q_update_chunks((int)mmax, s) * s * r, (size_t)border_chunks((int)mmax) * mmax * r,
-                    (size_t)qt_dot_partial_doubles((int)mmax, r)}));
+      sd.qs_on = h->tensor_gemm && qs_enabled(s, (int)mmax);
+      size_t qpd = std::max({(size_t)q_update_chunks((int)mmax, s) * s * r,
+                             (size_t)border_chunks((int)mmax) * mmax * r,
+                             (size_t)qt_dot_partial_doubles((int)mmax, r)});
+      if (sd.qs_on) {
+        sd.qs = qs_geometry(s, (int)mmax);
+        SWS(QA, uint8_t, "QA", sd.qs.bytesA);
+        SWS(QB, uint8_t, "QB", sd.qs.bytesB);
+        SWS(qexp, int, "qexp", 4);
+        qpd = std::max({qpd, (size_t)qs_chunks(s) * mmax * r, (size_t)qs_chunks(mmax) * s * r});
+      }
+      SWS(qpartial, double, "qpartial", qpd);
       SWS(sk_scratch, TC, "skscratch", std::max<int64_t>(1, sd.sk.npad * r));
       if (two_prec()) {
         SWS(sk_scratch64, double, "skscratch64", std::max<int64_t>(1, sd.sk.npad * r));
@@ -1180,6 +1194,7 @@ struct Solver {
     chol_small_launch(sd.partial, g, r, sd.R2, sd.Rinv, h->flags, 1e-28, st);
     ts_scale_launch(sd.w, s, r, sd.Rinv, sd.Q + (int64_t)m * s, s, st);
     combine_small_launch(sd.R2, sd.R1, sd.tau, r, 0, st);
+    if (sd.qs_on) qs_append_launch(sd.Q, sd.qs, m, r, sd.QA, sd.QB, st);
   }
 
   int init_side(Side<TB, TC, TV>& sd, const double* C) {
@@ -1372,22 +1387,27 @@ struct Solver {
         sketch_apply_launch<TB, TC>(sd.sk, sd.block(d + 1), r, sd.w, sd.sk_scratch, st);
     }
     const int nch = q_update_chunks(m, s);
-    {
+    // CGS2 against Q: on the tensor cores from the sliced copies of Q (the
+    // algorithmic bytes are those of the FP64 Q, so the two paths compare)
+    const bool tq = sd.qs_on && qs_enabled(s, m);
+    auto qt = [&](const double* w, double* t) {
       ProfScope ps(h, F_QTDOT, st, sm8 + sr8 + 8.0 * m * r, 2.0 * s * m * r);
-      qt_dot_launch(sd.Q, s, s, m, sd.w, r, sd.t1, sd.qpartial, st);
-    }
-    {
+      if (tq)
+        qs_qt_launch(sd.qs, sd.QA, m, w, r, t, sd.qpartial, sd.qexp, h->flags, st);
+      else
+        qt_dot_launch(sd.Q, s, s, m, w, r, t, sd.qpartial, st);
+    };
+    auto qupd = [&](const double* t, const double* w_in, double* w_out) {
       ProfScope ps(h, F_QUPDATE, st, sm8 + 2 * sr8 + 8.0 * m * r, 2.0 * s * m * r);
-      q_update_launch(sd.Q, s, s, m, sd.t1, r, sd.w, sd.w1, sd.qpartial, nch, st);
-    }
-    {
-      ProfScope ps(h, F_QTDOT, st, sm8 + sr8 + 8.0 * m * r, 2.0 * s * m * r);
-      qt_dot_launch(sd.Q, s, s, m, sd.w1, r, sd.t2, sd.qpartial, st);
-    }
-    {
-      ProfScope ps(h, F_QUPDATE, st, sm8 + 2 * sr8 + 8.0 * m * r, 2.0 * s * m * r);
-      q_update_launch(sd.Q, s, s, m, sd.t2, r, sd.w1, sd.w, sd.qpartial, nch, st);
-    }
+      if (tq)
+        qs_update_launch(sd.qs, sd.QB, m, t, r, w_in, w_out, sd.qpartial, sd.qexp, h->flags, st);
+      else
+        q_update_launch(sd.Q, s, s, m, t, r, w_in, w_out, sd.qpartial, nch, st);
+    };
+    qt(sd.w, sd.t1);
+    qupd(sd.t1, sd.w, sd.w1);
+    qt(sd.w1, sd.t2);
+    qupd(sd.t2, sd.w1, sd.w);
     {
       ProfScope ps(h, F_TSQR, st, 6 * sr8, 6.0 * s * r * r);
       sketch_qr(sd, m);

@@ -269,6 +269,32 @@ void ts_scale_launch(double* w, int64_t s, int r, const double* Rinv, double* ou
 int q_update_chunks(int m, int64_t s);
 void t_write_launch(double* T, int64_t ldT, int m, int r, const double* t1, const double* t2,
                     const double* tau, cudaStream_t st);
+// t[e] = sum over nchunk chunks of tpart[ch * count + e], chunks in order
+void qt_finish_launch(const double* tpart, int64_t count, int nchunk, double* t, cudaStream_t st);
+// w_out[i + c s] = w_in[i + c s] - sum_ch partial[(ch s + i) r + c]
+void q_update_finish_launch(const double* w_in, double* w_out, const double* partial, int64_t s,
+                            int r, int nchunk, cudaStream_t st);
+
+// Whitening products on the tensor cores (k_qslice.cu): two BF16-sliced
+// copies of Q, appended as Q grows, and the two products from them.
+struct QsGeom {
+  int64_t s = 0;
+  int mmax = 0;
+  int MTA = 0, KTA = 0, MTB = 0, KTB = 0;   // tiles of the two copies
+  size_t bytesA = 0, bytesB = 0;
+};
+QsGeom qs_geometry(int64_t s, int mmax);
+int qs_chunks(int64_t K);                  // K ranges (partial sums) of a product
+bool qs_enabled(int64_t s, int m);         // the tensor-core products pay off
+void qs_append_launch(const double* Q, const QsGeom& g, int m, int r, uint8_t* QA, uint8_t* QB,
+                      cudaStream_t st);
+// t (m x r, row-major) = Q^T w; tpart: qs_chunks(s) * m * r doubles; eB: r ints
+void qs_qt_launch(const QsGeom& g, const uint8_t* QA, int m, const double* w, int r, double* t,
+                  double* tpart, int* eB, uint32_t* flags, cudaStream_t st);
+// w_out = w_in - Q t; partial: qs_chunks(m) * s * r doubles; eB: r ints
+void qs_update_launch(const QsGeom& g, const uint8_t* QB, int m, const double* t, int r,
+                      const double* w_in, double* w_out, double* partial, int* eB,
+                      uint32_t* flags, cudaStream_t st);
 
 // ---------------------------------------------------------------- projected
 // partial: border_chunks(mp) * mp * r doubles of scratch

@@ -578,3 +578,45 @@ def test_three_d_workload_full_size_properties():
                     check="adaptive")
     assert g.converged
     assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 2e-8
+
+
+@pytest.mark.parametrize("name,k,s,d", [("cd2d_64_r4", 4, 3200, 100), ("cd2d_48_r3", 3, 1100, 100),
+                                         ("cd2d_64_r2", 2, 1100, 140), ("cd2d_96_r1", 2, 1100, 270)])
+def test_tensor_core_whitening_fixed_d_parity(name, k, s, d):
+    """From m = d r >= 256 columns of Q (and s >= 1024) the whitening products
+    Q^T w and Q t run on the tensor cores from BF16-sliced copies of Q
+    (r = 1..4: B operands of 16 and 32 rows).  Fixed-d parity with the
+    oracle, at d where the estimate is still above 1e-9 (past convergence the
+    sketched basis is numerically dependent and X is ill-determined): X
+    within 1e-10, rho within 1e-8 relative."""
+    P = I.workload(name)
+    g = spk().solve(P.A, P.BT, P.C1, P.C2, k=k, s=s, maxit=d, p=d, tol=0.0, seed=3, fixed_d=d)
+    o = SP.spkms(P.A, P.BT, P.C1, P.C2, k=k, s=s, tol=0.0, maxit=d, p=d, seed=3)
+    err = M.rel_error(host(g.X1), host(g.X2), o["X1"], o["X2"])
+    print(f"{name} d={d}: rel error {err:.2e}, rho {g.rho:.6e} vs {o['rho']:.6e}")
+    assert err < TOL_X, err
+    assert g.rho == pytest.approx(o["rho"], rel=1e-8)
+
+
+def test_tensor_core_whitening_matches_fp64_engine():
+    """The whitening's R factor T (m = 404 columns) from the tensor-core
+    products against the FP64 CUDA-core products: the same matrix up to FP64
+    rounding (1e-12 relative, column by column against its norm)."""
+    P = I.workload("cd2d_64_r4")
+    kw = dict(k=4, s=3200, maxit=100, p=100, tol=0.0, seed=1, fixed_d=100)
+    try:
+        spk().set_tensor_gemm(False)
+        spk().solve(P.A, P.BT, P.C1, P.C2, **kw)
+        T64 = spk().inspect("U_T")
+    finally:
+        spk().set_tensor_gemm(True)
+    spk().solve(P.A, P.BT, P.C1, P.C2, **kw)
+    Ttc = spk().inspect("U_T")
+    assert T64.shape == Ttc.shape
+    m = 101 * 4                        # T is (maxit + 1) r square, leading dimension m
+    A64 = T64[: m * m].reshape(m, m, order="F")
+    Atc = Ttc[: m * m].reshape(m, m, order="F")
+    den = np.linalg.norm(A64, axis=0) + 1e-300
+    rel = np.abs(Atc - A64).max(axis=0) / den
+    print(f"T columns: max relative difference {rel.max():.2e}")
+    assert rel.max() < 1e-12
