@@ -580,15 +580,15 @@ def test_three_d_workload_full_size_properties():
     assert M.true_residual(P.A, P.B, P.C1, P.C2, host(g.X1), host(g.X2)) < 2e-8
 
 
-@pytest.mark.parametrize("name,k,s,d", [("cd2d_64_r4", 4, 3200, 100), ("cd2d_48_r3", 3, 1100, 100),
-                                         ("cd2d_64_r2", 2, 1100, 140), ("cd2d_96_r1", 2, 1100, 270)])
+@pytest.mark.parametrize("name,k,s,d", [("cd2d_64_r4", 4, 3200, 100), ("cd2d_48_r3", 3, 1100, 86),
+                                         ("cd2d_64_r2", 2, 1100, 130), ("cd2d_128_r1", 2, 1100, 260)])
 def test_tensor_core_whitening_fixed_d_parity(name, k, s, d):
     """From m = d r >= 256 columns of Q (and s >= 1024) the whitening products
     Q^T w and Q t run on the tensor cores from BF16-sliced copies of Q
     (r = 1..4: B operands of 16 and 32 rows).  Fixed-d parity with the
-    oracle, at d where the estimate is still above 1e-9 (past convergence the
-    sketched basis is numerically dependent and X is ill-determined): X
-    within 1e-10, rho within 1e-8 relative."""
+    oracle, at d where the relative estimate is still about 1e-7 or above
+    (rho is a residual: nearer convergence its relative rounding error grows
+    for any FP64 path): X within 1e-10, rho within 1e-8 relative."""
     P = I.workload(name)
     g = spk().solve(P.A, P.BT, P.C1, P.C2, k=k, s=s, maxit=d, p=d, tol=0.0, seed=3, fixed_d=d)
     o = SP.spkms(P.A, P.BT, P.C1, P.C2, k=k, s=s, tol=0.0, maxit=d, p=d, seed=3)
