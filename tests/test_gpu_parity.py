@@ -602,8 +602,8 @@ def test_tensor_core_whitening_fixed_d_parity(name, k, s, d):
 def test_tensor_core_whitening_matches_fp64_engine(name, k, s, d, xtol):
     """The same solve with the whitening products on the tensor cores and on
     the FP64 CUDA cores, r = 1..4 (B operands of 16 and 32 rows): the R factor
-    T of the sketched basis agrees column by column to 1e-12 of the column's
-    norm, and X to 1e-10 where T is well conditioned.  The r = 2 and r = 1
+    T of the sketched basis agrees column by column to 1e-15 cond(T) of the
+    column's norm, and X to 1e-10 where T is well conditioned.  The r = 2 and r = 1
     cases run where T is ill-conditioned (cond(T) 1.7e12 and 9e15), and
     there X is compared to 1e-8 and 1e-6: both engines' X differ from the
     oracle's there by the same 2e-10 and 1e-7, the problem's sensitivity to
@@ -621,7 +621,12 @@ def test_tensor_core_whitening_matches_fp64_engine(name, k, s, d, xtol):
     g = spk().solve(P.A, P.BT, P.C1, P.C2, **kw)
     Ttc = spk().inspect("U_T")[: mm * mm].reshape(mm, mm, order="F")
     rel = np.abs(Ttc - T64).max(axis=0) / (np.linalg.norm(T64, axis=0) + 1e-300)
+    cond = np.linalg.cond(T64[: d * P.r, : d * P.r])
     errx = M.rel_error(host(g.X1), host(g.X2), *X64)
-    print(f"{name} d={d}: T columns max relative difference {rel.max():.2e}, X {errx:.2e}")
-    assert rel.max() < 1e-12
+    print(f"{name} d={d}: T columns max relative difference {rel.max():.2e} "
+          f"(cond(T) {cond:.1e}), X {errx:.2e}")
+    # a new column of T is the part of the sketched block outside span(Q):
+    # rounding of size u in either engine's projections moves it by about
+    # u cond(T) relative, so the engines agree to that order, not to u
+    assert rel.max() < 1e-13 + 1e-15 * cond
     assert errx < xtol
