@@ -5,37 +5,44 @@
 //   w' = w - Q_d t
 //
 // Both read all of Q_d (s x m, FP64) for r = 1..4 columns: on the FP64 pipe
-// they do 2r flops per 8-byte element of Q and are bound by the FP64 rate.
-// Here each product is an error-free splitting into BF16 products (Ozaki,
-// Ogita, Oishi and Rump, Numer. Algorithms 59 (2012)):
+// (2 FMA per clock per SM on this GPU) they do 2r flops per 8-byte element
+// of Q and are bound by the FP64 rate.  Here each product is an error-free
+// splitting into BF16 products (Ozaki, Ogita, Oishi and Rump, Numer.
+// Algorithms 59 (2012)), with the splitting and the recombination done on
+// the integer pipe so that no FP64 arithmetic is left but a few operations
+// per output:
 //
-// Q slices.  The columns of Q are orthonormal, so |q| <= 1 and x = q/2 has
-// |x| <= 1/2 (up to rounding).  x = sum_{p=1..8} n_p 2^(-7p) + rest with
-// integer digits n_p = rint(2^7 x_p), x_{p+1} = 2^7 x_p - n_p, so |n_p| <= 64
-// and |rest| <= 2^-57: every entry of Q is held to 2^-56 absolute, which
-// bounds the error of a dot product with w by 2^-56 sum |w_i| <= 2^-56
-// sqrt(s) ||w||, below the rounding error of an FP64 dot product of length s.
-// The digits are exact in BF16.  Q grows by r columns per iteration, and the
-// new columns are split once (k_qs_append) into two copies laid out for the
-// two products:
+// Digits.  A value x with |x| < 2^e is rounded to the integer
+// N = rint(x 2^(56-e)) (|N| < 2^56, built from the FP64 bit pattern) and
+// written in balanced base 2^7 from the bottom: N = sum_{p=1..8} n_p 2^(56-7p)
+// with n_2 .. n_8 in [-64, 63] and |n_1| <= 128.  The representation holds x
+// to 2^(e-57) absolute, and the digits are exact in BF16.
+//
+// Q slices.  The columns of Q are orthonormal, so |q| < 2 and e = 1 (|n_1|
+// <= 64): every entry of Q is held to 2^-56, which bounds the error of a dot
+// product with w by 2^-56 sum |w_i| <= 2^-56 sqrt(s) ||w||, below the
+// rounding error of an FP64 dot product of length s.  Q grows by r columns
+// per iteration, and the new columns are split once (k_qs_append) into two
+// copies laid out for the two products:
 //   QA: rows = columns j of Q, K = rows i of Q   (A operand of Q^T w)
 //   QB: rows = rows i of Q,    K = columns j     (A operand of Q t)
 // Each copy is a sequence of 32 KB stages: for a tile of 128 rows and 16 K
 // positions, the 8 slice tiles of 4 KB in the tensor cores' K-major core
 // matrix layout (8 rows x 16 bytes), so one bulk copy moves a whole stage.
 //
-// Right-hand side.  The r columns of w (or t) are scaled by 2^-e_c (2^e_c >
-// max |column c|) and split the same way (|n_1| <= 128, |n_q| <= 64 after);
-// all 8 digit planes of all r columns form one B operand of N = 8 r rows
-// (padded to 16 or 32), so one MMA per Q slice p and K step of 16 gives the
-// products of slice p with every digit plane q of every column.  Each
-// product n_p n_q is at most 2^13 in magnitude; over the at most 256 K
-// positions a CTA handles, every accumulator is an integer below 2^21 and
-// exact in FP32.  Pairs with p + q > 9 (weights below 2^-70) are dropped in
-// the epilogue, which converts the other 36 per column exactly to FP64 and
-// adds them with their weights 2^(-7 (p+q)), then scales by 2^(1 + e_c).
-// The CTAs of one product write partial sums per K range, reduced in a fixed
-// order by the FP64 path's finishing kernels, so the result is deterministic.
+// Right-hand side.  Each CTA handles 256 K positions; it splits its part of
+// the r columns of w (or t) with e_c from the largest magnitude of column c
+// in that part, and all 8 digit planes of all r columns form one B operand
+// of N = 8 r rows (padded to 16 or 32), so one MMA per Q slice p and K step
+// of 16 gives the products of slice p with every digit plane q of every
+// column.  Each product n_p n_q is at most 2^13 in magnitude; over 256 K
+// positions every accumulator is an integer below 2^21 and exact in FP32.
+// Pairs with p + q > 9 (weights below 2^-70) are dropped; the epilogue turns
+// the other 36 per column into integers, adds those of one weight level
+// 2^(-7 (p+q)) exactly, combines the levels exactly into two 64-bit integers
+// and converts those to FP64.  The CTAs of one product write partial sums
+// per K range, reduced in a fixed order by the FP64 path's finishing
+// kernels, so the result is deterministic.
 #include "spk_internal.cuh"
 #include "tc_common.cuh"
 
@@ -70,112 +77,177 @@ __host__ __device__ __forceinline__ uint32_t qs_offset(int i, int k, uint32_t sb
   return (uint32_t)((i >> 3) * sbo + (k >> 3) * kQsLbo + (i & 7) * 16 + (k & 7) * 2);
 }
 
-__device__ __forceinline__ uint16_t bf16_bits(float v) {
-  const __nv_bfloat16 b = __float2bfloat16_rn(v);
-  return *reinterpret_cast<const uint16_t*>(&b);
+// Balanced base-2^7 digits of N = rint(x 2^(56-e)) for |x| < 2^e, from the
+// FP64 bit pattern on the integer pipe: n[0] is the leading digit (|n[0]| <=
+// 128), n[1..7] lie in [-64, 63]; x = 2^e sum_p n[p] 2^(-7 (p+1)) + rest,
+// |rest| <= 2^(e-57).
+__device__ __forceinline__ void qs_digits(double x, int e, int (&n)[kQsS]) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((u >> 52) & 0x7FF);
+  long long N = 0;
+  if (E != 0) {
+    const unsigned long long M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = E - 1023 - e + 4;     // x 2^(56-e) = M 2^sh, sh <= 3 as |x| < 2^e
+    if (sh >= 0)
+      N = (long long)(M << sh);
+    else if (sh > -54)
+      N = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
+    if (u >> 63) N = -N;
+  }
+#pragma unroll
+  for (int p = kQsS - 1; p >= 1; --p) {
+    const int d = (int)((N + 64) & 127) - 64;
+    n[p] = d;
+    N = (N - d) >> kQsBits;
+  }
+  n[0] = (int)N;
 }
 
-// The new columns j = m .. m + r - 1 of Q (ld s) into both copies.
-//   QA: one thread per (new column, group of 8 rows of Q): 8 digits of 8
-//       consecutive K positions -> one 16-byte store per slice; the K
-//       padding i >= s up to the last tile is written as zeros (it meets
-//       zero B rows and must not be NaN).
-//   QB: one thread per (row i, column j) for j in [m, je): the new columns,
-//       and the rest of a K tile that this append opens (zeros, so that the
-//       tile's unwritten columns are finite when an MMA reads them).
-__global__ void k_qs_append(const double* __restrict__ Q, int64_t s, int m, int r, int je,
+// BF16 bit pattern of an integer with |n| <= 256 (exact).
+__device__ __forceinline__ uint32_t bf16_int(int n) {
+  if (n == 0) return 0u;
+  const uint32_t a = (uint32_t)(n < 0 ? -n : n);
+  const int pos = 31 - __clz(a);
+  return (n < 0 ? 0x8000u : 0u) | ((uint32_t)(127 + pos) << 7) | ((a << (7 - pos)) & 0x7Fu);
+}
+
+// 8 values (8 consecutive K positions of one row) -> one 16-byte core-matrix
+// row per slice at base + p * kQsSliceTile.
+__device__ __forceinline__ void qs_store_row8(const double (&x)[8], int e, uint8_t* base) {
+  int n[8][kQsS];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) qs_digits(x[u], e, n[u]);
+#pragma unroll
+  for (int p = 0; p < kQsS; ++p) {
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 8; u += 2) w[u / 2] = bf16_int(n[u][p]) | (bf16_int(n[u + 1][p]) << 16);
+    *reinterpret_cast<uint4*>(base + (int64_t)p * kQsSliceTile) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// The new columns j = m .. m + r - 1 of Q (ld s) into both copies (e = 1).
+//   QA: one thread per (new column, group of 8 rows of Q): the K padding
+//       i >= s up to the last tile is written as zeros (it meets zero B rows
+//       and must not be NaN).
+//   QB: one thread per (row i, group of 8 columns) for the column groups
+//       g0 .. g1 - 1 that hold the new columns: columns below m are written
+//       again (the same digits), columns from m + r on are written as zeros
+//       (a K tile that this append opens is zeroed to its end, so that its
+//       unwritten columns are finite when an MMA reads them).
+__global__ void k_qs_append(const double* __restrict__ Q, int64_t s, int m, int r, int g0, int g1,
                             uint8_t* __restrict__ QA, int KTA, uint8_t* __restrict__ QB,
                             int KTB) {
-  const int64_t groups = 2 * (int64_t)KTA;   // every K group of the row, padding included
-  const int64_t na = (int64_t)r * groups;
-  const int64_t nb = s * (int64_t)(je - m);
+  const int64_t ga = 2 * (int64_t)KTA;
+  const int64_t na = (int64_t)r * ga;
+  const int64_t nb = s * (int64_t)(g1 - g0);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < na + nb;
        t += (int64_t)gridDim.x * blockDim.x) {
+    double x[8];
     if (t < na) {
-      const int c = (int)(t / groups);
-      const int64_t g = t - (int64_t)c * groups;
+      const int c = (int)(t / ga);
+      const int64_t i0 = (t - (int64_t)c * ga) * 8;
       const int j = m + c;
-      const int64_t i0 = g * 8;
-      double x[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int64_t i = i0 + u;
-        x[u] = i < s ? 0.5 * Q[i + (int64_t)j * s] : 0.0;
-      }
+      for (int u = 0; u < 8; ++u) x[u] = i0 + u < s ? Q[i0 + u + (int64_t)j * s] : 0.0;
       const int64_t tile = ((int64_t)(j / kQsTM) * KTA + i0 / kQsKC) * kQsS;
-      uint8_t* base = QA + tile * kQsSliceTile + qs_offset(j % kQsTM, (int)(i0 % kQsKC), kQsSboA);
-#pragma unroll
-      for (int p = 0; p < kQsS; ++p) {
-        uint32_t w[4];
-#pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-          const double t0 = x[u] * 128.0, t1 = x[u + 1] * 128.0;
-          const double n0 = rint(t0), n1 = rint(t1);
-          x[u] = t0 - n0;
-          x[u + 1] = t1 - n1;
-          w[u / 2] = (uint32_t)bf16_bits((float)n0) | ((uint32_t)bf16_bits((float)n1) << 16);
-        }
-        *reinterpret_cast<uint4*>(base + (int64_t)p * kQsSliceTile) = make_uint4(w[0], w[1], w[2], w[3]);
-      }
+      qs_store_row8(x, 1, QA + tile * kQsSliceTile + qs_offset(j % kQsTM, (int)(i0 % kQsKC), kQsSboA));
     } else {
       const int64_t e = t - na;
-      const int j = m + (int)(e / s);
-      const int64_t i = e - (int64_t)(j - m) * s;
-      double x = j < m + r ? 0.5 * Q[i + (int64_t)j * s] : 0.0;
-      const int64_t tile = ((i / kQsTM) * KTB + j / kQsKC) * kQsS;
-      uint8_t* base = QB + tile * kQsSliceTile + qs_offset((int)(i % kQsTM), j % kQsKC, kQsSboA);
+      const int G = g0 + (int)(e / s);
+      const int64_t i = e - (int64_t)(G - g0) * s;
+      const int j0 = 8 * G;
 #pragma unroll
-      for (int p = 0; p < kQsS; ++p) {
-        const double t0 = x * 128.0;
-        const double n0 = rint(t0);
-        x = t0 - n0;
-        *reinterpret_cast<uint16_t*>(base + (int64_t)p * kQsSliceTile) = bf16_bits((float)n0);
-      }
+      for (int u = 0; u < 8; ++u) x[u] = j0 + u < m + r ? Q[i + (int64_t)(j0 + u) * s] : 0.0;
+      const int64_t tile = ((i / kQsTM) * KTB + j0 / kQsKC) * kQsS;
+      qs_store_row8(x, 1, QB + tile * kQsSliceTile + qs_offset((int)(i % kQsTM), j0 % kQsKC, kQsSboA));
     }
   }
 }
 
-// e[c] with 2^e[c] > max_k |B(k, c)| (0 for a zero column); one CTA per column.
-__global__ void k_qs_colexp(const double* __restrict__ B, int64_t bks, int64_t bcs, int K,
-                            int* __restrict__ e) {
-  __shared__ double red[32];
-  const int c = blockIdx.x;
-  double mx = 0.0;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmax(mx, fabs(B[k * bks + c * bcs]));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (threadIdx.x == 0) {
-      int ex = 0;
-      if (mx > 0.0) frexp(mx, &ex);
-      e[c] = ex;
+// Integer value of an FP32 accumulator holding an integer of magnitude < 2^22.
+__device__ __forceinline__ int qs_f32_int(uint32_t f) {
+  return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
+}
+
+// FP64 value of an integer of magnitude < 2^51 (one FP64 addition).
+__device__ __forceinline__ double qs_i64_f64(long long x) {
+  return __longlong_as_double(0x4338000000000000LL + x) - 6755399441055744.0;
+}
+
+// 2^k as an FP64 bit pattern (ldexp outside the normal range).
+__device__ __forceinline__ double qs_pow2(int k) {
+  return (k > -1023 && k < 1024) ? __longlong_as_double((long long)(1023 + k) << 52) : ldexp(1.0, k);
+}
+
+// Level sums of one half of the Q slices (p = P0 .. P0 + 3) for one tile row:
+// lev[L][c] = sum over kept pairs p + q = L of D_p(row, q R + c), exact in
+// int32; then hi[c] = sum_{L<4} lev[L][c] 2^(7 (3-L)), lo[c] = sum_{L>=4}
+// lev[L][c] 2^(7 (7-L)), exact in int64.
+template <int R, int N, int P0>
+__device__ __forceinline__ void qs_epilogue_half(uint32_t trow, long long (&hi)[R],
+                                                 long long (&lo)[R]) {
+  int lev[kQsS][R];
+#pragma unroll
+  for (int L = 0; L < kQsS; ++L)
+#pragma unroll
+    for (int c = 0; c < R; ++c) lev[L][c] = 0;
+#pragma unroll
+  for (int pp = 0; pp < 4; ++pp) {
+    const int p = P0 + pp;
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      if (c0 / R > kQsS - 1 - p) continue;    // no kept pair in these columns
+      uint32_t v[16];
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                     "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                     "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                   : "r"(trow + (uint32_t)(p * N + c0)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int n = c0 + j;
+        const int q = n / R, c = n % R;
+        if (n < 8 * R && p + q <= kQsS - 1) lev[p + q][c] += qs_f32_int(v[j]);
+      }
     }
+  }
+#pragma unroll
+  for (int c = 0; c < R; ++c) {
+    long long h = 0, l = 0;
+#pragma unroll
+    for (int L = 0; L < 4; ++L) h += (long long)lev[L][c] << (kQsBits * (3 - L));
+#pragma unroll
+    for (int L = 4; L < kQsS; ++L) l += (long long)lev[L][c] << (kQsBits * (7 - L));
+    hi[c] = h;
+    lo[c] = l;
   }
 }
 
 // One CTA per (128-row tile mt, K range ks of kQsKper positions):
 //   partial[(ks M + row) R + c] = sum_{k in range} Q-copy(row, k) B(k, c).
-// Warp 0 lane 0 streams the 32 KB stages of the A copy with bulk copies;
-// warp 1 lane 0 issues the MMAs (8 per stage, one per Q slice); all warps
-// split B into shared memory first and run the FP64 epilogue last.
+// Warp 0 lane 0 streams the 32 KB stages of the A copy with bulk copies (the
+// first ones before B is split); warp 1 lane 0 issues the MMAs (8 per stage,
+// one per Q slice); all warps split B into shared memory and run the
+// epilogue.
 template <int R>
 __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restrict__ As, int M,
                                                           int KT, int K,
                                                           const double* __restrict__ B,
-                                                          int64_t bks, int64_t bcs,
-                                                          const int* __restrict__ eB, int eA,
+                                                          int64_t bks, int64_t bcs, int eA,
                                                           double* __restrict__ partial,
                                                           uint32_t* __restrict__ flags) {
   constexpr int N = (8 * R + 15) / 16 * 16;
+  constexpr int kVals = (kQsKper * R + kQsThreads - 1) / kQsThreads;   // B values per thread
   // no-swizzle operands and bulk copies need 16-byte alignment only; a
   // smaller alignment keeps the static part small (two CTAs per SM)
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t* sA = smem;
   uint8_t* sB = smem + kQsStages * kQsStage;
   __shared__ __align__(8) uint64_t full[kQsStages], empty[kQsStages], done;
+  __shared__ unsigned long long cmax[4];
+  __shared__ int s_e[4];
   __shared__ uint32_t tmem_base;
   __shared__ int failed_s;
   volatile int& failed = failed_s;
@@ -184,7 +256,9 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
   const int k0 = ks * kQsKper;
   const int kn = min(kQsKper, K - k0);
   const int ns = (kn + kQsKC - 1) / kQsKC;
+  const int kt0 = k0 / kQsKC;
   if (tid == 0) failed = 0;
+  if (tid < 4) cmax[tid] = 0ull;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  :: "r"(tc::smem_u32(&tmem_base)), "r"(kQsS * N) : "memory");
@@ -198,21 +272,60 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc::smem_u32(&done)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // B digits: rows q R + c (q = digit plane, c = column), K positions of this range
   {
     uint4* z = reinterpret_cast<uint4*>(sB);
     for (int e = tid; e < N * kQsKper * 2 / 16; e += kQsThreads) z[e] = make_uint4(0, 0, 0, 0);
   }
   __syncthreads();
-  for (int e = tid; e < kn * R; e += kQsThreads) {
-    const int c = e / kn, k = e - c * kn;
-    double x = ldexp(B[(int64_t)(k0 + k) * bks + (int64_t)c * bcs], -eB[c]);
+  auto issue = [&](int st) {
+    const int slot = st % kQsStages;
+    const uint8_t* src = As + ((int64_t)mt * KT + kt0 + st) * kQsStage;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(tc::smem_u32(&full[slot])), "r"((uint32_t)kQsStage) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(tc::smem_u32(sA + slot * kQsStage)), "l"(src), "r"((uint32_t)kQsStage),
+                    "r"(tc::smem_u32(&full[slot])) : "memory");
+  };
+  if (tid == 0)
+    for (int st = 0; st < min(ns, kQsStages); ++st) issue(st);
+  // B digits: rows q R + c (q = digit plane, c = column) of this K range,
+  // with the exponent of each column's largest magnitude in the range
+  double bv[kVals];
+  unsigned long long mx[R];
 #pragma unroll
-    for (int q = 0; q < kQsS; ++q) {
-      const double t0 = x * 128.0;
-      const double n0 = rint(t0);
-      x = t0 - n0;
-      *reinterpret_cast<uint16_t*>(sB + qs_offset(q * R + c, k, kQsSboB)) = bf16_bits((float)n0);
+  for (int c = 0; c < R; ++c) mx[c] = 0ull;
+#pragma unroll
+  for (int u = 0; u < kVals; ++u) {
+    const int e = tid + u * kQsThreads;
+    bv[u] = 0.0;
+    if (e < kn * R) {
+      const int c = e / kn, k = e - c * kn;
+      bv[u] = B[(int64_t)(k0 + k) * bks + (int64_t)c * bcs];
+      const unsigned long long a = (unsigned long long)__double_as_longlong(bv[u]) & ~(1ull << 63);
+#pragma unroll
+      for (int cc = 0; cc < R; ++cc)
+        if (c == cc && a > mx[cc]) mx[cc] = a;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < R; ++c)
+    if (mx[c]) atomicMax(&cmax[c], mx[c]);
+  __syncthreads();
+  if (tid < R) {
+    const unsigned long long a = cmax[tid];
+    s_e[tid] = a ? (int)((a >> 52) & 0x7FF) - 1022 : 0;     // 2^e > max |B(:, c)|
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kVals; ++u) {
+    const int e = tid + u * kQsThreads;
+    if (e < kn * R) {
+      const int c = e / kn, k = e - c * kn;
+      int n[kQsS];
+      qs_digits(bv[u], s_e[c], n);
+#pragma unroll
+      for (int q = 0; q < kQsS; ++q)
+        *reinterpret_cast<uint16_t*>(sB + qs_offset(q * R + c, k, kQsSboB)) = (uint16_t)bf16_int(n[q]);
     }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -220,24 +333,17 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const int kt0 = k0 / kQsKC;
   if (tid == 0) {
     // producer: stage st into slot st % kQsStages once the MMAs of stage
     // st - kQsStages have released it
-    for (int st = 0; st < ns; ++st) {
+    for (int st = kQsStages; st < ns; ++st) {
       const int slot = st % kQsStages;
-      if (st >= kQsStages &&
-          !tc::mbar_wait(tc::smem_u32(&empty[slot]), (uint32_t)((st / kQsStages - 1) & 1), kQsSpin)) {
+      if (!tc::mbar_wait(tc::smem_u32(&empty[slot]), (uint32_t)((st / kQsStages - 1) & 1), kQsSpin)) {
         failed = 1;
         break;
       }
       if (failed) break;
-      const uint8_t* src = As + ((int64_t)mt * KT + kt0 + st) * kQsStage;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                   :: "r"(tc::smem_u32(&full[slot])), "r"((uint32_t)kQsStage) : "memory");
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                   :: "r"(tc::smem_u32(sA + slot * kQsStage)), "l"(src), "r"((uint32_t)kQsStage),
-                      "r"(tc::smem_u32(&full[slot])) : "memory");
+      issue(st);
     }
   } else if (tid == 32) {
     // MMA issuer
@@ -280,48 +386,37 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
   // epilogue: warps w and w + 4 share lane quadrant w (tile rows 32 w ..
   // 32 w + 31); warp half h takes the Q slices p = 4 h .. 4 h + 3
   const int quad = warp & 3, half = warp >> 2;
-  double acc[R];
-#pragma unroll
-  for (int c = 0; c < R; ++c) acc[c] = 0.0;
+  const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
+  long long hi[R], lo[R];
   if (got) {
-#pragma unroll
-    for (int pp = 0; pp < 4; ++pp) {
-      const int p = 4 * half + pp;
-#pragma unroll
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        uint32_t v[16];
-        const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(p * N + c0);
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                       "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                       "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                     : "r"(ta));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int n = c0 + j;
-          const int q = n / R, c = n - (n / R) * R;
-          if (n < 8 * R && p + q <= kQsS - 1)
-            acc[c] += tc::f32_int_to_f64(v[j], -kQsBits * (p + q + 2));
-        }
-      }
-    }
+    if (half == 0)
+      qs_epilogue_half<R, N, 0>(trow, hi, lo);
+    else
+      qs_epilogue_half<R, N, 4>(trow, hi, lo);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();    // every MMA is complete: sB is free for the half sums
-  double* red = reinterpret_cast<double*>(sB);
+  long long* red = reinterpret_cast<long long*>(sB);
   const int rt = 32 * quad + lane;
   if (half == 1 && got) {
 #pragma unroll
-    for (int c = 0; c < R; ++c) red[rt * R + c] = acc[c];
+    for (int c = 0; c < R; ++c) {
+      red[(2 * rt) * R + c] = hi[c];
+      red[(2 * rt + 1) * R + c] = lo[c];
+    }
   }
   __syncthreads();
   if (half == 0 && got) {
     const int row = mt * kQsTM + rt;
     if (row < M) {
 #pragma unroll
-      for (int c = 0; c < R; ++c)
-        partial[((int64_t)ks * M + row) * R + c] = ldexp(acc[c] + red[rt * R + c], eA + eB[c]);
+      for (int c = 0; c < R; ++c) {
+        const long long h = hi[c] + red[(2 * rt) * R + c];
+        const long long l = lo[c] + red[(2 * rt + 1) * R + c];
+        const int sc = eA + s_e[c];
+        partial[((int64_t)ks * M + row) * R + c] =
+            fma(qs_i64_f64(h), qs_pow2(sc - 5 * kQsBits), qs_i64_f64(l) * qs_pow2(sc - 9 * kQsBits));
+      }
     }
   }
   if (tid == 0 && !got) atomicOr(flags, kFlagTimeout);
@@ -332,7 +427,7 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
 
 template <int R>
 void qs_mma_launch(const uint8_t* As, int M, int KT, int K, const double* B, int64_t bks,
-                   int64_t bcs, const int* eB, double* partial, uint32_t* flags, cudaStream_t st) {
+                   int64_t bcs, double* partial, uint32_t* flags, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_qs_mma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, kQsSmem);
@@ -340,18 +435,16 @@ void qs_mma_launch(const uint8_t* As, int M, int KT, int K, const double* B, int
   }
   const dim3 grid((unsigned)((M + kQsTM - 1) / kQsTM), (unsigned)((K + kQsKper - 1) / kQsKper));
   count_launches(1);
-  k_qs_mma<R><<<grid, kQsThreads, kQsSmem, st>>>(As, M, KT, K, B, bks, bcs, eB, 1, partial, flags);
+  k_qs_mma<R><<<grid, kQsThreads, kQsSmem, st>>>(As, M, KT, K, B, bks, bcs, 1, partial, flags);
 }
 
 void qs_product(const uint8_t* As, int M, int KT, int K, const double* B, int64_t bks, int64_t bcs,
-                int r, int* eB, double* partial, uint32_t* flags, cudaStream_t st) {
-  count_launches(1);
-  k_qs_colexp<<<r, 512, 0, st>>>(B, bks, bcs, K, eB);
+                int r, double* partial, uint32_t* flags, cudaStream_t st) {
   switch (r) {
-    case 1: qs_mma_launch<1>(As, M, KT, K, B, bks, bcs, eB, partial, flags, st); break;
-    case 2: qs_mma_launch<2>(As, M, KT, K, B, bks, bcs, eB, partial, flags, st); break;
-    case 3: qs_mma_launch<3>(As, M, KT, K, B, bks, bcs, eB, partial, flags, st); break;
-    default: qs_mma_launch<4>(As, M, KT, K, B, bks, bcs, eB, partial, flags, st); break;
+    case 1: qs_mma_launch<1>(As, M, KT, K, B, bks, bcs, partial, flags, st); break;
+    case 2: qs_mma_launch<2>(As, M, KT, K, B, bks, bcs, partial, flags, st); break;
+    case 3: qs_mma_launch<3>(As, M, KT, K, B, bks, bcs, partial, flags, st); break;
+    default: qs_mma_launch<4>(As, M, KT, K, B, bks, bcs, partial, flags, st); break;
   }
 }
 
@@ -376,28 +469,29 @@ bool qs_enabled(int64_t s, int m) { return m >= 256 && s >= 1024; }
 
 void qs_append_launch(const double* Q, const QsGeom& g, int m, int r, uint8_t* QA, uint8_t* QB,
                       cudaStream_t st) {
-  // a K tile of QB opened by this append gets its remaining columns zeroed
+  // a K tile of QB opened by this append is zeroed to its end
   const int last = m + r - 1;
   const bool opens = m == 0 || last / kQsKC != (m - 1) / kQsKC;
   const int je = opens ? std::min(g.KTB * kQsKC, (last / kQsKC + 1) * kQsKC) : m + r;
-  const int64_t work = (int64_t)r * 2 * g.KTA + g.s * (int64_t)(je - m);
+  const int g0 = m / 8, g1 = (je + 7) / 8;
+  const int64_t work = (int64_t)r * 2 * g.KTA + g.s * (int64_t)(g1 - g0);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 8));
   count_launches(1);
-  k_qs_append<<<blocks, 256, 0, st>>>(Q, g.s, m, r, je, QA, g.KTA, QB, g.KTB);
+  k_qs_append<<<blocks, 256, 0, st>>>(Q, g.s, m, r, g0, g1, QA, g.KTA, QB, g.KTB);
 }
 
 void qs_qt_launch(const QsGeom& g, const uint8_t* QA, int m, const double* w, int r, double* t,
-                  double* tpart, int* eB, uint32_t* flags, cudaStream_t st) {
+                  double* tpart, uint32_t* flags, cudaStream_t st) {
   // t (m x r, row-major) = Q^T w, w column-major (ld s)
-  qs_product(QA, m, g.KTA, (int)g.s, w, 1, g.s, r, eB, tpart, flags, st);
+  qs_product(QA, m, g.KTA, (int)g.s, w, 1, g.s, r, tpart, flags, st);
   qt_finish_launch(tpart, (int64_t)m * r, qs_chunks(g.s), t, st);
 }
 
 void qs_update_launch(const QsGeom& g, const uint8_t* QB, int m, const double* t, int r,
-                      const double* w_in, double* w_out, double* partial, int* eB,
-                      uint32_t* flags, cudaStream_t st) {
+                      const double* w_in, double* w_out, double* partial, uint32_t* flags,
+                      cudaStream_t st) {
   // w_out = w_in - Q t, t row-major (m x r)
-  qs_product(QB, (int)g.s, g.KTB, m, t, r, 1, r, eB, partial, flags, st);
+  qs_product(QB, (int)g.s, g.KTB, m, t, r, 1, r, partial, flags, st);
   q_update_finish_launch(w_in, w_out, partial, g.s, r, qs_chunks(m), st);
 }
 

@@ -1004,7 +1004,6 @@ struct Side {
   // BF16-sliced copies of Q for the tensor-core whitening products
   QsGeom qs;
   uint8_t *QA = nullptr, *QB = nullptr;
-  int* qexp = nullptr;
   bool qs_on = false;
   double* Ht = nullptr;
   int64_t ldH = 0;
@@ -1145,7 +1144,6 @@ struct Solver {
         sd.qs = qs_geometry(s, (int)mmax);
         SWS(QA, uint8_t, "QA", sd.qs.bytesA);
         SWS(QB, uint8_t, "QB", sd.qs.bytesB);
-        SWS(qexp, int, "qexp", 4);
         qpd = std::max({qpd, (size_t)qs_chunks(s) * mmax * r, (size_t)qs_chunks(mmax) * s * r});
       }
       SWS(qpartial, double, "qpartial", qpd);
@@ -1393,14 +1391,14 @@ struct Solver {
     auto qt = [&](const double* w, double* t) {
       ProfScope ps(h, F_QTDOT, st, sm8 + sr8 + 8.0 * m * r, 2.0 * s * m * r);
       if (tq)
-        qs_qt_launch(sd.qs, sd.QA, m, w, r, t, sd.qpartial, sd.qexp, h->flags, st);
+        qs_qt_launch(sd.qs, sd.QA, m, w, r, t, sd.qpartial, h->flags, st);
       else
         qt_dot_launch(sd.Q, s, s, m, w, r, t, sd.qpartial, st);
     };
     auto qupd = [&](const double* t, const double* w_in, double* w_out) {
       ProfScope ps(h, F_QUPDATE, st, sm8 + 2 * sr8 + 8.0 * m * r, 2.0 * s * m * r);
       if (tq)
-        qs_update_launch(sd.qs, sd.QB, m, t, r, w_in, w_out, sd.qpartial, sd.qexp, h->flags, st);
+        qs_update_launch(sd.qs, sd.QB, m, t, r, w_in, w_out, sd.qpartial, h->flags, st);
       else
         q_update_launch(sd.Q, s, s, m, t, r, w_in, w_out, sd.qpartial, nch, st);
     };

@@ -288,13 +288,13 @@ int qs_chunks(int64_t K);                  // K ranges (partial sums) of a produ
 bool qs_enabled(int64_t s, int m);         // the tensor-core products pay off
 void qs_append_launch(const double* Q, const QsGeom& g, int m, int r, uint8_t* QA, uint8_t* QB,
                       cudaStream_t st);
-// t (m x r, row-major) = Q^T w; tpart: qs_chunks(s) * m * r doubles; eB: r ints
+// t (m x r, row-major) = Q^T w; tpart: qs_chunks(s) * m * r doubles
 void qs_qt_launch(const QsGeom& g, const uint8_t* QA, int m, const double* w, int r, double* t,
-                  double* tpart, int* eB, uint32_t* flags, cudaStream_t st);
-// w_out = w_in - Q t; partial: qs_chunks(m) * s * r doubles; eB: r ints
+                  double* tpart, uint32_t* flags, cudaStream_t st);
+// w_out = w_in - Q t; partial: qs_chunks(m) * s * r doubles
 void qs_update_launch(const QsGeom& g, const uint8_t* QB, int m, const double* t, int r,
-                      const double* w_in, double* w_out, double* partial, int* eB,
-                      uint32_t* flags, cudaStream_t st);
+                      const double* w_in, double* w_out, double* partial, uint32_t* flags,
+                      cudaStream_t st);
 
 // ---------------------------------------------------------------- projected
 // partial: border_chunks(mp) * mp * r doubles of scratch
