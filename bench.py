@@ -172,8 +172,9 @@ def measured_peaks():
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return d.get("hbm_gbs"), d.get("bf16_tflops"), "measured"
-    return 6800.0, 1900.0, "fallback"
+        return (d.get("hbm_gbs"), d.get("bf16_tflops"), "measured",
+                d.get("bf16_tflops_sustained") or d.get("bf16_tflops"))
+    return 6800.0, 1900.0, "fallback", 1700.0
 
 
 def fp64_alu_peak(sm_count: int):
@@ -227,11 +228,27 @@ def replica_throughput(world: int, steps: int, ms_max: float) -> float:
 # two concurrent inversions of a sign step, whose trailing products run on
 # the tensor cores): reported in the table, not chosen for the roofline
 COMPOSITE_FAMILIES = ("gje_invert",)
+# with the tensor-core engine: FP64 products emulated on the tensor cores
+# (36 BF16 slice products per FP64 product), and the whitening products,
+# which read BF16-sliced copies of Q and are bound by HBM
+TENSOR_FAMILIES = ("gje_update_H", "gemm_f64", "x_accumulate")
+SLICED_FAMILIES = ("whiten_qt_dot", "whiten_q_update")
+OZAKI_PAIRS = 36
 
 
-def pick_roofline(prof: dict, hbm_gbs: float, fp64_tflops: float):
-    """Dominant single-kernel family by GPU time; bound by its algorithmic
-    intensity."""
+def family_bound(fam: str, p: dict, engine: str, balance: float) -> str:
+    if engine == "tensor" and fam in TENSOR_FAMILIES:
+        return "tensor"
+    if engine == "tensor" and fam in SLICED_FAMILIES:
+        return "hbm"
+    return "alu" if p["flops"] / max(p["bytes"], 1.0) > balance else "hbm"
+
+
+def pick_roofline(prof: dict, hbm_gbs: float, fp64_tflops: float, tensor_fp64_tflops: float = 0.0,
+                  engine: str = "fp64"):
+    """Dominant single-kernel family by GPU time, against the peak of the unit
+    that bounds it: the FP64 pipe (derived), HBM (measured copy), or the
+    tensor cores' FP64-equivalent rate (measured sustained BF16 rate / 36)."""
     if not prof:
         return None, {}
     cands = [k for k in prof if k not in COMPOSITE_FAMILIES] or list(prof)
@@ -240,11 +257,15 @@ def pick_roofline(prof: dict, hbm_gbs: float, fp64_tflops: float):
     ms_per_launch_group = p["ms"] / max(1, p["groups"])
     secs = p["ms"] * 1e-3
     balance = fp64_tflops * 1e12 / (hbm_gbs * 1e9)   # flop per byte
-    intensity = p["flops"] / max(p["bytes"], 1.0)
-    if intensity > balance:
+    bound = family_bound(fam, p, engine, balance)
+    if bound == "alu":
         achieved = p["flops"] / secs / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
                 "frac": achieved / fp64_tflops}
+    elif bound == "tensor":
+        achieved = p["flops"] / secs / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tensor_fp64_tflops,
+                "unit": "TFLOP/s", "frac": achieved / tensor_fp64_tflops}
     else:
         achieved = p["bytes"] / secs / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
@@ -257,7 +278,8 @@ def pick_roofline(prof: dict, hbm_gbs: float, fp64_tflops: float):
     table = {k: {"ms": round(v["ms"], 3), "share": round(v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values())), 4),
                  "launches": v["launches"],
                  "GBps": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
-                 "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4)}
+                 "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4),
+                 "bound": family_bound(k, v, engine, fp64_tflops * 1e3 / hbm_gbs)}
              for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"]) if v["ms"] > 0}
     return roof, table
 
@@ -409,7 +431,7 @@ def run_spk(args, rank, world, local, pg):
     dA, dB = spk.DeviceCSR(P.A), spk.DeviceCSR(P.BT)
     c1 = torch.as_tensor(P.C1, device="cuda")
     c2 = torch.as_tensor(P.C2, device="cuda")
-    hbm, bf16, peak_src = measured_peaks()
+    hbm, bf16, peak_src, bf16_sus = measured_peaks()
     fp64 = spk.fp64_peak(local)
     forms = [f for f in args.forms.split(",") if f]
     per_form = {}
@@ -513,11 +535,14 @@ def run_spk(args, rank, world, local, pg):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     fp64_peak, mhz = fp64_alu_peak(sms)
-    roof, table = pick_roofline(base["prof"] or {}, hbm, fp64_peak)
+    tensor_fp64 = bf16_sus / OZAKI_PAIRS
+    roof, table = pick_roofline(base["prof"] or {}, hbm, fp64_peak, tensor_fp64, args.engine)
     if roof is not None:
         roof["peak_source"] = (f"HBM: {peak_src} copy GB/s (MEASURED_PEAKS.json); FP64 ALU: derived, "
                                f"{sms} SMs x 2 FMA/clk x 2 flop x {mhz:.0f} MHz = {fp64_peak:.4f} "
-                               f"TFLOP/s (live FMA probe {fp64:.4f})")
+                               f"TFLOP/s (live FMA probe {fp64:.4f}); tensor: FP64-equivalent = "
+                               f"{peak_src} sustained BF16 {bf16_sus:.1f} TFLOP/s / {OZAKI_PAIRS} "
+                               f"slice products = {tensor_fp64:.2f} TFLOP/s")
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         s = oracle_sample_fresh(args.workload, opts, args.cpu_sample_iters, base["checks"], P.r)
@@ -578,7 +603,8 @@ def run_kernel_case(args):
         spk.profile_enable(False)
         Ys[engine] = Y
         fams = {k: {"ms": round(v["ms"], 2), "launches": v["launches"],
-                    "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4)}
+                    "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4),
+                 "bound": family_bound(k, v, engine, fp64_tflops * 1e3 / hbm_gbs)}
                 for k, v in prof.items() if v["ms"] > 0}
         out[engine] = {"newton_iters": it, "seconds": secs, "families": fams}
     if "tensor" in Ys and "fp64" in Ys:

@@ -47,6 +47,27 @@ def test_roofline_picks_the_dominant_family_and_its_bound(bench):
     assert roof["kernel"] == "stream" and "gje_invert" in table
 
 
+def test_roofline_bounds_of_the_tensor_core_engine(bench):
+    """With the tensor-core engine the emulated FP64 products are rated
+    against the tensor cores' FP64-equivalent peak (sustained BF16 / 36) and
+    the whitening products against HBM, whatever their FP64 intensity; with
+    the FP64 engine the intensity rule holds."""
+    prof = {
+        "gje_update_H": {"ms": 400.0, "groups": 4, "launches": 40, "bytes": 1e9, "flops": 4e12},
+        "whiten_qt_dot": {"ms": 300.0, "groups": 3, "launches": 30, "bytes": 6e11, "flops": 6e11},
+    }
+    roof, table = bench.pick_roofline(prof, 5000.0, 1.0, 1700.0 / 36, "tensor")
+    assert roof["kernel"] == "gje_update_H" and roof["bound"] == "tensor"
+    assert roof["achieved"] == pytest.approx(10.0) and roof["peak"] == pytest.approx(1700.0 / 36)
+    assert table["whiten_qt_dot"]["bound"] == "hbm"
+    roof, table = bench.pick_roofline(prof, 5000.0, 1.0, 1700.0 / 36, "fp64")
+    assert roof["bound"] == "alu" and table["whiten_qt_dot"]["bound"] == "alu"
+    prof["gje_update_H"]["ms"] = 100.0
+    roof, _ = bench.pick_roofline(prof, 5000.0, 1.0, 1700.0 / 36, "tensor")
+    assert roof["kernel"] == "whiten_qt_dot" and roof["bound"] == "hbm"
+    assert roof["achieved"] == pytest.approx(2000.0) and roof["frac"] == pytest.approx(0.4)
+
+
 def test_fp64_alu_peak_from_units_and_clock(bench):
     peak, mhz = bench.fp64_alu_peak(152)
     assert peak == pytest.approx(152 * 2 * 2 * mhz * 1e6 / 1e12)
