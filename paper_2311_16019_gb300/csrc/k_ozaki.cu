@@ -6,31 +6,33 @@
 //
 //   C = alpha op(A) op(B) + beta C,   op(A): M x K,  op(B): K x N,  FP64.
 //
-// Splitting.  Row i of op(A) is scaled by 2^-eA_i (eA_i: the exponent of its
-// largest magnitude, so that every scaled entry lies in (-1, 1)) and written
-// as a sum of kOzS slices, v = sum_p n_p 2^(-7 p), each n_p an integer with
-// |n_p| <= 128 (rounded to nearest, so the remainder after slice p is at most
-// 2^(-7 p - 1)); likewise column j of op(B) with eB_j.  The integers are
-// exact in BF16.  After 8 slices the remainder is below 2^-57 of the row's
-// largest entry: the splitting is exact to more than FP64's 53 bits.
+// Splitting.  Row i of op(A) is rounded to 56 bits relative to 2^eA_i (eA_i:
+// 2^eA_i above its largest magnitude) and written as a sum of kOzS slices,
+// v = 2^eA_i sum_p n_p 2^(-7 p), balanced base-2^7 digits taken from the
+// FP64 bit pattern on the integer pipe (|n_1| <= 128, n_p in [-64, 63] for
+// p >= 2); likewise column j of op(B) with eB_j.  The integers are exact in
+// BF16, and the remainder is below 2^-57 of the row's scale: the splitting
+// is exact to more than FP64's 53 bits.
 //
 // Products.  The (at most 8) slice pairs of one level L = p + q share one
 // FP32 accumulator in tensor memory over K-ranges of 256 (four chunks of 64
-// staged through shared memory): |n_1| <= 128 and |n_p| <= 64 for p >= 2,
-// so a level sum is at most 256 (2 2^13 + 6 2^12) < 2^24 in magnitude (2^22
-// for L = 2) and every level sum is EXACT in FP32.  Levels 2 .. 9 (the 36
-// pairs with p + q <= 9; the pairs left out are below 2^-58 of |row| |col|
-// per product) live side by side in the 512 columns of tensor memory.  The
-// epilogue adds 2^(-7 L) D_L to FP64 accumulators held in registers, range
-// after range, converting the FP32 integers to FP64 by bit operations on the
-// integer pipe (one FP64 addition per level and element), and finally
-// scales by alpha 2^(eA_i + eB_j).
+// staged through shared memory): a level sum is at most
+// 256 (2 2^13 + 6 2^12) < 2^24 in magnitude (2^22 for L = 2), so every
+// level sum is EXACT in FP32.  Levels 2 .. 9 (the 36 pairs with p + q <= 9;
+// the pairs left out are below 2^-58 of |row| |col| per product) live side
+// by side in the 512 columns of tensor memory.  The epilogue reads each
+// level sum as an integer and adds it, shifted by its weight, to one of two
+// exact 64-bit integer accumulators per element (levels 2..5 and 6..9),
+// range after range, all on the integer pipe; at the end the two are
+// converted to FP64 (exact below 2^53) and scaled by alpha 2^(eA_i + eB_j).
+// GB300's FP64 pipe retires 2 FMAs per clock per SM, so FP64 arithmetic is
+// kept to three operations per element of C.
 //
 // Kernels: k_oz_rowexp (the exponents), k_oz_split (slices, written in the
 // tensor cores' shared-memory operand layout: 8-row x 16-byte core matrices,
 // K-major, no swizzle), k_oz_mma (one CTA per 128 x 64 tile of C; one thread
 // issues the bulk copies of the chunk's slices and the tcgen05.mma
-// instructions, all eight warps read tensor memory for the FP64 epilogue).
+// instructions, all eight warps read tensor memory for the epilogue).
 #include "spk_internal.cuh"
 #include "tc_common.cuh"
 
@@ -70,26 +72,35 @@ struct View {
 // 2^e > max |row|, e = 0 for a zero row.  One thread per row (rs == 1) or
 // one warp per row (ks == 1).
 __global__ void k_oz_rowexp(View v, int rows, int K, int rows_pad, int* __restrict__ e) {
+  // magnitudes compared as FP64 bit patterns with the sign cleared (the
+  // order of non-negative doubles), on the integer pipe
+  const unsigned long long kMag = ~(1ull << 63);
   if (v.rs == 1) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows_pad; i += gridDim.x * blockDim.x) {
-      double mx = 0.0;
+      unsigned long long mx = 0ull;
       if (i < rows)
-        for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(v.p[i + k * v.ks]));
-      int ex = 0;
-      if (mx > 0.0) frexp(mx, &ex);
-      e[i] = ex;
+        for (int k = 0; k < K; ++k) {
+          const unsigned long long a = (unsigned long long)__double_as_longlong(v.p[i + k * v.ks]) & kMag;
+          mx = a > mx ? a : mx;
+        }
+      e[i] = tc::exp_above(mx);
     }
   } else {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < rows_pad; i += warps) {
-      double mx = 0.0;
+      unsigned long long mx = 0ull;
       if (i < rows)
-        for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(v.p[i * v.rs + (int64_t)k * v.ks]));
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      int ex = 0;
-      if (mx > 0.0) frexp(mx, &ex);
-      if (lane == 0) e[i] = ex;
+        for (int k = lane; k < K; k += 32) {
+          const unsigned long long a =
+              (unsigned long long)__double_as_longlong(v.p[i * v.rs + (int64_t)k * v.ks]) & kMag;
+          mx = a > mx ? a : mx;
+        }
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+      }
+      if (lane == 0) e[i] = tc::exp_above(mx);
     }
   }
 }
@@ -118,12 +129,12 @@ __global__ void k_oz_split(View v, int rows, int K, const int* __restrict__ e, i
       i = t - g * rows_pad;
     }
     const int64_t k0 = g * 8;
-    double x[8];
     const int ei = i < rows ? e[i] : 0;
+    int n[8][kOzS];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int64_t k = k0 + u;
-      x[u] = (i < rows && k < K) ? ldexp(v.p[i * v.rs + k * v.ks], -ei) : 0.0;
+      tc::digits8((i < rows && k < K) ? v.p[i * v.rs + k * v.ks] : 0.0, ei, n[u]);
     }
     const int rt = (int)(i / TR), kt = (int)(k0 / kOzKC);
     uint4* o = reinterpret_cast<uint4*>(out + ((int64_t)rt * KT + kt) * tile +
@@ -132,14 +143,7 @@ __global__ void k_oz_split(View v, int rows, int K, const int* __restrict__ e, i
     for (int p = 0; p < kOzS; ++p) {
       uint32_t w[4];
 #pragma unroll
-      for (int u = 0; u < 8; u += 2) {
-        const double t0 = x[u] * 128.0, t1 = x[u + 1] * 128.0;
-        const double n0 = rint(t0), n1 = rint(t1);
-        x[u] = t0 - n0;
-        x[u + 1] = t1 - n1;
-        const __nv_bfloat162 b = __floats2bfloat162_rn((float)n0, (float)n1);
-        w[u / 2] = *reinterpret_cast<const uint32_t*>(&b);
-      }
+      for (int u = 0; u < 8; u += 2) w[u / 2] = tc::bf16_int(n[u][p]) | (tc::bf16_int(n[u + 1][p]) << 16);
       o[p * (slice / 8)] = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
@@ -191,9 +195,11 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_mma(const uint8_t* __restr
   // 32 w .. 32 w + 31 of the tile) and take one half of the columns each
   const int quad = warp & 3, half = warp >> 2;
   constexpr int kCols = kOzTN / 2;
-  double acc[kCols];
+  // exact integer accumulators: hi = sum over levels L = 0..3 of the level
+  // sums 2^(7 (3-L)), lo likewise over L = 4..7 (weights 2^-35 and 2^-63)
+  long long hi[kCols], lo[kCols];
 #pragma unroll
-  for (int j = 0; j < kCols; ++j) acc[j] = 0.0;
+  for (int j = 0; j < kCols; ++j) hi[j] = lo[j] = 0;
   for (int kt = 0; kt < KT; ++kt) {
     const uint32_t parity = kt & 1;
     if (tid == 0) {
@@ -245,24 +251,29 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_mma(const uint8_t* __restr
     // the level sums stay in tensor memory until the end of a 256-wide range
     if ((kt % kOzEpi) != kOzEpi - 1 && kt != KT - 1) continue;
     // FP64 epilogue: row 32 warp + lane of the tile, 64 columns per level
+    // levels lv0 .. lv0 + 3 into acc, level lv weighted 2^(7 (lv0 + 3 - lv))
+    auto levels = [&](long long (&acc)[kCols], int lv0) {
 #pragma unroll 1
-    for (int lv = 0; lv < kOzLevels; ++lv) {
-      const int sh = -kOzBits * (lv + 2);
+      for (int lv = lv0; lv < lv0 + 4; ++lv) {
+        const int sh = kOzBits * (lv0 + 3 - lv);
 #pragma unroll
-      for (int c0 = 0; c0 < kCols; c0 += 16) {
-        uint32_t r[16];
-        const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) +
-                            (uint32_t)(lv * kOzTN + half * kCols + c0);
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                       "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                       "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                     : "r"(ta));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int c0 = 0; c0 < kCols; c0 += 16) {
+          uint32_t r[16];
+          const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) +
+                              (uint32_t)(lv * kOzTN + half * kCols + c0);
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                         "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                         "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                       : "r"(ta));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[c0 + j] += tc::f32_int_to_f64(r[j], sh);
+          for (int j = 0; j < 16; ++j) acc[c0 + j] += (long long)tc::f32_int(r[j]) << sh;
+        }
       }
-    }
+    };
+    levels(hi, 0);
+    levels(lo, 4);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
   }
@@ -277,7 +288,9 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_mma(const uint8_t* __restr
         const int col = nt * kOzTN + half * kCols + j;
         if (col < N) {
           double* c = C + (int64_t)col * ldc + row;
-          const double v = alpha * ldexp(acc[j], ea + eB[col]);
+          const int sc = ea + eB[col];
+          const double v = alpha * (tc::i64_f64(hi[j], sc - 5 * kOzBits) +
+                                    tc::i64_f64(lo[j], sc - 9 * kOzBits));
           *c = beta == 0.0 ? v : fma(beta, *c, v);
         }
       }

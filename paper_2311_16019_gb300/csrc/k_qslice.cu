@@ -77,51 +77,17 @@ __host__ __device__ __forceinline__ uint32_t qs_offset(int i, int k, uint32_t sb
   return (uint32_t)((i >> 3) * sbo + (k >> 3) * kQsLbo + (i & 7) * 16 + (k & 7) * 2);
 }
 
-// Balanced base-2^7 digits of N = rint(x 2^(56-e)) for |x| < 2^e, from the
-// FP64 bit pattern on the integer pipe: n[0] is the leading digit (|n[0]| <=
-// 128), n[1..7] lie in [-64, 63]; x = 2^e sum_p n[p] 2^(-7 (p+1)) + rest,
-// |rest| <= 2^(e-57).
-__device__ __forceinline__ void qs_digits(double x, int e, int (&n)[kQsS]) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const int E = (int)((u >> 52) & 0x7FF);
-  long long N = 0;
-  if (E != 0) {
-    const unsigned long long M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = E - 1023 - e + 4;     // x 2^(56-e) = M 2^sh, sh <= 3 as |x| < 2^e
-    if (sh >= 0)
-      N = (long long)(M << sh);
-    else if (sh > -54)
-      N = (long long)((M + (1ull << (-sh - 1))) >> (-sh));
-    if (u >> 63) N = -N;
-  }
-#pragma unroll
-  for (int p = kQsS - 1; p >= 1; --p) {
-    const int d = (int)((N + 64) & 127) - 64;
-    n[p] = d;
-    N = (N - d) >> kQsBits;
-  }
-  n[0] = (int)N;
-}
-
-// BF16 bit pattern of an integer with |n| <= 256 (exact).
-__device__ __forceinline__ uint32_t bf16_int(int n) {
-  if (n == 0) return 0u;
-  const uint32_t a = (uint32_t)(n < 0 ? -n : n);
-  const int pos = 31 - __clz(a);
-  return (n < 0 ? 0x8000u : 0u) | ((uint32_t)(127 + pos) << 7) | ((a << (7 - pos)) & 0x7Fu);
-}
-
 // 8 values (8 consecutive K positions of one row) -> one 16-byte core-matrix
 // row per slice at base + p * kQsSliceTile.
 __device__ __forceinline__ void qs_store_row8(const double (&x)[8], int e, uint8_t* base) {
   int n[8][kQsS];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) qs_digits(x[u], e, n[u]);
+  for (int u = 0; u < 8; ++u) tc::digits8(x[u], e, n[u]);
 #pragma unroll
   for (int p = 0; p < kQsS; ++p) {
     uint32_t w[4];
 #pragma unroll
-    for (int u = 0; u < 8; u += 2) w[u / 2] = bf16_int(n[u][p]) | (bf16_int(n[u + 1][p]) << 16);
+    for (int u = 0; u < 8; u += 2) w[u / 2] = tc::bf16_int(n[u][p]) | (tc::bf16_int(n[u + 1][p]) << 16);
     *reinterpret_cast<uint4*>(base + (int64_t)p * kQsSliceTile) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
@@ -168,16 +134,6 @@ __global__ void k_qs_append(const double* __restrict__ Q, int64_t s, int m, int 
 // Integer value of an FP32 accumulator holding an integer of magnitude < 2^22.
 __device__ __forceinline__ int qs_f32_int(uint32_t f) {
   return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
-}
-
-// FP64 value of an integer of magnitude < 2^51 (one FP64 addition).
-__device__ __forceinline__ double qs_i64_f64(long long x) {
-  return __longlong_as_double(0x4338000000000000LL + x) - 6755399441055744.0;
-}
-
-// 2^k as an FP64 bit pattern (ldexp outside the normal range).
-__device__ __forceinline__ double qs_pow2(int k) {
-  return (k > -1023 && k < 1024) ? __longlong_as_double((long long)(1023 + k) << 52) : ldexp(1.0, k);
 }
 
 // Level sums of one half of the Q slices (p = P0 .. P0 + 3) for one tile row:
@@ -313,7 +269,7 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
   __syncthreads();
   if (tid < R) {
     const unsigned long long a = cmax[tid];
-    s_e[tid] = a ? (int)((a >> 52) & 0x7FF) - 1022 : 0;     // 2^e > max |B(:, c)|
+    s_e[tid] = tc::exp_above(a);     // 2^e > max |B(:, c)|
   }
   __syncthreads();
 #pragma unroll
@@ -322,10 +278,10 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
     if (e < kn * R) {
       const int c = e / kn, k = e - c * kn;
       int n[kQsS];
-      qs_digits(bv[u], s_e[c], n);
+      tc::digits8(bv[u], s_e[c], n);
 #pragma unroll
       for (int q = 0; q < kQsS; ++q)
-        *reinterpret_cast<uint16_t*>(sB + qs_offset(q * R + c, k, kQsSboB)) = (uint16_t)bf16_int(n[q]);
+        *reinterpret_cast<uint16_t*>(sB + qs_offset(q * R + c, k, kQsSboB)) = (uint16_t)tc::bf16_int(n[q]);
     }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -415,7 +371,7 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
         const long long l = lo[c] + red[(2 * rt + 1) * R + c];
         const int sc = eA + s_e[c];
         partial[((int64_t)ks * M + row) * R + c] =
-            fma(qs_i64_f64(h), qs_pow2(sc - 5 * kQsBits), qs_i64_f64(l) * qs_pow2(sc - 9 * kQsBits));
+            tc::i64_f64(h, sc - 5 * kQsBits) + tc::i64_f64(l, sc - 9 * kQsBits);
       }
     }
   }
