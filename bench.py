@@ -603,8 +603,7 @@ def run_kernel_case(args):
         spk.profile_enable(False)
         Ys[engine] = Y
         fams = {k: {"ms": round(v["ms"], 2), "launches": v["launches"],
-                    "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4),
-                 "bound": family_bound(k, v, engine, fp64_tflops * 1e3 / hbm_gbs)}
+                    "TFLOPs": round(v["flops"] / max(v["ms"], 1e-9) / 1e9, 4)}
                 for k, v in prof.items() if v["ms"] > 0}
         out[engine] = {"newton_iters": it, "seconds": secs, "families": fams}
     if "tensor" in Ys and "fp64" in Ys:
