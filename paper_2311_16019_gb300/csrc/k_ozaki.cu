@@ -105,7 +105,8 @@ __global__ void k_oz_rowexp(View v, int rows, int K, int rows_pad, int* __restri
   }
 }
 
-// Slices of the view: out[((p * RT + rt) * KT + kt) * tile + oz_offset(i % TR, k % KC)]
+// Slices of the view: out[(((rt * KT + kt) * kOzS + p) * tile + oz_offset(i % TR, k % KC)]
+// (the 8 slice tiles of one tile and K chunk are contiguous: one bulk copy)
 // = n_p(i, k) for the tiles of TR rows and kOzKC columns; padding is zero.
 // One thread per row and group of 8 consecutive k (one 16-byte row of a
 // core matrix): 8 loads, and one 16-byte store per slice.
@@ -115,7 +116,6 @@ __global__ void k_oz_split(View v, int rows, int K, const int* __restrict__ e, i
   const int64_t rows_pad = (int64_t)RT * TR, groups = (int64_t)KT * (kOzKC / 8);
   const int64_t total = rows_pad * groups;
   const int64_t tile = (int64_t)TR * kOzKC;
-  const int64_t slice = (int64_t)RT * KT * tile;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     // consecutive threads take consecutive rows (coalesced when the view's
@@ -137,14 +137,14 @@ __global__ void k_oz_split(View v, int rows, int K, const int* __restrict__ e, i
       tc::digits8((i < rows && k < K) ? v.p[i * v.rs + k * v.ks] : 0.0, ei, n[u]);
     }
     const int rt = (int)(i / TR), kt = (int)(k0 / kOzKC);
-    uint4* o = reinterpret_cast<uint4*>(out + ((int64_t)rt * KT + kt) * tile +
+    uint4* o = reinterpret_cast<uint4*>(out + ((int64_t)rt * KT + kt) * kOzS * tile +
                                         oz_offset((int)(i % TR), (int)(k0 % kOzKC)) / 2);
 #pragma unroll
     for (int p = 0; p < kOzS; ++p) {
       uint32_t w[4];
 #pragma unroll
       for (int u = 0; u < 8; u += 2) w[u / 2] = tc::bf16_int(n[u][p]) | (tc::bf16_int(n[u + 1][p]) << 16);
-      o[p * (slice / 8)] = make_uint4(w[0], w[1], w[2], w[3]);
+      o[p * (tile / 8)] = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
@@ -205,16 +205,18 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_mma(const uint8_t* __restr
     if (tid == 0) {
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                    :: "r"(smem_u32(&bar_load)), "r"((uint32_t)kOzSmem) : "memory");
-      for (int p = 0; p < kOzS; ++p) {
-        const uint8_t* src = As + (((int64_t)p * MT + mt) * KT + kt) * kOzATile;
+      // the chunk's 8 A slice tiles and 8 B slice tiles are contiguous: two
+      // bulk copies (many small copies are processed one after another)
+      {
+        const uint8_t* src = As + ((int64_t)mt * KT + kt) * kOzS * kOzATile;
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     :: "r"(smem_u32(sA + p * kOzATile)), "l"(src), "r"((uint32_t)kOzATile),
+                     :: "r"(smem_u32(sA)), "l"(src), "r"((uint32_t)(kOzS * kOzATile)),
                         "r"(smem_u32(&bar_load)) : "memory");
       }
-      for (int q = 0; q < kOzS; ++q) {
-        const uint8_t* src = Bs + (((int64_t)q * NT + nt) * KT + kt) * kOzBTile;
+      {
+        const uint8_t* src = Bs + ((int64_t)nt * KT + kt) * kOzS * kOzBTile;
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     :: "r"(smem_u32(sB + q * kOzBTile)), "l"(src), "r"((uint32_t)kOzBTile),
+                     :: "r"(smem_u32(sB)), "l"(src), "r"((uint32_t)(kOzS * kOzBTile)),
                         "r"(smem_u32(&bar_load)) : "memory");
       }
       if (!oz_wait(smem_u32(&bar_load), parity)) {
