@@ -185,21 +185,37 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const uint8_t* __rest
                                                     const uint8_t* __restrict__ Bs,
                                                     const int* __restrict__ eA,
                                                     const int* __restrict__ eB, int M, int N,
-                                                    int MT, int NT, int KT, double alpha,
-                                                    double beta, double* __restrict__ C,
-                                                    int64_t ldc, uint32_t* __restrict__ flags) {
+                                                    int MT, int NT, int KT, int S, int ups,
+                                                    double alpha, double beta,
+                                                    double* __restrict__ C, int64_t ldc,
+                                                    double* __restrict__ partial,
+                                                    uint32_t* __restrict__ flags) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[kOzStages], empty[kOzStages], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base;
   __shared__ int failed_s;
   volatile int& failed = failed_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ntiles = MT * NT;
+  // work items: (tile, K split), the tile's column block fastest so that the
+  // CTAs sharing a block of A rows run together; item w covers the units
+  // (kOzRange K positions each) ups w_s .. ups (w_s + 1) - 1 of its tile
+  const int nitems = MT * NT * S;
   constexpr int kPerRange = kOzRange / kOzKS;
   const int nr = (KT + kPerRange - 1) / kPerRange;     // units per tile
-  int mytiles = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) ++mytiles;
-  const int64_t total = (int64_t)mytiles * KT;          // stages of this CTA
+  auto item = [&](int w, int& mt, int& nt, int& r0, int& r1) {
+    nt = w % NT;
+    const int rest = w / NT;
+    const int sk = rest % S;
+    mt = rest / S;
+    r0 = sk * ups;
+    r1 = min(nr, r0 + ups);
+  };
+  int64_t total = 0;                                    // stages of this CTA
+  for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+    int mt, nt, r0, r1;
+    item(w, mt, nt, r0, r1);
+    total += min(KT, r1 * kPerRange) - r0 * kPerRange;
+  }
   if (tid == 0) failed = 0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -224,9 +240,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const uint8_t* __rest
   if (warp == 0) {
     if (lane == 0) {
       int64_t g = 0;
-      for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-        const int mt = tile % MT, nt = tile / MT;
-        for (int kt = 0; kt < KT; ++kt, ++g) {
+      for (int w = blockIdx.x; w < nitems && !failed; w += gridDim.x) {
+        int mt, nt, r0, r1;
+        item(w, mt, nt, r0, r1);
+        for (int kt = r0 * kPerRange; kt < min(KT, r1 * kPerRange); ++kt, ++g) {
           const int slot = (int)(g % kOzStages);
           const int64_t use = g / kOzStages;
           if (use > 0 && !oz_wait(smem_u32(&empty[slot]), (uint32_t)((use - 1) & 1))) {
@@ -251,8 +268,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const uint8_t* __rest
     if (lane == 0) {
       constexpr uint32_t idesc = tc::idesc_bf16(kOzTM, kOzTN);
       int64_t g = 0, u = 0;
-      for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-        for (int r = 0; r < nr && !failed; ++r, ++u) {
+      for (int w = blockIdx.x; w < nitems && !failed; w += gridDim.x) {
+        int mt, nt, r0, r1;
+        item(w, mt, nt, r0, r1);
+        for (int r = r0; r < r1 && !failed; ++r, ++u) {
           const int set = (int)(u & 1);
           const int64_t uses = u >> 1;
           if (uses > 0 && !oz_wait(smem_u32(&tempty[set]), (uint32_t)((uses - 1) & 1))) {
@@ -306,10 +325,11 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const uint8_t* __rest
 #pragma unroll
     for (int j = 0; j < kOzTN; ++j) hi[j] = lo[j] = 0;
     int64_t u = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      const int mt = tile % MT, nt = tile / MT;
+    for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
+      int mt, nt, r0, r1;
+      item(w, mt, nt, r0, r1);
       bool stop = false;
-      for (int r = 0; r < nr; ++r, ++u) {
+      for (int r = r0; r < r1; ++r, ++u) {
         const int set = (int)(u & 1);
         bool got = !failed && oz_wait(smem_u32(&tfull[set]), (uint32_t)((u >> 1) & 1));
         got = __all_sync(0xffffffffu, got);        // the loads below are .aligned
@@ -353,11 +373,17 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const uint8_t* __rest
         for (int j = 0; j < kOzTN; ++j) {
           const int col = nt * kOzTN + j;
           if (col < N) {
-            double* c = C + (int64_t)col * ldc + row;
             const int sc = ea + eB[col];
             const double v = alpha * (tc::i64_f64(hi[j], sc - 5 * kOzBits) +
                                       tc::i64_f64(lo[j], sc - 9 * kOzBits));
-            *c = beta == 0.0 ? v : fma(beta, *c, v);
+            if (S == 1) {
+              double* c = C + (int64_t)col * ldc + row;
+              *c = beta == 0.0 ? v : fma(beta, *c, v);
+            } else {
+              // K split: partial sums (column-major M x N per split), added
+              // in split order by k_oz_reduce
+              partial[((int64_t)(r0 / ups) * N + col) * M + row] = v;
+            }
           }
         }
       }
@@ -372,6 +398,20 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const uint8_t* __rest
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                  :: "r"(tmem), "r"(2 * kOzSetCols) : "memory");
+}
+
+// C = beta C + sum over the S splits (in order) of the partial products.
+__global__ void k_oz_reduce(const double* __restrict__ partial, int M, int N, int S, double beta,
+                            double* __restrict__ C, int64_t ldc) {
+  const int64_t count = (int64_t)M * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = partial[e];
+    for (int k = 1; k < S; ++k) s += partial[(int64_t)k * count + e];
+    const int64_t col = e / M, row = e - col * M;
+    double* c = C + col * ldc + row;
+    *c = beta == 0.0 ? s : fma(beta, *c, s);
+  }
 }
 
 int oz_grid(int64_t work, int block) {
@@ -390,13 +430,29 @@ int oz_sm_count() {
   return n;
 }
 
+// K splits: enough work items for about two per SM when the tiles alone are
+// fewer, each split at least one exact range of K.
+void oz_splits(int M, int N, int K, int* S, int* ups) {
+  const int64_t tiles = (int64_t)((M + kOzTM - 1) / kOzTM) * ((N + kOzTN - 1) / kOzTN);
+  const int nr = (K + kOzRange - 1) / kOzRange;
+  int want = tiles >= 2 * 152 ? 1 : (int)std::min<int64_t>(nr, (2 * 152 + tiles - 1) / tiles);
+  want = std::max(1, want);
+  *ups = (nr + want - 1) / want;
+  *S = (nr + *ups - 1) / *ups;
+}
+
 }  // namespace
 
+// Work of every product with M' <= M, N' <= N, K' <= K: the slices, the
+// exponents and the K-split partial sums, S' M' N' <= M N + 2 152 kOzTM kOzTN
+// doubles (a split happens only when the tiles, each kOzTM x kOzTN, number
+// fewer than 2 x 152).
 size_t ozaki_work_bytes(int M, int N, int K) {
   const int64_t MT = (M + kOzTM - 1) / kOzTM, NT = (N + kOzTN - 1) / kOzTN;
   const int64_t KT = (K + kOzKS - 1) / kOzKS;
   return (size_t)(MT * KT * kOzAStage + NT * KT * kOzBStage) +
-         sizeof(int) * (size_t)(MT * kOzTM + NT * kOzTN) + 1024;
+         sizeof(int) * (size_t)(MT * kOzTM + NT * kOzTN) + 1024 +
+         sizeof(double) * ((size_t)M * N + 2 * 152 * (size_t)kOzTM * kOzTN) + 256;
 }
 
 bool ozaki_enabled(int M, int N, int K) {
@@ -419,6 +475,13 @@ void ozaki_gemm(char ta, char tb, int M, int N, int K, double alpha, const doubl
   uint8_t* Bs = As + (size_t)MT * KT * kOzAStage;
   int* eA = reinterpret_cast<int*>(Bs + (size_t)NT * KT * kOzBStage);
   int* eB = eA + (size_t)MT * kOzTM;
+  int S = 1, ups = 1;
+  oz_splits(M, N, K, &S, &ups);
+  double* partial = nullptr;
+  if (S > 1) {
+    const uintptr_t p = reinterpret_cast<uintptr_t>(eB + (size_t)NT * kOzTN);
+    partial = reinterpret_cast<double*>((p + 255) & ~(uintptr_t)255);
+  }
   // op(A)(i, k) and B^T(j, k) = op(B)(k, j) as strided views
   const View va = ta == 'N' ? View{A, 1, lda} : View{A, lda, 1};
   const View vb = tb == 'N' ? View{B, ldb, 1} : View{B, 1, ldb};
@@ -431,9 +494,13 @@ void ozaki_gemm(char ta, char tb, int M, int N, int K, double alpha, const doubl
       va, M, K, eA, MT, KT, reinterpret_cast<__nv_bfloat16*>(As));
   k_oz_split<kOzTN><<<oz_grid((int64_t)NT * kOzTN * KT * (kOzKS / 8), 256), 256, 0, st>>>(
       vb, N, K, eB, NT, KT, reinterpret_cast<__nv_bfloat16*>(Bs));
-  const int grid = std::min(MT * NT, oz_sm_count());
-  k_oz_gemm<<<grid, kOzThreads, kOzSmem, st>>>(As, Bs, eA, eB, M, N, MT, NT, KT, alpha, beta, C,
-                                               ldc, flags);
+  const int grid = std::min(MT * NT * S, oz_sm_count());
+  k_oz_gemm<<<grid, kOzThreads, kOzSmem, st>>>(As, Bs, eA, eB, M, N, MT, NT, KT, S, ups, alpha,
+                                               beta, C, ldc, partial, flags);
+  if (S > 1) {
+    count_launches(1);
+    k_oz_reduce<<<oz_grid((int64_t)M * N, 256), 256, 0, st>>>(partial, M, N, S, beta, C, ldc);
+  }
 }
 
 }  // namespace spk
