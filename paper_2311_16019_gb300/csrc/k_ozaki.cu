@@ -339,27 +339,34 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_gemm(const uint8_t* __rest
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // levels lv0 .. lv0 + 3 into acc, level lv weighted 2^(7 (lv0 + 3 - lv))
-        auto levels = [&](long long (&acc)[kOzTN], int lv0) {
-#pragma unroll 1
-          for (int lv = lv0; lv < lv0 + 4; ++lv) {
-            const int sh = kOzBits * (lv0 + 3 - lv);
+        // two levels per round: both loads issued, then one wait (each
+        // wait is a round trip to tensor memory)
+        auto two_levels = [&](long long (&acc)[kOzTN], int lv, int sh0) {
+          uint32_t v[2][kOzTN];
 #pragma unroll
-            for (int c0 = 0; c0 < kOzTN; c0 += 16) {
-              uint32_t v[16];
-              asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                           : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                             "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                             "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                           : "r"(trow + (uint32_t)(set * kOzSetCols + lv * kOzTN + c0)));
-              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          for (int h = 0; h < 2; ++h)
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                         : "=r"(v[h][0]), "=r"(v[h][1]), "=r"(v[h][2]), "=r"(v[h][3]), "=r"(v[h][4]),
+                           "=r"(v[h][5]), "=r"(v[h][6]), "=r"(v[h][7]), "=r"(v[h][8]), "=r"(v[h][9]),
+                           "=r"(v[h][10]), "=r"(v[h][11]), "=r"(v[h][12]), "=r"(v[h][13]),
+                           "=r"(v[h][14]), "=r"(v[h][15]), "=r"(v[h][16]), "=r"(v[h][17]),
+                           "=r"(v[h][18]), "=r"(v[h][19]), "=r"(v[h][20]), "=r"(v[h][21]),
+                           "=r"(v[h][22]), "=r"(v[h][23]), "=r"(v[h][24]), "=r"(v[h][25]),
+                           "=r"(v[h][26]), "=r"(v[h][27]), "=r"(v[h][28]), "=r"(v[h][29]),
+                           "=r"(v[h][30]), "=r"(v[h][31])
+                         : "r"(trow + (uint32_t)(set * kOzSetCols + (lv + h) * kOzTN)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-              for (int j = 0; j < 16; ++j) acc[c0 + j] += (long long)tc::f32_int(v[j]) << sh;
-            }
-          }
+          for (int j = 0; j < kOzTN; ++j)
+            acc[j] += ((long long)tc::f32_int(v[0][j]) << sh0) +
+                      ((long long)tc::f32_int(v[1][j]) << (sh0 - kOzBits));
         };
-        levels(hi, 0);
-        levels(lo, 4);
+        // level lv of hi (lv < 4) weighs 2^(7 (3 - lv)), of lo 2^(7 (7 - lv))
+        two_levels(hi, 0, 3 * kOzBits);
+        two_levels(hi, 2, 1 * kOzBits);
+        two_levels(lo, 4, 3 * kOzBits);
+        two_levels(lo, 6, 1 * kOzBits);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0)
