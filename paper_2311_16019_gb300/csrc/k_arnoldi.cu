@@ -14,6 +14,7 @@
 // The second (two-pass) sweep re-runs spmm (no dots), update and the two
 // scalings with the stored coefficients, which reproduces U_j bit for bit.
 #include "spk_internal.cuh"
+#include "small_mat.cuh"
 
 #include <algorithm>
 
@@ -178,52 +179,55 @@ __global__ void __launch_bounds__(256) k_update_gram(TC* __restrict__ W, int64_t
 }
 
 // G = sum of partial Grams; R upper with R^T R = G; Rinv = R^{-1}.
-__global__ void k_chol_small(const double* __restrict__ partial, int nparts, int r,
+// Gram matrix from the partial sums, then its Cholesky factor (upper,
+// positive diagonal) and the factor's inverse, in registers.
+template <int R>
+__global__ void k_chol_small(const double* __restrict__ partial, int nparts,
                              double* __restrict__ Rout, double* __restrict__ Rinv,
                              uint32_t* flags, double rel_floor) {
-  __shared__ double G[kMaxR * kMaxR];
-  const int rr = r * r;
-  sum_partials(partial, nparts, rr, rr, G);
+  __shared__ double G[R * R];
+  sum_partials(partial, nparts, R * R, R * R, G);
   __syncthreads();
   if (threadIdx.x != 0) return;
-  double R[kMaxR][kMaxR] = {};
+  double U[R][R];
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int b = 0; b < R; ++b) U[a][b] = 0.0;
   double tr = 0.0;
-  bool bad = false;
-  for (int a = 0; a < r; ++a) tr += G[a * r + a];
-  if (!isfinite(tr)) bad = true;
-  for (int j = 0; j < r && !bad; ++j) {
-    double s = G[j * r + j];
-    for (int l = 0; l < j; ++l) s -= R[l][j] * R[l][j];
-    if (!(s > rel_floor * tr) || !(tr > 0.0)) {
-      atomicOr(flags, kFlagBreakdown);
-      s = (tr > 0.0 && isfinite(tr)) ? fmax(s, rel_floor * tr) : 1.0;
-      if (!(s > 0.0)) s = 1.0;
+#pragma unroll
+  for (int a = 0; a < R; ++a) tr += G[a * R + a];
+  const bool bad = !isfinite(tr);
+  if (!bad) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      double s = G[j * R + j];
+#pragma unroll
+      for (int l = 0; l < j; ++l) s -= U[l][j] * U[l][j];
+      if (!(s > rel_floor * tr) || !(tr > 0.0)) {
+        atomicOr(flags, kFlagBreakdown);
+        s = (tr > 0.0 && isfinite(tr)) ? fmax(s, rel_floor * tr) : 1.0;
+        if (!(s > 0.0)) s = 1.0;
+      }
+      U[j][j] = sqrt(s);
+      const double dj = 1.0 / U[j][j];
+#pragma unroll
+      for (int i = j + 1; i < R; ++i) {
+        double t = G[j * R + i];
+#pragma unroll
+        for (int l = 0; l < j; ++l) t -= U[l][j] * U[l][i];
+        U[j][i] = t * dj;
+      }
     }
-    R[j][j] = sqrt(s);
-    for (int i = j + 1; i < r; ++i) {
-      double t = G[j * r + i];
-      for (int l = 0; l < j; ++l) t -= R[l][j] * R[l][i];
-      R[j][i] = t / R[j][j];
-    }
-  }
-  if (bad) {
+  } else {
     atomicOr(flags, kFlagNonfinite);
-    for (int a = 0; a < r; ++a) R[a][a] = 1.0;
+#pragma unroll
+    for (int a = 0; a < R; ++a) U[a][a] = 1.0;
   }
-  double Ri[kMaxR][kMaxR] = {};
-  for (int j = 0; j < r; ++j) {
-    Ri[j][j] = 1.0 / R[j][j];
-    for (int i = j - 1; i >= 0; --i) {
-      double t = 0.0;
-      for (int l = i + 1; l <= j; ++l) t += R[i][l] * Ri[l][j];
-      Ri[i][j] = -t / R[i][i];
-    }
-  }
-  for (int a = 0; a < r; ++a)
-    for (int b = 0; b < r; ++b) {
-      if (Rout) Rout[a * r + b] = R[a][b];
-      if (Rinv) Rinv[a * r + b] = Ri[a][b];
-    }
+  double Ui[R][R];
+  sm::upper_inv<R>(U, Ui);
+  if (Rout) sm::store_rm<R>(U, Rout);
+  if (Rinv) sm::store_rm<R>(Ui, Rinv);
 }
 
 template <typename TC, int R>
@@ -341,17 +345,18 @@ __global__ void k_convert(const double* __restrict__ src, TD* __restrict__ dst, 
     Store<TD>::st(dst + e, (decltype(Store<TD>::ld(dst)))src[e]);
 }
 
-// mode 0: C = A B;  mode 1: C = A B^T  (r x r row-major)
-__global__ void k_combine_small(const double* A, const double* B, double* C, int r, int mode) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double out[kMaxR * kMaxR];
-  for (int a = 0; a < r; ++a)
-    for (int b = 0; b < r; ++b) {
-      double s = 0.0;
-      for (int l = 0; l < r; ++l) s += A[a * r + l] * (mode == 0 ? B[l * r + b] : B[b * r + l]);
-      out[a * r + b] = s;
-    }
-  for (int e = 0; e < r * r; ++e) C[e] = out[e];
+// mode 0: C = A B;  mode 1: C = A B^T  (r x r row-major); one thread per entry
+template <int R>
+__global__ void k_combine_small(const double* A, const double* B, double* C, int mode) {
+  const int e = threadIdx.x;
+  double s = 0.0;
+  if (e < R * R) {
+    const int a = e / R, b = e - a * R;
+#pragma unroll
+    for (int l = 0; l < R; ++l) s += A[a * R + l] * (mode == 0 ? B[l * R + b] : B[b * R + l]);
+  }
+  __syncthreads();    // C may alias A or B
+  if (e < R * R) C[e] = s;
 }
 
 int default_grid(int64_t n) {
@@ -492,7 +497,12 @@ void update_gram_launch(TC* W, int64_t n, int r, WindowPtrs win, const double* h
 void chol_small_launch(const double* partial, int nparts, int r, double* R, double* Rinv,
                        uint32_t* flags, double rel_floor, cudaStream_t st) {
   count_launches(1);
-  k_chol_small<<<1, 256, 0, st>>>(partial, nparts, r, R, Rinv, flags, rel_floor);
+  switch (r) {
+    case 1: k_chol_small<1><<<1, 256, 0, st>>>(partial, nparts, R, Rinv, flags, rel_floor); break;
+    case 2: k_chol_small<2><<<1, 256, 0, st>>>(partial, nparts, R, Rinv, flags, rel_floor); break;
+    case 3: k_chol_small<3><<<1, 256, 0, st>>>(partial, nparts, R, Rinv, flags, rel_floor); break;
+    default: k_chol_small<4><<<1, 256, 0, st>>>(partial, nparts, R, Rinv, flags, rel_floor); break;
+  }
 }
 
 template <typename TC>
@@ -548,7 +558,12 @@ void convert_block_launch(const double* src, TB* dst, int64_t count, cudaStream_
 void combine_small_launch(const double* A, const double* B, double* C, int r, int mode,
                           cudaStream_t st) {
   count_launches(1);
-  k_combine_small<<<1, 32, 0, st>>>(A, B, C, r, mode);
+  switch (r) {
+    case 1: k_combine_small<1><<<1, 32, 0, st>>>(A, B, C, mode); break;
+    case 2: k_combine_small<2><<<1, 32, 0, st>>>(A, B, C, mode); break;
+    case 3: k_combine_small<3><<<1, 32, 0, st>>>(A, B, C, mode); break;
+    default: k_combine_small<4><<<1, 32, 0, st>>>(A, B, C, mode); break;
+  }
 }
 
 // ---- explicit instantiations: FP64, mixed FP32, mixed BF16-basis

@@ -13,6 +13,7 @@
 // rho (Eq. (3.5)) uses the whitened subdiagonals
 //   hhat = tau_{d+1} h_{d+1,d} tau_d^{-1},  ghat = theta_{d+1} g_{d+1,d} theta_d^{-1}.
 #include "spk_internal.cuh"
+#include "small_mat.cuh"
 
 #include <algorithm>
 
@@ -102,108 +103,136 @@ __global__ void __launch_bounds__(kBWarps * 32) k_border_gemv(const double* __re
 
 // Rows i < mp of the new block column of H~:
 // (-sum of GEMV partials + T_{d-1} H_col + T_H h_{d,d}) tau_d^{-1}.
-__global__ void k_border_col(double* __restrict__ Ht, int64_t ldH, int mp, int r,
+template <int R>
+__global__ void k_border_col(double* __restrict__ Ht, int64_t ldH, int mp,
                              const double* __restrict__ T, int64_t ldT,
                              const double* __restrict__ hslots, int first_block, int nslots,
                              const double* __restrict__ h_dd, const double* __restrict__ partial,
                              int nchunk) {
-  __shared__ double tinv[kMaxR * kMaxR];
-  __shared__ double hdd[kMaxR * kMaxR];
-  if (threadIdx.x == 0) upper_inv(T, ldT, mp, r, tinv);
-  if (threadIdx.x < r * r) hdd[threadIdx.x] = h_dd[threadIdx.x];
+  __shared__ double tinv[R * R];
+  __shared__ double hdd[R * R];
+  if (threadIdx.x == 0) {
+    double U[R][R], Ui[R][R];
+    sm::load_tblock<R>(T, ldT, mp, U);
+    sm::upper_inv<R>(U, Ui);
+    sm::store_rm<R>(Ui, tinv);
+  }
+  if (threadIdx.x < R * R) hdd[threadIdx.x] = h_dd[threadIdx.x];
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= mp) return;
-  double v[kMaxR] = {0, 0, 0, 0};
+  double v[R];
+#pragma unroll
+  for (int c = 0; c < R; ++c) v[c] = 0.0;
 #pragma unroll 4
   for (int ch = 0; ch < nchunk; ++ch) {
-    const double* pp = partial + ((int64_t)ch * mp + i) * r;
+    const double* pp = partial + ((int64_t)ch * mp + i) * R;
 #pragma unroll
-    for (int c = 0; c < kMaxR; ++c)
-      if (c < r) v[c] -= pp[c];
+    for (int c = 0; c < R; ++c) v[c] -= pp[c];
   }
   for (int q = 0; q < nslots; ++q) {
     const int b = first_block + q;  // 1-based block index
-    for (int a = 0; a < r; ++a) {
-      const int l = (b - 1) * r + a;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      const int l = (b - 1) * R + a;
       const double t = T[i + (int64_t)l * ldT];
-      for (int c = 0; c < r; ++c) v[c] += t * hslots[(q * r + a) * r + c];
+#pragma unroll
+      for (int c = 0; c < R; ++c) v[c] += t * hslots[(q * R + a) * R + c];
     }
   }
-  for (int a = 0; a < r; ++a) {
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
     const double t = T[i + (int64_t)(mp + a) * ldT];
-    for (int c = 0; c < r; ++c) v[c] += t * hdd[a * r + c];
+#pragma unroll
+    for (int c = 0; c < R; ++c) v[c] += t * hdd[a * R + c];
   }
-  for (int c = 0; c < r; ++c) {
+#pragma unroll
+  for (int c = 0; c < R; ++c) {
     double s = 0.0;
-    for (int a = 0; a <= c; ++a) s += v[a] * tinv[a * r + c];
+#pragma unroll
+    for (int a = 0; a <= c; ++a) s += v[a] * tinv[a * R + c];
     Ht[i + (int64_t)(mp + c) * ldH] = s;
   }
 }
 
 }  // namespace
 
-// Rows mp..mp+r of H~ (the (2,1) and (2,2) blocks of the bordering update).
-__host__ __device__ void border_small_body(double* Ht, int64_t ldH, int mp, int r, const double* T,
-                                           int64_t ldT, const double* h_sub, const double* h_dd) {
-  double tau[kMaxR * kMaxR], tinv[kMaxR * kMaxR], X[kMaxR * kMaxR], Y[kMaxR * kMaxR];
-  tblock(T, ldT, mp, r, tau);
-  upper_inv(T, ldT, mp, r, tinv);
-  if (mp == 0) {
-    mm(tau, h_dd, X, r);
-    mm(X, tinv, Y, r);
-    for (int a = 0; a < r; ++a)
-      for (int c = 0; c < r; ++c) Ht[a + (int64_t)c * ldH] = Y[a * r + c];
-    return;
-  }
-  double tpinv[kMaxR * kMaxR];
-  upper_inv(T, ldT, mp - r, r, tpinv);
-  // (2,1): tau_d h_{d,d-1} tau_{d-1}^{-1}
-  double hs_tp[kMaxR * kMaxR];
-  mm(h_sub, tpinv, hs_tp, r);
-  mm(tau, hs_tp, X, r);
-  for (int a = 0; a < r; ++a)
-    for (int c = 0; c < r; ++c) Ht[mp + a + (int64_t)(mp - r + c) * ldH] = X[a * r + c];
-  // (2,2): tau_d (h_{d,d} - h_{d,d-1} tau_{d-1}^{-1} E^T T_H) tau_d^{-1}
-  double ET[kMaxR * kMaxR];
-  for (int a = 0; a < r; ++a)
-    for (int c = 0; c < r; ++c) ET[a * r + c] = T[mp - r + a + (int64_t)(mp + c) * ldT];
-  mm(hs_tp, ET, X, r);
-  for (int e = 0; e < r * r; ++e) X[e] = h_dd[e] - X[e];
-  mm(tau, X, Y, r);
-  mm(Y, tinv, X, r);
-  for (int a = 0; a < r; ++a)
-    for (int c = 0; c < r; ++c) Ht[mp + a + (int64_t)(mp + c) * ldH] = X[a * r + c];
-}
-
 namespace {
 
-__global__ void k_border_small(double* __restrict__ Ht, int64_t ldH, int mp, int r,
+// Rows mp..mp+r of H~ (the (2,1) and (2,2) blocks of the bordering update).
+template <int R>
+__global__ void k_border_small(double* __restrict__ Ht, int64_t ldH, int mp,
                                const double* __restrict__ T, int64_t ldT,
                                const double* __restrict__ h_sub, const double* __restrict__ h_dd) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  border_small_body(Ht, ldH, mp, r, T, ldT, h_sub, h_dd);
+  double tau[R][R], tinv[R][R], X[R][R], Y[R][R], H[R][R];
+  sm::load_tblock<R>(T, ldT, mp, tau);
+  sm::upper_inv<R>(tau, tinv);
+  sm::load_rm<R>(h_dd, H);
+  if (mp == 0) {
+    sm::mul<R>(tau, H, X);
+    sm::mul<R>(X, tinv, Y);
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int c = 0; c < R; ++c) Ht[a + (int64_t)c * ldH] = Y[a][c];
+    return;
+  }
+  double tp[R][R], tpinv[R][R], hs[R][R], hs_tp[R][R], ET[R][R];
+  sm::load_tblock<R>(T, ldT, mp - R, tp);
+  sm::upper_inv<R>(tp, tpinv);
+  // (2,1): tau_d h_{d,d-1} tau_{d-1}^{-1}
+  sm::load_rm<R>(h_sub, hs);
+  sm::mul<R>(hs, tpinv, hs_tp);
+  sm::mul<R>(tau, hs_tp, X);
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int c = 0; c < R; ++c) Ht[mp + a + (int64_t)(mp - R + c) * ldH] = X[a][c];
+  // (2,2): tau_d (h_{d,d} - h_{d,d-1} tau_{d-1}^{-1} E^T T_H) tau_d^{-1}
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int c = 0; c < R; ++c) ET[a][c] = T[mp - R + a + (int64_t)(mp + c) * ldT];
+  sm::mul<R>(hs_tp, ET, X);
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int c = 0; c < R; ++c) X[a][c] = H[a][c] - X[a][c];
+  sm::mul<R>(tau, X, Y);
+  sm::mul<R>(Y, tinv, X);
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int c = 0; c < R; ++c) Ht[mp + a + (int64_t)(mp + c) * ldH] = X[a][c];
 }
 
 // H~[:, m-r:m] += T[:, m:m+r] h_{d+1,d} tau_d^{-1}  (rows < m)
-__global__ void k_border_correct(double* __restrict__ Ht, int64_t ldH, int m, int r,
+template <int R>
+__global__ void k_border_correct(double* __restrict__ Ht, int64_t ldH, int m,
                                  const double* __restrict__ T, int64_t ldT,
                                  const double* __restrict__ h_next) {
-  __shared__ double K[kMaxR * kMaxR];
+  __shared__ double K[R * R];
   if (threadIdx.x == 0) {
-    double tinv[kMaxR * kMaxR];
-    upper_inv(T, ldT, m - r, r, tinv);
-    mm(h_next, tinv, K, r);
+    double U[R][R], Ui[R][R], Hn[R][R], Kk[R][R];
+    sm::load_tblock<R>(T, ldT, m - R, U);
+    sm::upper_inv<R>(U, Ui);
+    sm::load_rm<R>(h_next, Hn);
+    sm::mul<R>(Hn, Ui, Kk);
+    sm::store_rm<R>(Kk, K);
   }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
-  double v[kMaxR];
-  for (int a = 0; a < r; ++a) v[a] = T[i + (int64_t)(m + a) * ldT];
-  for (int c = 0; c < r; ++c) {
+  double v[R];
+#pragma unroll
+  for (int a = 0; a < R; ++a) v[a] = T[i + (int64_t)(m + a) * ldT];
+#pragma unroll
+  for (int c = 0; c < R; ++c) {
     double s = 0.0;
-    for (int a = 0; a < r; ++a) s += v[a] * K[a * r + c];
-    Ht[i + (int64_t)(m - r + c) * ldH] += s;
+#pragma unroll
+    for (int a = 0; a < R; ++a) s += v[a] * K[a * R + c];
+    Ht[i + (int64_t)(m - R + c) * ldH] += s;
   }
 }
 
@@ -347,20 +376,38 @@ void border_col_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, 
   count_launches(1);
   k_border_gemv<<<grid, kBWarps * 32, 0, st>>>(Ht, ldH, mp, r, T, ldT, partial);
   count_launches(1);
-  k_border_col<<<(mp + 31) / 32, 32, 0, st>>>(Ht, ldH, mp, r, T, ldT, hslots, first_block,
-                                              nslots, h_dd, partial, nch);
+  const unsigned g = (unsigned)((mp + 31) / 32);
+#define SPK_BCOL(R) k_border_col<R><<<g, 32, 0, st>>>(Ht, ldH, mp, T, ldT, hslots, first_block, nslots, h_dd, partial, nch)
+  switch (r) {
+    case 1: SPK_BCOL(1); break;
+    case 2: SPK_BCOL(2); break;
+    case 3: SPK_BCOL(3); break;
+    default: SPK_BCOL(4); break;
+  }
+#undef SPK_BCOL
 }
 
 void border_small_launch(double* Ht, int64_t ldH, int mp, int r, const double* T, int64_t ldT,
                          const double* h_sub, const double* h_dd, cudaStream_t st) {
   count_launches(1);
-  k_border_small<<<1, 32, 0, st>>>(Ht, ldH, mp, r, T, ldT, h_sub, h_dd);
+  switch (r) {
+    case 1: k_border_small<1><<<1, 32, 0, st>>>(Ht, ldH, mp, T, ldT, h_sub, h_dd); break;
+    case 2: k_border_small<2><<<1, 32, 0, st>>>(Ht, ldH, mp, T, ldT, h_sub, h_dd); break;
+    case 3: k_border_small<3><<<1, 32, 0, st>>>(Ht, ldH, mp, T, ldT, h_sub, h_dd); break;
+    default: k_border_small<4><<<1, 32, 0, st>>>(Ht, ldH, mp, T, ldT, h_sub, h_dd); break;
+  }
 }
 
 void border_correct_launch(double* Ht, int64_t ldH, int m, int r, const double* T, int64_t ldT,
                            const double* h_next, cudaStream_t st) {
   count_launches(1);
-  k_border_correct<<<(m + 127) / 128, 128, 0, st>>>(Ht, ldH, m, r, T, ldT, h_next);
+  const unsigned g = (unsigned)((m + 127) / 128);
+  switch (r) {
+    case 1: k_border_correct<1><<<g, 128, 0, st>>>(Ht, ldH, m, T, ldT, h_next); break;
+    case 2: k_border_correct<2><<<g, 128, 0, st>>>(Ht, ldH, m, T, ldT, h_next); break;
+    case 3: k_border_correct<3><<<g, 128, 0, st>>>(Ht, ldH, m, T, ldT, h_next); break;
+    default: k_border_correct<4><<<g, 128, 0, st>>>(Ht, ldH, m, T, ldT, h_next); break;
+  }
 }
 
 void rho_launch(const double* Y, int64_t ldY, int m, int r, const double* TU, int64_t ldTU,
