@@ -151,21 +151,28 @@ __device__ __forceinline__ void qs_epilogue_half(uint32_t trow, long long (&hi)[
 #pragma unroll
   for (int pp = 0; pp < 4; ++pp) {
     const int p = P0 + pp;
+    // the slice's column chunks with a kept pair, loaded together and waited
+    // for once (each wait is a round trip to tensor memory)
+    uint32_t v[N / 16][16];
 #pragma unroll
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      if (c0 / R > kQsS - 1 - p) continue;    // no kept pair in these columns
-      uint32_t v[16];
+    for (int ch = 0; ch < N / 16; ++ch) {
+      if ((16 * ch) / R > kQsS - 1 - p) continue;
       asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                   : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                     "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                     "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                   : "r"(trow + (uint32_t)(p * N + c0)));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                   : "=r"(v[ch][0]), "=r"(v[ch][1]), "=r"(v[ch][2]), "=r"(v[ch][3]), "=r"(v[ch][4]),
+                     "=r"(v[ch][5]), "=r"(v[ch][6]), "=r"(v[ch][7]), "=r"(v[ch][8]), "=r"(v[ch][9]),
+                     "=r"(v[ch][10]), "=r"(v[ch][11]), "=r"(v[ch][12]), "=r"(v[ch][13]),
+                     "=r"(v[ch][14]), "=r"(v[ch][15])
+                   : "r"(trow + (uint32_t)(p * N + 16 * ch)));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int ch = 0; ch < N / 16; ++ch) {
+      if ((16 * ch) / R > kQsS - 1 - p) continue;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const int n = c0 + j;
+        const int n = 16 * ch + j;
         const int q = n / R, c = n % R;
-        if (n < 8 * R && p + q <= kQsS - 1) lev[p + q][c] += qs_f32_int(v[j]);
+        if (n < 8 * R && p + q <= kQsS - 1) lev[p + q][c] += qs_f32_int(v[ch][j]);
       }
     }
   }
