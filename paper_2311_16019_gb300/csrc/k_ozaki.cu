@@ -254,35 +254,29 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_mma(const uint8_t* __restr
     if ((kt % kOzEpi) != kOzEpi - 1 && kt != KT - 1) continue;
     // FP64 epilogue: row 32 warp + lane of the tile, 64 columns per level
     // levels lv0 .. lv0 + 3 into acc, level lv weighted 2^(7 (lv0 + 3 - lv))
-    // two levels per round: their loads are issued together and waited for
-    // once (each wait is a round trip to tensor memory)
-    auto two_levels = [&](long long (&acc)[kCols], int lv, int sh0) {
-      uint32_t v[2][kCols];
+    // levels lv0 .. lv0 + 3 into acc, level lv weighted 2^(7 (lv0 + 3 - lv))
+    auto levels = [&](long long (&acc)[kCols], int lv0) {
+#pragma unroll 1
+      for (int lv = lv0; lv < lv0 + 4; ++lv) {
+        const int sh = kOzBits * (lv0 + 3 - lv);
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                     "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                     : "=r"(v[h][0]), "=r"(v[h][1]), "=r"(v[h][2]), "=r"(v[h][3]), "=r"(v[h][4]),
-                       "=r"(v[h][5]), "=r"(v[h][6]), "=r"(v[h][7]), "=r"(v[h][8]), "=r"(v[h][9]),
-                       "=r"(v[h][10]), "=r"(v[h][11]), "=r"(v[h][12]), "=r"(v[h][13]),
-                       "=r"(v[h][14]), "=r"(v[h][15]), "=r"(v[h][16]), "=r"(v[h][17]),
-                       "=r"(v[h][18]), "=r"(v[h][19]), "=r"(v[h][20]), "=r"(v[h][21]),
-                       "=r"(v[h][22]), "=r"(v[h][23]), "=r"(v[h][24]), "=r"(v[h][25]),
-                       "=r"(v[h][26]), "=r"(v[h][27]), "=r"(v[h][28]), "=r"(v[h][29]),
-                       "=r"(v[h][30]), "=r"(v[h][31])
-                     : "r"(tmem + ((uint32_t)(32 * quad) << 16) +
-                           (uint32_t)((lv + h) * kOzTN + half * kCols)));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int c0 = 0; c0 < kCols; c0 += 16) {
+          uint32_t r[16];
+          const uint32_t ta = tmem + ((uint32_t)(32 * quad) << 16) +
+                              (uint32_t)(lv * kOzTN + half * kCols + c0);
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                         "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                         "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                       : "r"(ta));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < kCols; ++j)
-        acc[j] += ((long long)tc::f32_int(v[0][j]) << sh0) +
-                  ((long long)tc::f32_int(v[1][j]) << (sh0 - kOzBits));
+          for (int j = 0; j < 16; ++j) acc[c0 + j] += (long long)tc::f32_int(r[j]) << sh;
+        }
+      }
     };
-    // level lv of hi (lv < 4) weighs 2^(7 (3 - lv)), of lo 2^(7 (7 - lv))
-    two_levels(hi, 0, 3 * kOzBits);
-    two_levels(hi, 2, 1 * kOzBits);
-    two_levels(lo, 4, 3 * kOzBits);
-    two_levels(lo, 6, 1 * kOzBits);
+    levels(hi, 0);
+    levels(lo, 4);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
   }
