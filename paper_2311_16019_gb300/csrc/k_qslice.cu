@@ -58,8 +58,12 @@ constexpr int kQsTM = 128;                                // tile rows (M of the
 constexpr int kQsKC = 16;                                 // K per stage (one MMA per slice)
 constexpr int kQsStages = 3;                              // stages in flight per CTA
 constexpr int kQsKper = 256;                              // K positions per CTA
-constexpr int kQsSliceTile = kQsTM * kQsKC * 2;           // 4 KB
+constexpr int kQsSliceTile = kQsTM * kQsKC * 2;           // 4 KB (BF16, shared memory)
 constexpr int kQsStage = kQsS * kQsSliceTile;             // 32 KB
+constexpr int kQsSliceTile8 = kQsTM * kQsKC;              // 2 KB (biased int8 digits, global)
+constexpr int kQsStage8 = kQsS * kQsSliceTile8;           // 16 KB
+constexpr int kQsLoaders = 256;                           // warps 0..7 widen the stages
+constexpr int kQsLoads = kQsStage8 / 16 / kQsLoaders;     // 16-byte loads per loader and stage
 constexpr int kQsNmax = 32;                               // B rows (8 r, padded)
 constexpr int kQsBBytes = kQsNmax * kQsKper * 2;          // 16 KB
 constexpr int kQsSmem = kQsStages * kQsStage + kQsBBytes; // 112 KB: two CTAs per SM
@@ -67,7 +71,7 @@ constexpr uint32_t kQsLbo = 128;                          // next 8-element K gr
 constexpr uint32_t kQsSboA = (kQsKC / 8) * 128;           // next 8-row group, A tiles
 constexpr uint32_t kQsSboB = (kQsKper / 8) * 128;         // next 8-row group, B
 constexpr long kQsSpin = 1l << 26;                        // bounded mbarrier waits
-constexpr int kQsThreads = 256;
+constexpr int kQsThreads = kQsLoaders + 32;              // + warp 8: the MMA issuer
 
 static_assert(kQsKper % kQsKC == 0, "stages tile the K range of a CTA");
 static_assert(kQsKper * (1 << 13) < (1 << 24), "accumulators stay exact in FP32");
@@ -77,18 +81,25 @@ __host__ __device__ __forceinline__ uint32_t qs_offset(int i, int k, uint32_t sb
   return (uint32_t)((i >> 3) * sbo + (k >> 3) * kQsLbo + (i & 7) * 16 + (k & 7) * 2);
 }
 
-// 8 values (8 consecutive K positions of one row) -> one 16-byte core-matrix
-// row per slice at base + p * kQsSliceTile.
+// Byte offset of (row i, K position k) inside an int8 slice tile: the BF16
+// core-matrix layout at half the bytes, so that the widened copy of byte
+// offset o lies at 2 o.
+__host__ __device__ __forceinline__ uint32_t qs_offset8(int i, int k) {
+  return (uint32_t)((i >> 3) * (kQsSboA / 2) + (k >> 3) * (kQsLbo / 2) + (i & 7) * 8 + (k & 7));
+}
+
+// 8 values (8 consecutive K positions of one row) -> one 8-byte core-matrix
+// row of biased digits (n + 128) per slice at base + p * kQsSliceTile8.
 __device__ __forceinline__ void qs_store_row8(const double (&x)[8], int e, uint8_t* base) {
   int n[8][kQsS];
 #pragma unroll
   for (int u = 0; u < 8; ++u) tc::digits8(x[u], e, n[u]);
 #pragma unroll
   for (int p = 0; p < kQsS; ++p) {
-    uint32_t w[4];
+    uint32_t w[2] = {0u, 0u};
 #pragma unroll
-    for (int u = 0; u < 8; u += 2) w[u / 2] = tc::bf16_int(n[u][p]) | (tc::bf16_int(n[u + 1][p]) << 16);
-    *reinterpret_cast<uint4*>(base + (int64_t)p * kQsSliceTile) = make_uint4(w[0], w[1], w[2], w[3]);
+    for (int u = 0; u < 8; ++u) w[u >> 2] |= (uint32_t)(n[u][p] + 128) << (8 * (u & 3));
+    *reinterpret_cast<uint2*>(base + (int64_t)p * kQsSliceTile8) = make_uint2(w[0], w[1]);
   }
 }
 
@@ -117,7 +128,7 @@ __global__ void k_qs_append(const double* __restrict__ Q, int64_t s, int m, int 
 #pragma unroll
       for (int u = 0; u < 8; ++u) x[u] = i0 + u < s ? Q[i0 + u + (int64_t)j * s] : 0.0;
       const int64_t tile = ((int64_t)(j / kQsTM) * KTA + i0 / kQsKC) * kQsS;
-      qs_store_row8(x, 1, QA + tile * kQsSliceTile + qs_offset(j % kQsTM, (int)(i0 % kQsKC), kQsSboA));
+      qs_store_row8(x, 1, QA + tile * kQsSliceTile8 + qs_offset8(j % kQsTM, (int)(i0 % kQsKC)));
     } else {
       const int64_t e = t - na;
       const int G = g0 + (int)(e / s);
@@ -126,9 +137,28 @@ __global__ void k_qs_append(const double* __restrict__ Q, int64_t s, int m, int 
 #pragma unroll
       for (int u = 0; u < 8; ++u) x[u] = j0 + u < m + r ? Q[i + (int64_t)(j0 + u) * s] : 0.0;
       const int64_t tile = ((i / kQsTM) * KTB + j0 / kQsKC) * kQsS;
-      qs_store_row8(x, 1, QB + tile * kQsSliceTile + qs_offset((int)(i % kQsTM), j0 % kQsKC, kQsSboA));
+      qs_store_row8(x, 1, QB + tile * kQsSliceTile8 + qs_offset8((int)(i % kQsTM), j0 % kQsKC));
     }
   }
+}
+
+// 16 biased int8 digits -> 16 BF16 values (two 16-byte stores): 2^23 + u is
+// exact in FP32, minus 2^23 + 128 gives the digit, and the upper half of an
+// FP32 holding an integer of at most 8 bits is its BF16 pattern.
+__device__ __forceinline__ void qs_widen16(const uint4 v, uint8_t* dst) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  uint32_t o[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float f[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      f[j] = __uint_as_float(__byte_perm(w[q], 0x4B00u, 0x5440u | (uint32_t)j)) - 8388736.0f;
+    o[2 * q] = __byte_perm(__float_as_uint(f[0]), __float_as_uint(f[1]), 0x7632u);
+    o[2 * q + 1] = __byte_perm(__float_as_uint(f[2]), __float_as_uint(f[3]), 0x7632u);
+  }
+  reinterpret_cast<uint4*>(dst)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+  reinterpret_cast<uint4*>(dst)[1] = make_uint4(o[4], o[5], o[6], o[7]);
 }
 
 // Integer value of an FP32 accumulator holding an integer of magnitude < 2^22.
@@ -229,7 +259,9 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
   }
   if (tid == 32) {
     for (int q = 0; q < kQsStages; ++q) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc::smem_u32(&full[q])) : "memory");
+      // full: one arrive per loader warp; empty: the MMA commit
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
+                   :: "r"(tc::smem_u32(&full[q])), "r"(kQsLoaders / 32) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc::smem_u32(&empty[q])) : "memory");
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc::smem_u32(&done)) : "memory");
@@ -240,17 +272,15 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
     for (int e = tid; e < N * kQsKper * 2 / 16; e += kQsThreads) z[e] = make_uint4(0, 0, 0, 0);
   }
   __syncthreads();
-  auto issue = [&](int st) {
-    const int slot = st % kQsStages;
-    const uint8_t* src = As + ((int64_t)mt * KT + kt0 + st) * kQsStage;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(tc::smem_u32(&full[slot])), "r"((uint32_t)kQsStage) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(tc::smem_u32(sA + slot * kQsStage)), "l"(src), "r"((uint32_t)kQsStage),
-                    "r"(tc::smem_u32(&full[slot])) : "memory");
+  // loaders: the int8 digits of stage st, 16 bytes per load, kQsLoads per thread
+  const bool loader = tid < kQsLoaders;
+  auto load_stage = [&](int st, uint4 (&v)[kQsLoads]) {
+    const uint4* src = reinterpret_cast<const uint4*>(As + ((int64_t)mt * KT + kt0 + st) * kQsStage8);
+#pragma unroll
+    for (int u = 0; u < kQsLoads; ++u) v[u] = __ldcs(src + tid + u * kQsLoaders);
   };
-  if (tid == 0)
-    for (int st = 0; st < min(ns, kQsStages); ++st) issue(st);
+  uint4 cur[kQsLoads], nxt[kQsLoads];
+  if (loader && ns > 0) load_stage(0, cur);
   // B digits: rows q R + c (q = digit plane, c = column) of this K range,
   // with the exponent of each column's largest magnitude in the range
   double bv[kVals];
@@ -296,19 +326,29 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  if (tid == 0) {
-    // producer: stage st into slot st % kQsStages once the MMAs of stage
-    // st - kQsStages have released it
-    for (int st = kQsStages; st < ns; ++st) {
+  if (loader) {
+    // stage st into slot st % kQsStages once the MMAs of stage st - kQsStages
+    // have released it; the next stage's loads are in flight meanwhile
+    for (int st = 0; st < ns; ++st) {
+      if (st + 1 < ns) load_stage(st + 1, nxt);
       const int slot = st % kQsStages;
-      if (!tc::mbar_wait(tc::smem_u32(&empty[slot]), (uint32_t)((st / kQsStages - 1) & 1), kQsSpin)) {
+      if (st >= kQsStages &&
+          !tc::mbar_wait(tc::smem_u32(&empty[slot]), (uint32_t)((st / kQsStages - 1) & 1), kQsSpin)) {
         failed = 1;
         break;
       }
       if (failed) break;
-      issue(st);
+      uint8_t* dst = sA + slot * kQsStage;
+#pragma unroll
+      for (int u = 0; u < kQsLoads; ++u) qs_widen16(cur[u], dst + 32 * (tid + u * kQsLoaders));
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc::smem_u32(&full[slot])) : "memory");
+#pragma unroll
+      for (int u = 0; u < kQsLoads; ++u) cur[u] = nxt[u];
     }
-  } else if (tid == 32) {
+  } else if (tid == kQsLoaders) {
     // MMA issuer
     constexpr uint32_t idesc = tc::idesc_bf16(kQsTM, N);
     bool ok = true;
@@ -351,7 +391,7 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
   const int quad = warp & 3, half = warp >> 2;
   const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
   long long hi[R], lo[R];
-  if (got) {
+  if (got && loader) {
     if (half == 0)
       qs_epilogue_half<R, N, 0>(trow, hi, lo);
     else
@@ -361,7 +401,7 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
   __syncthreads();    // every MMA is complete: sB is free for the half sums
   long long* red = reinterpret_cast<long long*>(sB);
   const int rt = 32 * quad + lane;
-  if (half == 1 && got) {
+  if (half == 1 && got && loader) {
 #pragma unroll
     for (int c = 0; c < R; ++c) {
       red[(2 * rt) * R + c] = hi[c];
@@ -421,8 +461,8 @@ QsGeom qs_geometry(int64_t s, int mmax) {
   g.KTA = (int)((s + kQsKC - 1) / kQsKC);
   g.MTB = (int)((s + kQsTM - 1) / kQsTM);
   g.KTB = (mmax + kQsKC - 1) / kQsKC;
-  g.bytesA = (size_t)g.MTA * g.KTA * kQsStage;
-  g.bytesB = (size_t)g.MTB * g.KTB * kQsStage;
+  g.bytesA = (size_t)g.MTA * g.KTA * kQsStage8;
+  g.bytesB = (size_t)g.MTB * g.KTB * kQsStage8;
   return g;
 }
 
