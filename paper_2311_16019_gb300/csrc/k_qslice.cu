@@ -30,14 +30,13 @@
 // positions, the 8 slice tiles of 4 KB in the tensor cores' K-major core
 // matrix layout (8 rows x 16 bytes), so one bulk copy moves a whole stage.
 //
-// Right-hand side.  Each CTA handles 1024 K positions; it splits its part of
+// Right-hand side.  Each CTA handles 256 K positions; it splits its part of
 // the r columns of w (or t) with e_c from the largest magnitude of column c
 // in that part, and all 8 digit planes of all r columns form one B operand
 // of N = 8 r rows (padded to 16 or 32), so one MMA per Q slice p and K step
 // of 16 gives the products of slice p with every digit plane q of every
-// column.  Each product n_p n_q is at most 2^13 in magnitude; over the 1024
-// K positions of a CTA every accumulator is an integer of magnitude at most
-// 2^23 and exact in FP32.
+// column.  Each product n_p n_q is at most 2^13 in magnitude; over 256 K
+// positions every accumulator is an integer below 2^21 and exact in FP32.
 // Pairs with p + q > 9 (weights below 2^-70) are dropped; the epilogue turns
 // the other 36 per column into integers, adds those of one weight level
 // 2^(-7 (p+q)) exactly, combines the levels exactly into two 64-bit integers
@@ -58,7 +57,7 @@ constexpr int kQsBits = 7;                                // bits per slice
 constexpr int kQsTM = 128;                                // tile rows (M of the MMA)
 constexpr int kQsKC = 16;                                 // K per stage (one MMA per slice)
 constexpr int kQsStages = 3;                              // stages in flight per CTA
-constexpr int kQsKper = 1024;                             // K positions per CTA
+constexpr int kQsKper = 256;                              // K positions per CTA
 constexpr int kQsSliceTile = kQsTM * kQsKC * 2;           // 4 KB (BF16, shared memory)
 constexpr int kQsStage = kQsS * kQsSliceTile;             // 32 KB
 constexpr int kQsSliceTile8 = kQsTM * kQsKC;              // 2 KB (biased int8 digits, global)
@@ -66,16 +65,16 @@ constexpr int kQsStage8 = kQsS * kQsSliceTile8;           // 16 KB
 constexpr int kQsLoaders = 256;                           // warps 0..7 widen the stages
 constexpr int kQsLoads = kQsStage8 / 16 / kQsLoaders;     // 16-byte loads per loader and stage
 constexpr int kQsNmax = 32;                               // B rows (8 r, padded)
-constexpr int kQsBStage = kQsNmax * kQsKC * 2;            // 1 KB of B digits per stage
-constexpr int kQsStageSm = kQsStage + kQsBStage;          // one shared-memory stage
-constexpr int kQsSmem = kQsStages * kQsStageSm;           // 99 KB: two CTAs per SM
+constexpr int kQsBBytes = kQsNmax * kQsKper * 2;          // 16 KB
+constexpr int kQsSmem = kQsStages * kQsStage + kQsBBytes; // 112 KB: two CTAs per SM
 constexpr uint32_t kQsLbo = 128;                          // next 8-element K group
 constexpr uint32_t kQsSboA = (kQsKC / 8) * 128;           // next 8-row group, A tiles
+constexpr uint32_t kQsSboB = (kQsKper / 8) * 128;         // next 8-row group, B
 constexpr long kQsSpin = 1l << 26;                        // bounded mbarrier waits
 constexpr int kQsThreads = kQsLoaders + 32;              // + warp 8: the MMA issuer
 
 static_assert(kQsKper % kQsKC == 0, "stages tile the K range of a CTA");
-static_assert(kQsKper * (1 << 13) <= (1 << 23), "accumulators stay exact in FP32");
+static_assert(kQsKper * (1 << 13) < (1 << 24), "accumulators stay exact in FP32");
 
 // Byte offset of (row i, K position k) inside a tile of `sbo`-spaced row groups.
 __host__ __device__ __forceinline__ uint32_t qs_offset(int i, int k, uint32_t sbo) {
@@ -162,6 +161,11 @@ __device__ __forceinline__ void qs_widen16(const uint4 v, uint8_t* dst) {
   reinterpret_cast<uint4*>(dst)[1] = make_uint4(o[4], o[5], o[6], o[7]);
 }
 
+// Integer value of an FP32 accumulator holding an integer of magnitude < 2^22.
+__device__ __forceinline__ int qs_f32_int(uint32_t f) {
+  return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
+}
+
 // Level sums of one half of the Q slices (p = P0 .. P0 + 3) for one tile row:
 // lev[L][c] = sum over kept pairs p + q = L of D_p(row, q R + c), exact in
 // int32; then hi[c] = sum_{L<4} lev[L][c] 2^(7 (3-L)), lo[c] = sum_{L>=4}
@@ -198,7 +202,7 @@ __device__ __forceinline__ void qs_epilogue_half(uint32_t trow, long long (&hi)[
       for (int j = 0; j < 16; ++j) {
         const int n = 16 * ch + j;
         const int q = n / R, c = n % R;
-        if (n < 8 * R && p + q <= kQsS - 1) lev[p + q][c] += tc::f32_int(v[ch][j]);
+        if (n < 8 * R && p + q <= kQsS - 1) lev[p + q][c] += qs_f32_int(v[ch][j]);
       }
     }
   }
@@ -228,11 +232,12 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
                                                           double* __restrict__ partial,
                                                           uint32_t* __restrict__ flags) {
   constexpr int N = (8 * R + 15) / 16 * 16;
+  constexpr int kVals = (kQsKper * R + kQsThreads - 1) / kQsThreads;   // B values per thread
   // no-swizzle operands and bulk copies need 16-byte alignment only; a
   // smaller alignment keeps the static part small (two CTAs per SM)
   extern __shared__ __align__(128) uint8_t smem[];
-  auto sA = [&](int slot) { return smem + slot * kQsStageSm; };
-  auto sB = [&](int slot) { return smem + slot * kQsStageSm + kQsStage; };
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + kQsStages * kQsStage;
   __shared__ __align__(8) uint64_t full[kQsStages], empty[kQsStages], done;
   __shared__ unsigned long long cmax[4];
   __shared__ int s_e[4];
@@ -262,43 +267,61 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(tc::smem_u32(&done)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int e = tid; e < kQsStages * kQsBStage / 16; e += kQsThreads)
-    reinterpret_cast<uint4*>(sB(e / (kQsBStage / 16)))[e % (kQsBStage / 16)] = make_uint4(0, 0, 0, 0);
+  {
+    uint4* z = reinterpret_cast<uint4*>(sB);
+    for (int e = tid; e < N * kQsKper * 2 / 16; e += kQsThreads) z[e] = make_uint4(0, 0, 0, 0);
+  }
   __syncthreads();
-  // loaders: the int8 digits of stage st, 16 bytes per load, kQsLoads per
-  // thread; threads tid < 16 R also fetch one value of B for the stage
+  // loaders: the int8 digits of stage st, 16 bytes per load, kQsLoads per thread
   const bool loader = tid < kQsLoaders;
-  const bool bthread = tid < kQsKC * R;
-  const int bc = tid / kQsKC, bk = tid % kQsKC;
-  auto load_stage = [&](int st, uint4 (&v)[kQsLoads], double& bval) {
+  auto load_stage = [&](int st, uint4 (&v)[kQsLoads]) {
     const uint4* src = reinterpret_cast<const uint4*>(As + ((int64_t)mt * KT + kt0 + st) * kQsStage8);
 #pragma unroll
     for (int u = 0; u < kQsLoads; ++u) v[u] = __ldcs(src + tid + u * kQsLoaders);
-    const int k = st * kQsKC + bk;
-    bval = (bthread && k < kn) ? B[(int64_t)(k0 + k) * bks + (int64_t)bc * bcs] : 0.0;
   };
   uint4 cur[kQsLoads], nxt[kQsLoads];
-  double bcur = 0.0, bnxt = 0.0;
-  if (loader && ns > 0) load_stage(0, cur, bcur);
-  // exponent of each column's largest magnitude over this K range
-  {
-    unsigned long long mx[R];
+  if (loader && ns > 0) load_stage(0, cur);
+  // B digits: rows q R + c (q = digit plane, c = column) of this K range,
+  // with the exponent of each column's largest magnitude in the range
+  double bv[kVals];
+  unsigned long long mx[R];
 #pragma unroll
-    for (int c = 0; c < R; ++c) mx[c] = 0ull;
-    for (int e = tid; e < kn * R; e += kQsThreads) {
+  for (int c = 0; c < R; ++c) mx[c] = 0ull;
+#pragma unroll
+  for (int u = 0; u < kVals; ++u) {
+    const int e = tid + u * kQsThreads;
+    bv[u] = 0.0;
+    if (e < kn * R) {
       const int c = e / kn, k = e - c * kn;
-      const unsigned long long a =
-          (unsigned long long)__double_as_longlong(B[(int64_t)(k0 + k) * bks + (int64_t)c * bcs]) & ~(1ull << 63);
+      bv[u] = B[(int64_t)(k0 + k) * bks + (int64_t)c * bcs];
+      const unsigned long long a = (unsigned long long)__double_as_longlong(bv[u]) & ~(1ull << 63);
 #pragma unroll
       for (int cc = 0; cc < R; ++cc)
         if (c == cc && a > mx[cc]) mx[cc] = a;
     }
+  }
 #pragma unroll
-    for (int c = 0; c < R; ++c)
-      if (mx[c]) atomicMax(&cmax[c], mx[c]);
+  for (int c = 0; c < R; ++c)
+    if (mx[c]) atomicMax(&cmax[c], mx[c]);
+  __syncthreads();
+  if (tid < R) {
+    const unsigned long long a = cmax[tid];
+    s_e[tid] = tc::exp_above(a);     // 2^e > max |B(:, c)|
   }
   __syncthreads();
-  if (tid < R) s_e[tid] = tc::exp_above(cmax[tid]);     // 2^e > max |B(:, c)|
+#pragma unroll
+  for (int u = 0; u < kVals; ++u) {
+    const int e = tid + u * kQsThreads;
+    if (e < kn * R) {
+      const int c = e / kn, k = e - c * kn;
+      int n[kQsS];
+      tc::digits8(bv[u], s_e[c], n);
+#pragma unroll
+      for (int q = 0; q < kQsS; ++q)
+        *reinterpret_cast<uint16_t*>(sB + qs_offset(q * R + c, k, kQsSboB)) = (uint16_t)tc::bf16_int(n[q]);
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -307,7 +330,7 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
     // stage st into slot st % kQsStages once the MMAs of stage st - kQsStages
     // have released it; the next stage's loads are in flight meanwhile
     for (int st = 0; st < ns; ++st) {
-      if (st + 1 < ns) load_stage(st + 1, nxt, bnxt);
+      if (st + 1 < ns) load_stage(st + 1, nxt);
       const int slot = st % kQsStages;
       if (st >= kQsStages &&
           !tc::mbar_wait(tc::smem_u32(&empty[slot]), (uint32_t)((st / kQsStages - 1) & 1), kQsSpin)) {
@@ -315,25 +338,15 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
         break;
       }
       if (failed) break;
-      uint8_t* dst = sA(slot);
+      uint8_t* dst = sA + slot * kQsStage;
 #pragma unroll
       for (int u = 0; u < kQsLoads; ++u) qs_widen16(cur[u], dst + 32 * (tid + u * kQsLoaders));
-      if (bthread) {
-        // B digits: rows q R + c (q = digit plane, c = column), 16 K positions
-        int n[kQsS];
-        tc::digits8(bcur, s_e[bc], n);
-#pragma unroll
-        for (int q = 0; q < kQsS; ++q)
-          *reinterpret_cast<uint16_t*>(sB(slot) + qs_offset(q * R + bc, bk, kQsSboA)) =
-              (uint16_t)tc::bf16_int(n[q]);
-      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc::smem_u32(&full[slot])) : "memory");
 #pragma unroll
       for (int u = 0; u < kQsLoads; ++u) cur[u] = nxt[u];
-      bcur = bnxt;
     }
   } else if (tid == kQsLoaders) {
     // MMA issuer
@@ -348,10 +361,10 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint64_t db = tc::desc_kmajor(tc::smem_u32(sB(slot)), kQsLbo, kQsSboA);
+      const uint64_t db = tc::desc_kmajor(tc::smem_u32(sB) + (uint32_t)st * 2 * kQsLbo, kQsLbo, kQsSboB);
 #pragma unroll
       for (int p = 0; p < kQsS; ++p) {
-        const uint64_t da = tc::desc_kmajor(tc::smem_u32(sA(slot) + p * kQsSliceTile),
+        const uint64_t da = tc::desc_kmajor(tc::smem_u32(sA + slot * kQsStage + p * kQsSliceTile),
                                             kQsLbo, kQsSboA);
         const uint32_t d = tmem + (uint32_t)(p * N);
         const uint32_t accum = st > 0 ? 1u : 0u;
@@ -385,8 +398,8 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
       qs_epilogue_half<R, N, 4>(trow, hi, lo);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();    // every MMA is complete: the stages are free for the half sums
-  long long* red = reinterpret_cast<long long*>(smem);
+  __syncthreads();    // every MMA is complete: sB is free for the half sums
+  long long* red = reinterpret_cast<long long*>(sB);
   const int rt = 32 * quad + lane;
   if (half == 1 && got && loader) {
 #pragma unroll
