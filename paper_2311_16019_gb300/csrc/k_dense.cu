@@ -265,9 +265,10 @@ __global__ void __launch_bounds__(kGjePanelThreads) k_gje_panel_step(double* A, 
 // Step j needs the pivot row p_j, the pivot value and the raw pivot column
 // (column j before the row exchange); the CTA that owns column j publishes
 // them during step j - 1, right after its own update of that column: it
-// writes them to cstore / pstore / ipiv, fences, and releases ready[j - k0]
-// (= gen, a number unique to this launch).  Every other CTA acquires that
-// flag before step j, so the steps proceed with no launch in between.  The
+// writes the column to cstore (each thread fences its part), then its first
+// thread writes the step's record in pstore and releases the record's fourth
+// word (= gen, a number unique to this launch).  Every other CTA acquires
+// that word before step j, so the steps proceed with no launch in between.  The
 // arithmetic and its order are those of k_gje_first + k_gje_panel_step, so
 // the result is the same to the bit.  Each wait is bounded: on expiry the
 // CTA sets kFlagTimeout and stops (the host then reports SPK_ERR_TIMEOUT).
@@ -346,8 +347,11 @@ __global__ void __launch_bounds__(kGjePersistThreads) k_gje_panel_persist(
       if (!(fabs(piv) > 1e-300) || !isfinite(piv)) atomicOr(gs.flags, kFlagZeroPivot);
       const double ld0 = __ldcg(gs.scal);
       __stcg(gs.scal, (jj == 0 ? 0.0 : ld0) + log(fabs(piv)));
-      __threadfence();
-      st_release_u32(gs.ready + (jj - k0), gen);
+      // the record's fourth word carries the generation: one release store
+      // orders this thread's record writes (and, through the fences and the
+      // barrier above, the column) before it, and the waiting CTAs poll the
+      // record itself
+      st_release_u32(reinterpret_cast<uint32_t*>(rec + 3), gen);
     }
   };
   __syncthreads();
@@ -357,7 +361,7 @@ __global__ void __launch_bounds__(kGjePersistThreads) k_gje_panel_persist(
     if (tid == 0) {
       long it = 0;
       uint64_t t0 = 0;
-      while (ld_acquire_u32(gs.ready + q) != gen) {
+      while (ld_acquire_u32(reinterpret_cast<const uint32_t*>(gs.pstore + 4 * q + 3)) != gen) {
         if (++it == 64) t0 = globaltimer_ns();
         if (it > 64) {
           __nanosleep(64);

@@ -462,6 +462,8 @@ int sign_solve(spk_handle* h, int m, double* Hk, double* Gk, double* F, int max_
       return fail(h, SPK_ERR_ALLOC, "cannot allocate Gauss-Jordan panel work");
     CK(cudaMemsetAsync(rdyH, 0, sizeof(uint32_t) * nbw, st));
     CK(cudaMemsetAsync(rdyG, 0, sizeof(uint32_t) * nbw, st));
+    CK(cudaMemsetAsync(pstH, 0, sizeof(double) * 4 * nbw, st));
+    CK(cudaMemsetAsync(pstG, 0, sizeof(double) * 4 * nbw, st));
   }
   WS(permH, int32_t, "sg_permH", 4 * (size_t)nbw + 1);
   WS(permG, int32_t, "sg_permG", 4 * (size_t)nbw + 1);
@@ -746,6 +748,7 @@ int minus_block(spk_handle* h, int m, const double* A, int64_t lda, const double
     if (!gs.cstore || !gs.pstore || !gs.ready || !gs.perm)
       return fail(h, SPK_ERR_ALLOC, "cannot allocate split-solve panel work");
     CK(cudaMemsetAsync(gs.ready, 0, sizeof(uint32_t) * nbw, st));
+    CK(cudaMemsetAsync(gs.pstore, 0, sizeof(double) * 4 * nbw, st));
   }
   for (int i = kA - 1; i >= 0; --i) {
     row_rhs_launch(Rt, T, kA, i, Zt, m, rhs, st);

@@ -342,7 +342,9 @@ struct GjeState {
   void* oz_work = nullptr;   // ozaki_work_bytes(m, m, nb): trailing updates on the tensor cores
   // one launch per panel (gje_persistent_ok): the published pivot columns
   // (nb x m), per-step records (4 nb: pivot row, pivot value, raw column at
-  // the step's row) and ready flags (nb, zeroed once)
+  // the step's row, and in the fourth word the generation that releases the
+  // record; zeroed per solve); `ready` (nb words, zeroed per solve) is not
+  // read by the kernel any more, its presence selects the one-launch path
   double* cstore = nullptr;
   double* pstore = nullptr;
   uint32_t* ready = nullptr;
