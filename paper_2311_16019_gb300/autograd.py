@@ -13,9 +13,12 @@ the operators A^T and B, right-hand side of rank one):
     dL/du = X v,          dL/dv = X^T u.
 
 Both solves and the C1, C2 and theta gradients run in libspk (spk_solve,
-spk_solve_adjoint, spk_adjoint_gradients).  This module assembles A(theta),
-B(theta) on the host, and evaluates the loss itself and its u, v gradients
-(products of the n x l factors with one vector) with torch.
+spk_solve_adjoint, spk_adjoint_gradients).  The operators A(theta),
+B(theta)^T, A(theta)^T and B(theta) live on the device on the union sparsity
+pattern of their two parts, set up once per family; their values
+v0 + theta v_theta are formed by libspk's FP64 product (spk_dense_gemm) at
+each theta.  The loss itself and its u, v gradients (products of the n x l
+factors with one vector) are torch operations.
 """
 from __future__ import annotations
 
@@ -41,11 +44,71 @@ class OperatorFamily:
                    sp.csr_matrix(P.B - P.theta * P.B_theta), sp.csr_matrix(P.B_theta))
 
     def at(self, theta: float):
+        """A(theta), B(theta) on the host (for checks against the oracle)."""
         A = sp.csr_matrix(self.A0 + theta * self.A_theta)
         B = sp.csr_matrix(self.B0 + theta * self.B_theta)
         A.sort_indices()
         B.sort_indices()
         return A, B
+
+    def device_ops(self, theta, device: int = 0):
+        """A(theta), B(theta)^T, A(theta)^T, B(theta) as device CSR matrices;
+        `theta` is a device scalar tensor."""
+        torch = _torch()
+        dev = _family_device(self, device)
+        coef = torch.cat([torch.ones(1, dtype=torch.float64, device=theta.device),
+                          theta.detach().reshape(1).to(torch.float64)])
+        out = []
+        for name in ("A", "BT", "AT", "B"):
+            op = dev[name]
+            nnz = op.val.numel()
+            # values = [v0, v_theta] [1, theta]^T on the union pattern
+            spk.dense_gemm_device(nnz, 1, 2, op.parts, nnz, coef, 2, op.val, nnz, device=device)
+            out.append(op.csr)
+        return tuple(out)
+
+    def device_theta_ops(self, device: int = 0):
+        """A_theta and B_theta as device CSR matrices (for the theta gradient)."""
+        dev = _family_device(self, device)
+        return dev["A_theta"], dev["B_theta"]
+
+
+class _DeviceOperator:
+    """X0 + theta X_theta on the union of the two sparsity patterns: the
+    pattern (int32) and the two value arrays on the device, and the values at
+    the last theta."""
+
+    def __init__(self, X0, Xt, device):
+        import numpy as np
+        torch = _torch()
+        X0, Xt = sp.csr_matrix(X0), sp.csr_matrix(Xt)
+        P = sp.csr_matrix(abs(X0) + abs(Xt))
+        P.eliminate_zeros()
+        P.sort_indices()
+        rows, cols = P.nonzero()
+        v0 = np.asarray(X0[rows, cols], dtype=np.float64).ravel()
+        vt = np.asarray(Xt[rows, cols], dtype=np.float64).ravel()
+        dv = "cuda:%d" % device
+        self.rowptr = torch.as_tensor(P.indptr.astype(np.int32), device=dv)
+        self.col = torch.as_tensor(P.indices.astype(np.int32), device=dv)
+        # column-major nnz x 2: [v0, v_theta]
+        self.parts = torch.as_tensor(np.stack([v0, vt]), device=dv).contiguous()
+        self.val = torch.empty(len(v0), dtype=torch.float64, device=dv)
+        self.csr = spk.DeviceCSR.from_device(P.shape, self.rowptr, self.col, self.val)
+
+
+def _family_device(fam: "OperatorFamily", device: int):
+    cache = fam.__dict__.setdefault("_device_cache", {})
+    if device not in cache:
+        cache[device] = {
+            "A": _DeviceOperator(fam.A0, fam.A_theta, device),
+            "BT": _DeviceOperator(fam.B0.T, fam.B_theta.T, device),
+            "AT": _DeviceOperator(fam.A0.T, fam.A_theta.T, device),
+            "B": _DeviceOperator(fam.B0, fam.B_theta, device),
+            "A_theta": spk.DeviceCSR(fam.A_theta),
+            "B_theta": spk.DeviceCSR(fam.B_theta),
+        }
+    return cache[device]
 
 
 def _torch():
@@ -66,16 +129,15 @@ def _make_function():
     class SylvesterBilinear(torch.autograd.Function):
         @staticmethod
         def forward(ctx, C1, C2, theta, u, v, family: OperatorFamily, opts: dict):
-            th = float(theta.detach().cpu())
-            A, B = family.at(th)
-            sol = spk.solve(A, sp.csr_matrix(B.T), C1.detach(), C2.detach(), **opts)
+            dA, dBT, dAT, dB = family.device_ops(theta)
+            sol = spk.solve(dA, dBT, C1.detach(), C2.detach(), **opts)
             X1, X2 = sol.X1, sol.X2
             uu, vv = u.detach().reshape(-1), v.detach().reshape(-1)
             if X1 is None:
                 val = torch.zeros((), dtype=torch.float64, device=C1.device)
             else:
                 val = (uu @ X1) @ (X2.T @ vv)
-            ctx.family, ctx.opts, ctx.A, ctx.B = family, opts, A, B
+            ctx.family, ctx.opts, ctx.AT, ctx.B = family, opts, dAT, dB
             ctx.sol = sol
             ctx.save_for_backward(C1, C2, u, v)
             return val
@@ -84,10 +146,10 @@ def _make_function():
         def backward(ctx, gL):
             C1, C2, u, v = ctx.saved_tensors
             uu, vv = u.detach().reshape(-1, 1), v.detach().reshape(-1, 1)
-            lam = spk.solve_adjoint(sp.csr_matrix(ctx.A.T), ctx.B, uu, vv, **ctx.opts)
+            lam = spk.solve_adjoint(ctx.AT, ctx.B, uu, vv, **ctx.opts)
+            dAth, dBth = ctx.family.device_theta_ops()
             dC1, dC2, dth = spk.adjoint_gradients(spk.result_view(ctx.sol), spk.result_view(lam),
-                                                  C1.detach(), C2.detach(), ctx.family.A_theta,
-                                                  ctx.family.B_theta)
+                                                  C1.detach(), C2.detach(), dAth, dBth)
             X1, X2 = ctx.sol.X1, ctx.sol.X2
             g = gL.to(torch.float64)
             du = (X1 @ (X2.T @ vv.reshape(-1))).reshape(u.shape) if X1 is not None else None

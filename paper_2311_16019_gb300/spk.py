@@ -147,6 +147,17 @@ class DeviceCSR:
         self.c = Csr(M.shape[0], M.shape[1], M.nnz, self.rowptr.data_ptr(), self.col.data_ptr(),
                      self.val.data_ptr())
 
+    @classmethod
+    def from_device(cls, shape, rowptr, col, val) -> "DeviceCSR":
+        """Wrap device tensors (int32 rowptr and col, float64 values) that the
+        caller keeps alive."""
+        self = cls.__new__(cls)
+        self.shape = tuple(shape)
+        self.rowptr, self.col, self.val = rowptr, col, val
+        self.c = Csr(self.shape[0], self.shape[1], int(val.numel()), rowptr.data_ptr(),
+                     col.data_ptr(), val.data_ptr())
+        return self
+
 
 class _CAI:
     def __init__(self, ptr: int, shape, typestr="<f8"):
@@ -577,6 +588,23 @@ def dense_gemm(A, B, *, ta="N", tb="N", alpha=1.0, beta=0.0, Cin=None, engine="t
     if rc != SPK_OK:
         raise SpkError(rc, h.error())
     return Cd.t().cpu().numpy()
+
+
+def dense_gemm_device(M: int, N: int, K: int, A, lda: int, B, ldb: int, Cm, ldc: int, *,
+                      ta="N", tb="N", alpha=1.0, beta=0.0, engine="fp64", device: int = 0,
+                      stream=None):
+    """Cm = alpha op(A) op(B) + beta Cm on device tensors (column-major views
+    given by the leading dimensions), through spk_dense_gemm."""
+    h = handle(device)
+    rc = h.lib.spk_dense_gemm(h.h, 0 if engine == "fp64" else 1, ta.encode(), tb.encode(), M, N,
+                              K, alpha, _ptr(A), lda, _ptr(B), ldb, beta, _ptr(Cm), ldc,
+                              _stream_ptr(stream))
+    if rc != SPK_OK:
+        raise SpkError(rc, h.error())
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
 
 
 def inspect(name: str, device: int = 0) -> np.ndarray:
