@@ -56,8 +56,7 @@ constexpr int kQsS = 8;                                   // slices
 constexpr int kQsBits = 7;                                // bits per slice
 constexpr int kQsTM = 128;                                // tile rows (M of the MMA)
 constexpr int kQsKC = 16;                                 // K per stage (one MMA per slice)
-constexpr int kQsStages = 2;                              // BF16 stages (MMA operands)
-constexpr int kQsStaging = 2;                             // int8 stages in flight (cp.async)
+constexpr int kQsStages = 3;                              // stages in flight per CTA
 constexpr int kQsKper = 256;                              // K positions per CTA
 constexpr int kQsSliceTile = kQsTM * kQsKC * 2;           // 4 KB (BF16, shared memory)
 constexpr int kQsStage = kQsS * kQsSliceTile;             // 32 KB
@@ -67,7 +66,7 @@ constexpr int kQsLoaders = 256;                           // warps 0..7 widen th
 constexpr int kQsLoads = kQsStage8 / 16 / kQsLoaders;     // 16-byte loads per loader and stage
 constexpr int kQsNmax = 32;                               // B rows (8 r, padded)
 constexpr int kQsBBytes = kQsNmax * kQsKper * 2;          // 16 KB
-constexpr int kQsSmem = kQsStages * kQsStage + kQsStaging * kQsStage8 + kQsBBytes;   // 112 KB: two CTAs per SM
+constexpr int kQsSmem = kQsStages * kQsStage + kQsBBytes; // 112 KB: two CTAs per SM
 constexpr uint32_t kQsLbo = 128;                          // next 8-element K group
 constexpr uint32_t kQsSboA = (kQsKC / 8) * 128;           // next 8-row group, A tiles
 constexpr uint32_t kQsSboB = (kQsKper / 8) * 128;         // next 8-row group, B
@@ -221,10 +220,10 @@ __device__ __forceinline__ void qs_epilogue_half(uint32_t trow, long long (&hi)[
 
 // One CTA per (128-row tile mt, K range ks of kQsKper positions):
 //   partial[(ks M + row) R + c] = sum_{k in range} Q-copy(row, k) B(k, c).
-// Warps 0..7 stream the int8 stages of the A copy into a staging ring by
-// cp.async (the first ones before B is split) and widen them into the BF16
-// stages; warp 8 lane 0 issues the MMAs (8 per stage, one per Q slice); all
-// warps split B into shared memory, warps 0..7 run the epilogue.
+// Warp 0 lane 0 streams the 32 KB stages of the A copy with bulk copies (the
+// first ones before B is split); warp 1 lane 0 issues the MMAs (8 per stage,
+// one per Q slice); all warps split B into shared memory and run the
+// epilogue.
 template <int R>
 __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restrict__ As, int M,
                                                           int KT, int K,
@@ -238,8 +237,7 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
   // smaller alignment keeps the static part small (two CTAs per SM)
   extern __shared__ __align__(128) uint8_t smem[];
   uint8_t* sA = smem;
-  uint8_t* s8 = smem + kQsStages * kQsStage;               // int8 staging ring
-  uint8_t* sB = s8 + kQsStaging * kQsStage8;
+  uint8_t* sB = smem + kQsStages * kQsStage;
   __shared__ __align__(8) uint64_t full[kQsStages], empty[kQsStages], done;
   __shared__ unsigned long long cmax[4];
   __shared__ int s_e[4];
@@ -276,22 +274,13 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
   __syncthreads();
   // loaders: the int8 digits of stage st, 16 bytes per load, kQsLoads per thread
   const bool loader = tid < kQsLoaders;
-  // stage st's int8 digits into staging slot st % kQsStaging by cp.async
-  // (16 bytes per copy, one commit group per stage); each loader widens
-  // exactly the chunks it copied, so no barrier is needed between the two
-  auto stage_in = [&](int st) {
-    const uint8_t* src = As + ((int64_t)mt * KT + kt0 + st) * kQsStage8;
-    uint8_t* dst = s8 + (st % kQsStaging) * kQsStage8;
+  auto load_stage = [&](int st, uint4 (&v)[kQsLoads]) {
+    const uint4* src = reinterpret_cast<const uint4*>(As + ((int64_t)mt * KT + kt0 + st) * kQsStage8);
 #pragma unroll
-    for (int u = 0; u < kQsLoads; ++u) {
-      const int o = 16 * (tid + u * kQsLoaders);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
-                   :: "r"(tc::smem_u32(dst + o)), "l"(src + o) : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int u = 0; u < kQsLoads; ++u) v[u] = __ldcs(src + tid + u * kQsLoaders);
   };
-  if (loader)
-    for (int st = 0; st < min(ns, kQsStaging); ++st) stage_in(st);
+  uint4 cur[kQsLoads], nxt[kQsLoads];
+  if (loader && ns > 0) load_stage(0, cur);
   // B digits: rows q R + c (q = digit plane, c = column) of this K range,
   // with the exponent of each column's largest magnitude in the range
   double bv[kVals];
@@ -339,13 +328,9 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
   const uint32_t tmem = tmem_base;
   if (loader) {
     // stage st into slot st % kQsStages once the MMAs of stage st - kQsStages
-    // have released it; the next stages' copies are in flight meanwhile
+    // have released it; the next stage's loads are in flight meanwhile
     for (int st = 0; st < ns; ++st) {
-      // this stage's group is complete once at most the later one is pending
-      if (st + 1 < ns)
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-      else
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      if (st + 1 < ns) load_stage(st + 1, nxt);
       const int slot = st % kQsStages;
       if (st >= kQsStages &&
           !tc::mbar_wait(tc::smem_u32(&empty[slot]), (uint32_t)((st / kQsStages - 1) & 1), kQsSpin)) {
@@ -354,20 +339,15 @@ __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restr
       }
       if (failed) break;
       uint8_t* dst = sA + slot * kQsStage;
-      const uint8_t* src8 = s8 + (st % kQsStaging) * kQsStage8;
 #pragma unroll
-      for (int u = 0; u < kQsLoads; ++u) {
-        const int q = tid + u * kQsLoaders;
-        qs_widen16(*reinterpret_cast<const uint4*>(src8 + 16 * q), dst + 32 * q);
-      }
+      for (int u = 0; u < kQsLoads; ++u) qs_widen16(cur[u], dst + 32 * (tid + u * kQsLoaders));
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(tc::smem_u32(&full[slot])) : "memory");
-      // the staging slot is free again (this thread read its chunks above)
-      if (st + kQsStaging < ns) stage_in(st + kQsStaging);
+#pragma unroll
+      for (int u = 0; u < kQsLoads; ++u) cur[u] = nxt[u];
     }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");   // none left in flight on any path
   } else if (tid == kQsLoaders) {
     // MMA issuer
     constexpr uint32_t idesc = tc::idesc_bf16(kQsTM, N);
