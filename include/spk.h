@@ -272,20 +272,24 @@ int spk_sylvester_dense(spk_handle* h, int32_t m, const double* H_dev,
  * or 'T', device pointers), by one of the library's two engines: engine 0,
  * the FP64 CUDA-core GEMM; engine 1, the tcgen05 tensor cores by
  * error-free splitting of the FP64 operands into BF16 slices (Ozaki et al.,
- * 2012): eight 7-bit slices per row of op(A) and column of op(B), level
- * sums exact in the FP32 accumulators, FP64 sum of the levels.  These are
- * the products of the projected solve (Eq. (3.4)); exposed for parity
- * tests.  SPK_ERR_ARG for bad sizes or pointers.  Synchronises `stream`. */
+ * 2012): eight balanced base-2^7 digits per entry, scaled per row of op(A)
+ * and column of op(B), level sums exact in the FP32 accumulators, combined
+ * exactly in 64-bit integers and converted to FP64 once.  These are the
+ * products of the projected solve (Eq. (3.4)) and of the factor recovery;
+ * exposed for parity tests and for small device-side products of the
+ * binding.  SPK_ERR_ARG for bad sizes or pointers.  Synchronises `stream`. */
 int spk_dense_gemm(spk_handle* h, int32_t engine, char ta, char tb, int32_t M, int32_t N,
                    int32_t K, double alpha, const double* A_dev, int64_t lda,
                    const double* B_dev, int64_t ldb, double beta, double* C_dev, int64_t ldc,
                    void* stream);
 
-/* spk_set_tensor_gemm: whether the handle's projected solves (the Gauss-Jordan
- * trailing updates and the right-hand-side products of the sign iteration)
- * run their large dense products on the tensor cores (on = 1, the default)
- * or on the FP64 CUDA cores (on = 0).  Both are FP64-accurate; the switch
- * exists for comparison.  Applies to the handle's batched workers too.    */
+/* spk_set_tensor_gemm: whether the handle's solves run their large dense
+ * FP64 products on the tensor cores (on = 1, the default) or on the FP64
+ * CUDA cores (on = 0): the whitening products against Q (Proposition 2.1,
+ * from 256 columns of Q and 1024 sketch rows), the Gauss-Jordan trailing
+ * updates and right-hand-side products of the projected solve (Eq. (3.4))
+ * and the factor recovery.  Both are FP64-accurate; the switch exists for
+ * comparison.  Applies to the handle's batched workers too.               */
 int spk_set_tensor_gemm(spk_handle* h, int32_t on);
 
 /* ---- allocation-free variant ----------------------------------------------
