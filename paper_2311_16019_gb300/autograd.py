@@ -73,6 +73,21 @@ class OperatorFamily:
         return dev["A_theta"], dev["B_theta"]
 
 
+def union_pattern(X0, Xt):
+    """The union of the sparsity patterns of X0 and Xt (CSR, sorted) and the
+    two matrices' values on it: (shape, indptr, indices, v0, vt), so that
+    X0 + theta Xt has the values v0 + theta vt on that pattern."""
+    import numpy as np
+    X0, Xt = sp.csr_matrix(X0), sp.csr_matrix(Xt)
+    P = sp.csr_matrix(abs(X0) + abs(Xt))
+    P.eliminate_zeros()
+    P.sort_indices()
+    rows, cols = P.nonzero()
+    v0 = np.asarray(X0[rows, cols], dtype=np.float64).ravel()
+    vt = np.asarray(Xt[rows, cols], dtype=np.float64).ravel()
+    return P.shape, P.indptr.astype(np.int32), P.indices.astype(np.int32), v0, vt
+
+
 class _DeviceOperator:
     """X0 + theta X_theta on the union of the two sparsity patterns: the
     pattern (int32) and the two value arrays on the device, and the values at
@@ -81,20 +96,14 @@ class _DeviceOperator:
     def __init__(self, X0, Xt, device):
         import numpy as np
         torch = _torch()
-        X0, Xt = sp.csr_matrix(X0), sp.csr_matrix(Xt)
-        P = sp.csr_matrix(abs(X0) + abs(Xt))
-        P.eliminate_zeros()
-        P.sort_indices()
-        rows, cols = P.nonzero()
-        v0 = np.asarray(X0[rows, cols], dtype=np.float64).ravel()
-        vt = np.asarray(Xt[rows, cols], dtype=np.float64).ravel()
+        shape, indptr, indices, v0, vt = union_pattern(X0, Xt)
         dv = "cuda:%d" % device
-        self.rowptr = torch.as_tensor(P.indptr.astype(np.int32), device=dv)
-        self.col = torch.as_tensor(P.indices.astype(np.int32), device=dv)
+        self.rowptr = torch.as_tensor(indptr, device=dv)
+        self.col = torch.as_tensor(indices, device=dv)
         # column-major nnz x 2: [v0, v_theta]
         self.parts = torch.as_tensor(np.stack([v0, vt]), device=dv).contiguous()
         self.val = torch.empty(len(v0), dtype=torch.float64, device=dv)
-        self.csr = spk.DeviceCSR.from_device(P.shape, self.rowptr, self.col, self.val)
+        self.csr = spk.DeviceCSR.from_device(shape, self.rowptr, self.col, self.val)
 
 
 def _family_device(fam: "OperatorFamily", device: int):
