@@ -81,7 +81,8 @@ __device__ __forceinline__ void digits8(double x, int e, int (&n)[8]) {
   n[0] = (int)N;
 }
 
-// BF16 bit pattern of an integer with |n| <= 256 (exact).
+// BF16 bit pattern of an integer with |n| <= 255 (exact; the digits passed
+// here have |n| <= 128).
 __device__ __forceinline__ uint32_t bf16_int(int n) {
   if (n == 0) return 0u;
   const uint32_t a = (uint32_t)(n < 0 ? -n : n);
