@@ -26,9 +26,13 @@
 // copies laid out for the two products:
 //   QA: rows = columns j of Q, K = rows i of Q   (A operand of Q^T w)
 //   QB: rows = rows i of Q,    K = columns j     (A operand of Q t)
-// Each copy is a sequence of 32 KB stages: for a tile of 128 rows and 16 K
-// positions, the 8 slice tiles of 4 KB in the tensor cores' K-major core
-// matrix layout (8 rows x 16 bytes), so one bulk copy moves a whole stage.
+// The digits are stored as biased bytes (n + 128), one byte per digit, so a
+// copy is as large as Q itself.  Each copy is a sequence of 16 KB stages:
+// for a tile of 128 rows and 16 K positions, the 8 slice tiles of 2 KB in
+// the byte order of the tensor cores' K-major core-matrix layout at half
+// width; loader warps read a stage with 16-byte loads (the next stage in
+// flight) and widen it to BF16 in shared memory, where byte offset o lands
+// at 2 o, the layout the MMAs read.
 //
 // Right-hand side.  Each CTA handles 256 K positions; it splits its part of
 // the r columns of w (or t) with e_c from the largest magnitude of column c
@@ -36,7 +40,8 @@
 // of N = 8 r rows (padded to 16 or 32), so one MMA per Q slice p and K step
 // of 16 gives the products of slice p with every digit plane q of every
 // column.  Each product n_p n_q is at most 2^13 in magnitude; over 256 K
-// positions every accumulator is an integer below 2^21 and exact in FP32.
+// positions every accumulator is an integer of magnitude at most 2^21 and
+// exact in FP32.
 // Pairs with p + q > 9 (weights below 2^-70) are dropped; the epilogue turns
 // the other 36 per column into integers, adds those of one weight level
 // 2^(-7 (p+q)) exactly, combines the levels exactly into two 64-bit integers
