@@ -225,9 +225,10 @@ __device__ __forceinline__ void qs_epilogue_half(uint32_t trow, long long (&hi)[
 
 // One CTA per (128-row tile mt, K range ks of kQsKper positions):
 //   partial[(ks M + row) R + c] = sum_{k in range} Q-copy(row, k) B(k, c).
-// Warp 0 lane 0 streams the 32 KB stages of the A copy with bulk copies (the
-// first ones before B is split); warp 1 lane 0 issues the MMAs (8 per stage,
-// one per Q slice); all warps split B into shared memory and run the
+// Warps 0..7 load the 16 KB int8 stages of the A copy (the first before B is
+// split, each next one while the current one is widened) and widen them into
+// a ring of 32 KB BF16 stages; warp 8 lane 0 issues the MMAs (8 per stage,
+// one per Q slice); all warps split B into shared memory, warps 0..7 run the
 // epilogue.
 template <int R>
 __global__ void __launch_bounds__(kQsThreads, 2) k_qs_mma(const uint8_t* __restrict__ As, int M,
