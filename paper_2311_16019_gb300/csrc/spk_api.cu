@@ -1004,7 +1004,7 @@ struct Side {
   double* T = nullptr;
   int64_t ldT = 0;
   double* Q = nullptr;       // s x ldT
-  // BF16-sliced copies of Q for the tensor-core whitening products
+  // int8 digit copies of Q for the tensor-core whitening products
   QsGeom qs;
   uint8_t *QA = nullptr, *QB = nullptr;
   bool qs_on = false;

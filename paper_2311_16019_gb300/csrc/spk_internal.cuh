@@ -275,8 +275,9 @@ void qt_finish_launch(const double* tpart, int64_t count, int nchunk, double* t,
 void q_update_finish_launch(const double* w_in, double* w_out, const double* partial, int64_t s,
                             int r, int nchunk, cudaStream_t st);
 
-// Whitening products on the tensor cores (k_qslice.cu): two BF16-sliced
-// copies of Q, appended as Q grows, and the two products from them.
+// Whitening products on the tensor cores (k_qslice.cu): two int8 digit
+// copies of Q (one byte per BF16 digit), appended as Q grows, and the two
+// products from them.
 struct QsGeom {
   int64_t s = 0;
   int mmax = 0;
